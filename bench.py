@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Benchmark of one fit_transform step of the UMAP hot path on GB300.
+
+A step is one pass of the whole path over one synthetic 70,000 x 50 input
+(exact k-NN graph -> fuzzy graph -> a,b -> init -> 500 SGD epochs), with the
+input already resident in device memory.  The metric is SGD edge-updates per
+second over the whole step: an edge update is one activation of a directed
+CSR entry together with its negative samples; the count per fit is
+sum_e floor(T q_e / 2^24), a pure function of the graph.
+
+Multi-GPU (torchrun): each rank embeds its own independent instance (data
+seed = rank); there is no exchange on the data path ("replicas", weak
+scaling).  The only collective is the max-reduction of the timings.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SGD edge-updates/s, s/embed at 70K & 10M; batched and MLP pts/s at equal recall"
+UNIT = "edge-updates/s"
+N_EPOCHS = 500
+K_NN = 15
+NEG = 5
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                  "sm_max_mhz": 2070.0}
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+def workload(rank: int, name: str):
+    import datagen
+    if name == "70k":
+        X, _ = datagen.config_70k(seed=rank)
+    elif name == "2k":
+        X, _ = datagen.config_small(seed=rank)
+    else:
+        raise ValueError(name)
+    return np.ascontiguousarray(X, dtype=np.float32)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.proc = None
+        self.device = device
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        else:
+            self.lines = []
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unavailable"], "samples": 0}
+        loaded = [v for v in sm if v > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- traffic record
+def kernel_traffic(kernel: str, source_rel: str):
+    """DRAM bytes per launch recorded from an ncu capture of `kernel`, if the
+    capture was taken from the current source of that kernel; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.md")
+    src = os.path.join(ROOT, source_rel)
+    if not (os.path.exists(path) and os.path.exists(src)):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
+    for ln in open(path):
+        cells = [c.strip() for c in ln.strip().strip("|").split("|")]
+        if len(cells) >= 4 and cells[0] == kernel and cells[3] == sha:
+            try:
+                return float(cells[2])
+            except ValueError:
+                return None
+    return None
+
+
+# ---------------------------------------------------------------- CPU (oracle) leg
+def oracle_fit_estimate(X: np.ndarray, n_query: int, n_sub: int, n_ep: int, seed: int = 0):
+    """Time the oracle on a bounded sample and extrapolate to one full fit.
+
+    k-NN: exact rows for `n_query` queries against all n points, scaled by
+    n / n_query.  Graph + epochs: the oracle's own k-NN, fuzzy graph and
+    `n_ep` epochs on an `n_sub`-point subsample, scaled linearly in n (and the
+    epochs by N_EPOCHS / n_ep).  Returns (seconds per fit, sample text).
+    """
+    from oracle import fuzzy as ofuzzy, knn as oknn, sgd as osgd
+    n = X.shape[0]
+    g = np.random.default_rng(seed)
+    rows = g.choice(n, size=n_query, replace=False)
+    t0 = time.perf_counter()
+    oknn.knn_rows(X, rows, K_NN)
+    t_knn = (time.perf_counter() - t0) * n / n_query
+    sub = np.sort(g.choice(n, size=n_sub, replace=False))
+    Xs = X[sub]
+    t0 = time.perf_counter()
+    si, sd = oknn.knn(Xs, K_NN)
+    t_sub_knn = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    gr = ofuzzy.build_csr(si, sd, N_EPOCHS, K_NN)
+    t_graph = (time.perf_counter() - t0) * n / n_sub
+    Y = osgd.init_embedding(n_sub, 1, 10.0)
+    t0 = time.perf_counter()
+    for t in range(n_ep):
+        Y = osgd.epoch(Y, gr["row_ptr"], gr["col"], gr["q"], 1.577, 0.895, 1.0 - t / N_EPOCHS, NEG, t, 2)
+    t_ep = (time.perf_counter() - t0) / n_ep * N_EPOCHS * n / n_sub
+    sample = (f"oracle (FP64 NumPy) timed on: exact k-NN of {n_query} query rows against all {n} "
+              f"points (x{n / n_query:.1f}); fuzzy graph and {n_ep} of {N_EPOCHS} epochs on a "
+              f"{n_sub}-point subsample (x{n / n_sub:.1f}, epochs x{N_EPOCHS / n_ep:.0f}); "
+              f"extrapolated linearly to one {n}-point fit (subsample k-NN {t_sub_knn:.2f}s not counted)")
+    return t_knn + t_graph + t_ep, sample
+
+
+def updates_per_fit_cpu(X: np.ndarray, n_sub: int, seed: int = 0) -> float:
+    """Edge updates of one fit estimated from the oracle's graph on a subsample
+    (per-point rate x n); used only where the GPU count is unavailable."""
+    from oracle import fuzzy as ofuzzy, knn as oknn, sgd as osgd
+    n = X.shape[0]
+    sub = np.sort(np.random.default_rng(seed).choice(n, size=n_sub, replace=False))
+    si, sd = oknn.knn(X[sub], K_NN)
+    gr = ofuzzy.build_csr(si, sd, N_EPOCHS, K_NN)
+    return float(osgd.active_count(gr["q"], N_EPOCHS).sum()) * n / n_sub
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    X = workload(0, args.workload)
+    n = X.shape[0]
+    cores = os.cpu_count()
+    updates = updates_per_fit_cpu(X, min(n, 10_000))
+    for _ in range(args.warmup):
+        oracle_fit_estimate(X, 200, min(n, 4000), 1)
+    times, sample = [], ""
+    for s in range(args.steps):
+        t, sample = oracle_fit_estimate(X, 300, min(n, 6000), 2, seed=s)
+        times.append(t)
+    sec = float(np.mean(times))
+    value = updates / sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args, n),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config(args, n):
+    return {"workload": f"{args.workload}: synthetic 28x28 blob images -> FP32 PCA to 50-d, "
+                        f"n={n}, k={K_NN}, {N_EPOCHS} epochs, {NEG} negatives, fit_transform"
+            if args.workload == "70k" else
+            f"{args.workload}: 10-cluster Gaussian mixture n={n} d=50, k={K_NN}, {N_EPOCHS} epochs",
+            "n": n, "d": 50, "k": K_NN, "n_epochs": N_EPOCHS, "neg": NEG,
+            "knn_mode": args.knn_mode, "l2": "256 MiB buffer written between timed steps",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    import paper_2603_04035_gb300 as drgb
+
+    X_host = workload(rank, args.workload)
+    n, d = X_host.shape
+    X = torch.from_numpy(X_host).to(dev)
+    params = dict(k=K_NN, n_epochs=N_EPOCHS, neg=NEG, knn_mode=args.knn_mode,
+                  seed_init=1, seed_neg=2)
+
+    # updates per fit from the library's own graph (bookkeeping, untimed)
+    idx, dst = drgb.knn_graph(X, K_NN, mode=args.knn_mode)
+    g = drgb.fuzzy_weights(idx, dst, N_EPOCHS)
+    q64 = g.q.to(torch.int64)
+    updates = float(((N_EPOCHS * q64) >> 24).sum().item())
+    nnz = g.nnz
+    act_sum_neg = updates  # active entries summed over the epochs
+    del idx, dst, g, q64
+
+    Y = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        drgb.fit_transform(X, out=Y, **params)
+    torch.cuda.synchronize(dev)
+
+    drgb.set_profiling(True, local)
+    stage_acc = {}
+    launches0 = drgb.launch_count(local)
+    step_ms = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            drgb.fit_transform(X, out=Y, **params)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            for kk, v in drgb.stage_times(local).items():
+                stage_acc[kk] = stage_acc.get(kk, 0.0) + v
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    launches = drgb.launch_count(local) - launches0
+    drgb.set_profiling(False, local)
+    total_ms = float(sum(step_ms))
+
+    # e2e: host buffers in and out, copies inside the timed region
+    X_pin = torch.from_numpy(X_host).pin_memory()
+    Y_pin = torch.empty((n, 2), dtype=torch.float32).pin_memory()
+    Xd = torch.empty_like(X)
+    e2e_ms = []
+    for s in range(max(1, args.steps)):
+        flush.fill_(1)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        Xd.copy_(X_pin, non_blocking=True)
+        drgb.fit_transform(Xd, out=Y, **params)
+        Y_pin.copy_(Y, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = float(sum(e2e_ms))
+
+    t = torch.tensor([total_ms, e2e_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms, e2e_total = float(t[0]), float(t[1])
+    value = world * updates * args.steps / (total_ms / 1e3)
+    e2e_value = world * updates * len(e2e_ms) / (e2e_total / 1e3)
+
+    if rank == 0:
+        peaks, peak_src = load_peaks()
+        roof = roofline(args, n, d, nnz, act_sum_neg, stage_acc, args.steps, peaks, peak_src)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config(args, n),
+                "s_per_embed": total_ms / args.steps / 1e3,
+                "edge_updates_per_fit": updates,
+                "stage_ms_per_step": {kk: v / args.steps for kk, v in stage_acc.items()},
+                "roofline": roof,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(X_host.nbytes),
+                        "d2h_bytes_per_step": int(n * 2 * 4),
+                        "ms_per_step": e2e_total / len(e2e_ms)},
+                "gpu_launches": int(launches),
+                "clocks": clk.summary(),
+                "paper_context": "UMAP fit_transform 2.60 s on Fashion-MNIST 70K, Apple M3 Ultra (Table 1)"}
+        if not args.no_cpu_baseline:
+            sec, sample = oracle_fit_estimate(X_host, 1500, 10_000, 3)
+            line["cpu_baseline"] = {"value": updates / sec, "unit": UNIT, "cores": os.cpu_count(),
+                                    "kind": "oracle", "sample": sample, "s_per_embed": sec}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def roofline(args, n, d, nnz, updates, stage_acc, steps, peaks, peak_src):
+    """Roofline entry for the step's dominant stage (its average launch)."""
+    knn_ms = stage_acc.get("knn", 0.0) / steps
+    ep_ms = stage_acc.get("epochs", 0.0) / steps
+    if ep_ms >= knn_ms:
+        per_launch_s = ep_ms / N_EPOCHS / 1e3
+        # algorithmic bytes per epoch (average over the T epochs): row_ptr,
+        # Y_i read + Y'_i write, col + q of every entry, 8-byte gathers of
+        # the tail and the negatives of every active entry
+        act_per_epoch = updates / N_EPOCHS
+        bytes_ep = 4 * (n + 1) + 16 * n + 8 * nnz + 8 * act_per_epoch * (1 + NEG)
+        achieved = bytes_ep / per_launch_s / 1e9
+        peak = float(peaks["hbm_gbs"])
+        return {"kernel": "embed_epoch_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": f"hbm_gbs ({peak_src})",
+                "bytes_per_launch": bytes_ep, "launch_ms": per_launch_s * 1e3,
+                "traffic": kernel_traffic("embed_epoch_kernel",
+                                          "paper_2603_04035_gb300/csrc/epoch.cu")}
+    per_launch_s = knn_ms / 1e3
+    if args.knn_mode != 2:
+        flops = 3.0 * n * n * d      # subtract, multiply, add per pair and dimension
+        mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        achieved = flops / per_launch_s / 1e12
+        return {"kernel": "knn_exact_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
+                               f"{mhz:.0f} MHz ({peak_src} clock)",
+                "flops_per_launch": flops, "launch_ms": knn_ms,
+                "traffic": kernel_traffic("knn_exact_kernel", "paper_2603_04035_gb300/csrc/knn.cu")}
+    flops = 2.0 * n * n * d
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    achieved = flops / per_launch_s / 1e12
+    return {"kernel": "knn_tc_kernel", "bound": "tensor", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_source": f"bf16_tflops_sustained ({peak_src})", "flops_per_launch": flops,
+            "launch_ms": knn_ms,
+            "traffic": kernel_traffic("knn_tc_kernel", "paper_2603_04035_gb300/csrc/knn_tc.cu")}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["70k", "2k"], default="70k")
+    ap.add_argument("--knn-mode", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,249 @@
+/*
+ * drgb.h - C ABI of the GB300 neighbour-embedding library (libdrgb.so).
+ *
+ * The library computes the data-parallel hot path of the UMAP method as used
+ * by mlx-vis (arXiv 2603.04035): the exact k-NN graph (Section 2.2), the
+ * fuzzy simplicial-set graph and the a, b kernel fit (Section 2.3), and the
+ * synchronous negative-sampling SGD epoch (Section 2.5, "UMAP's SGD step";
+ * Section 4.1, scatter-add updates on sampled edges), composed into
+ * fit_transform(X) -> n x 2 (Section 2.1, public API).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named X, Y, idx, dist, row_ptr, col, w, q, ... are DEVICE
+ *   pointers owned by the caller; the library never frees them and never keeps
+ *   them past the call.  Matrices are dense row-major: X is n x d FP32 (row
+ *   stride d), Y is n x 2 FP32 (x, y interleaved; 8-byte aligned).
+ * - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *   stream.  All device work is enqueued on it; calls return before it runs
+ *   unless documented as synchronous.
+ * - A drgb_ctx owns the library's scratch memory (grown on demand with
+ *   cudaMalloc, released by drgb_ctx_destroy), a device status word that the
+ *   kernels set on device-side errors, and the last error message.  A context
+ *   is bound to one device and must not be used from two host threads at once.
+ * - Every function returns an int status: DRGB_OK or a negative DRGB_ERR_*.
+ *   Argument errors are detected on the host before anything is enqueued.
+ *   Device-side errors (non-finite input, a timed-out wait) are recorded in
+ *   the context and reported by the next synchronising call (drgb_sync or a
+ *   call documented as synchronous).
+ */
+#ifndef DRGB_H
+#define DRGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DRGB_OK 0
+#define DRGB_ERR_INVALID (-1)    /* bad argument: null/misaligned pointer, n < k+1, k out of range */
+#define DRGB_ERR_WORKSPACE (-2)  /* caller-provided capacity too small */
+#define DRGB_ERR_CUDA (-3)       /* a CUDA runtime call failed (message in drgb_last_error) */
+#define DRGB_ERR_TIMEOUT (-4)    /* a bounded device-side wait gave up */
+#define DRGB_ERR_NONFINITE (-5)  /* NaN or Inf found in an input */
+#define DRGB_ERR_DEVICE (-6)     /* device is not sm_103 (GB300) */
+
+#define DRGB_MAX_K 32            /* largest supported number of neighbours */
+
+typedef struct drgb_ctx drgb_ctx;
+
+/* Hyper-parameters of fit_transform (Section 2.1: "instantiate with
+ * hyperparameters"; defaults follow UMAP as used in Section 3). */
+typedef struct drgb_params {
+    int32_t k;            /* neighbours per point (default 15), 1..DRGB_MAX_K */
+    int32_t n_epochs;     /* T, number of SGD epochs (Section 3: 500 for UMAP) */
+    int32_t neg;          /* negative samples per active edge (default 5) */
+    float lr0;            /* initial learning rate, decayed as lr0 (1 - t/T) */
+    float min_dist;       /* output-kernel min_dist (default 0.1) */
+    float spread;         /* output-kernel spread (default 1.0) */
+    float init_range;     /* Y0 ~ U[-init_range, init_range]^2 (default 10) */
+    uint64_t seed_init;   /* Philox key of the initialisation */
+    uint64_t seed_neg;    /* Philox key of the negative samples */
+    int32_t knn_mode;     /* 0 auto, 1 exact FP32 scan, 2 BF16 / 3 FP16 tensor-core + FP32 re-rank */
+    int32_t reserved;
+} drgb_params;
+
+/* Called after each epoch by fit_transform (Section 2.1, epoch_callback).
+ * Y_dev is the current device embedding (n x 2, valid during the call only);
+ * the stream is synchronised before the call.  Return non-zero to stop early. */
+typedef int (*drgb_epoch_cb)(int32_t epoch, const float* Y_dev, int64_t n, void* user);
+
+/* ------------------------------------------------------------------ context */
+
+/* Library version as 10000*major + 100*minor + patch. */
+int drgb_version(void);
+
+/* Create a context on `device` (must be compute capability 10.3).
+ * Errors: DRGB_ERR_INVALID (out == NULL), DRGB_ERR_DEVICE, DRGB_ERR_CUDA. */
+int drgb_ctx_create(int device, drgb_ctx** out);
+
+/* Free the context's scratch memory and the context.  NULL is a no-op. */
+int drgb_ctx_destroy(drgb_ctx* ctx);
+
+/* Last error message of `ctx` ("" if none); valid until the next call. */
+const char* drgb_last_error(const drgb_ctx* ctx);
+
+/* Synchronise `stream`, read and clear the device status word.
+ * Returns DRGB_OK or the first device-side error since the last sync. */
+int drgb_sync(drgb_ctx* ctx, void* stream);
+
+/* Bytes of scratch the context currently holds (for memory accounting). */
+int64_t drgb_ctx_scratch_bytes(const drgb_ctx* ctx);
+
+/* Number of kernels this context has launched (graph replays count every
+ * kernel node they contain).  Host-side counter, for launch accounting. */
+int64_t drgb_launch_count(const drgb_ctx* ctx);
+
+/* Tuning knobs (performance only; results do not depend on them):
+ *   DRGB_TUNE_EPOCH_ROWS  rows per warp block of the epoch kernel: 4, 8, 16, 31
+ * Returns DRGB_ERR_INVALID for an unknown parameter or value. */
+#define DRGB_TUNE_EPOCH_ROWS 1
+int drgb_set_tuning(drgb_ctx* ctx, int32_t param, int32_t value);
+
+/* Stage timing of drgb_fit_transform.  When enabled (on != 0), each fit
+ * records CUDA events on its stream between its stages; drgb_stage_times
+ * (synchronous: waits for the events) writes up to `max` elapsed times in
+ * milliseconds: [0] k-NN graph, [1] fuzzy graph, [2] initialisation,
+ * [3] epoch loop, and returns the number written (or a negative error). */
+int drgb_set_profiling(drgb_ctx* ctx, int on);
+int drgb_stage_times(drgb_ctx* ctx, float* ms, int max);
+
+/* ------------------------------------------------------------- k-NN graph */
+
+/* Exact k-nearest-neighbour graph (Section 2.2: "k-nearest neighbor search is
+ * the first stage of every method"; the paper uses approximate NNDescent, this
+ * library returns the exact graph).
+ *   X        n x d FP32, row-major (16-byte aligned).
+ *   idx_out  n x k int32: the k nearest OTHER points of each row (self
+ *            excluded), ordered by FP32 squared distance sum_c (x_ic - x_jc)^2
+ *            evaluated directly (not by the expansion), ties by lower index.
+ *   dist_out n x k FP32 Euclidean distances (square roots), same order.
+ * mode: 0 auto (3 when n >= 4096, d <= 61, k < 32; else 1), 1 exact FP32
+ * SIMT scan, 2 BF16 tcgen05 distance GEMM with a fused top-32 selection and
+ * an FP32 re-rank, 3 the same GEMM with FP16 operands (power-of-two scaled;
+ * 8x smaller rounding residual at the same tensor-core rate).  In modes 2
+ * and 3, rows whose candidate set cannot be certified to contain the exact
+ * FP32 k nearest are recomputed by the exact scan, so every mode returns the
+ * same exact result.
+ * Errors: DRGB_ERR_INVALID if n < k + 1, k < 1, k > DRGB_MAX_K, d < 1,
+ * a pointer is NULL or X is not 16-byte aligned. */
+int drgb_knn_graph(drgb_ctx* ctx, const float* X, int64_t n, int32_t d, int32_t k,
+                   int32_t mode, int32_t* idx_out, float* dist_out, void* stream);
+
+/* Number of rows whose BF16 candidate set was not certified during the last
+ * mode-2 drgb_knn_graph call on `ctx` (synchronous: waits for that call). */
+int drgb_knn_uncertified(drgb_ctx* ctx, int64_t* count, void* stream);
+
+/* -------------------------------------------------------- fuzzy weights */
+
+/* Fuzzy simplicial-set graph of a k-NN graph (Section 3: UMAP's
+ * "fuzzy-simplicial-set graph"; construction of UMAP, cited in Section 1):
+ *   rho_i   = dist[i][0];
+ *   sigma_i : sum_j exp(-max(0, dist[i][j] - rho_i) / sigma_i) = log2 k, by 64
+ *             bisection steps (start 1, double until bracketed, then halve),
+ *             floored at 1e-3 * mean_j dist[i][j];
+ *   w_{j|i} = exp(-max(0, dist[i][j] - rho_i) / sigma_i);
+ *   w_ij    = w_{j|i} + w_{i|j} - w_{j|i} w_{i|j} (fuzzy union).
+ * Output is a CSR holding both (i,j) and (j,i), rows sorted by column, with
+ * schedule words q = round(2^24 w / w_max); entries with n_epochs * q < 2^24
+ * (never active in n_epochs epochs) are dropped.
+ *   idx, dist  n x k (as produced by drgb_knn_graph; dist ascending per row).
+ *   row_ptr    n + 1 int32 (row_ptr[n] = number of entries, written on device).
+ *   col, w, q  capacity `cap` entries each (int32, FP32, uint32); cap >= 2 n k
+ *              always suffices.
+ *   rho, sigma optional n-float outputs (may be NULL).
+ * Errors: DRGB_ERR_INVALID (bad sizes/pointers), DRGB_ERR_WORKSPACE if
+ * cap < 2 n k. */
+int drgb_fuzzy_weights(drgb_ctx* ctx, const int32_t* idx, const float* dist, int64_t n,
+                       int32_t k, int32_t n_epochs, int32_t* row_ptr, int32_t* col, float* w,
+                       uint32_t* q, int64_t cap, float* rho, float* sigma, void* stream);
+
+/* ------------------------------------------------------------- a, b fit */
+
+/* Host, synchronous.  Least-squares fit of Phi(x) = 1 / (1 + a x^(2b)) to
+ * psi(x) = 1 (x < min_dist), exp(-(x - min_dist) / spread) otherwise, on 300
+ * points in [0, 3 spread], by Gauss-Newton (Section 2.3: "UMAP fits its output
+ * kernel parameters via Gauss-Newton optimization").  FP64 internally.
+ * Errors: DRGB_ERR_INVALID (NULL outputs, spread <= 0, min_dist < 0). */
+int drgb_find_ab(float spread, float min_dist, float* a, float* b);
+
+/* ----------------------------------------------------- initialisation */
+
+/* Y0[i] = (u_x, u_y) * 2R - R with u = (Philox4x32-10 word >> 8) / 2^24 at
+ * counter (i, 0, 0, 1), key = seed (low word, high word); one FP32 rounding.
+ * Y is n x 2 FP32 (8-byte aligned).  Errors: DRGB_ERR_INVALID. */
+int drgb_init_embedding(drgb_ctx* ctx, int64_t n, float init_range, uint64_t seed, float* Y,
+                        void* stream);
+
+/* ---------------------------------------------------------- SGD epoch */
+
+/* One synchronous SGD epoch t over a head-sorted CSR (Section 2.5, "UMAP's
+ * SGD step"; Section 4.1, scatter-add on randomly sampled edges).  For every
+ * row i and entry e = (i, j) active at t, i.e.
+ *   floor((t+1) q_e / 2^24) > floor(t q_e / 2^24):
+ *   d = |Y_i - Y_j|^2;  g_i += clip4(-2ab d^(b-1) / (1 + a d^b) (Y_i - Y_j)),
+ *   (0 when d = 0); then for j' < neg: u = word (j' mod 4) of
+ *   Philox4x32-10(key = seed, counter = (e, t, j' div 4, 0)), m = (u n) >> 32,
+ *   skipped if m = i, d = |Y_i - Y_m|^2,
+ *   g_i += clip4(2b / ((0.001 + d)(1 + a d^b)) (Y_i - Y_m)).
+ * Y_out[i] = Y_in[i] + lr g_i.  All reads are from Y_in (Y^(t)); Y_out must
+ * not alias Y_in.  Only row i is written per row: no atomics.
+ *   Y_in, Y_out  n x 2 FP32 (8-byte aligned);  row_ptr n+1, col, q as from
+ *   drgb_fuzzy_weights.
+ * Errors: DRGB_ERR_INVALID (NULL/aliasing/misaligned pointers, n < 1,
+ * neg < 0). */
+int drgb_embed_epoch(drgb_ctx* ctx, const float* Y_in, float* Y_out, const int32_t* row_ptr,
+                     const int32_t* col, const uint32_t* q, int64_t n, float a, float b, float lr,
+                     int32_t neg, int32_t epoch, uint64_t seed, void* stream);
+
+/* Epochs t_begin .. t_end-1 of a T = n_epochs schedule, lr_t = lr0 (1 - t/T),
+ * as one captured CUDA graph replayed on `stream`.  Y (n x 2) holds Y^(t_begin)
+ * on entry and Y^(t_end) on return; Y_tmp (n x 2) is ping-pong scratch.
+ * Because the schedule and the negatives are pure functions of (t, seed),
+ * running [0, t1) then [t1, T) gives bit-identical results to [0, T).
+ * Errors: as drgb_embed_epoch, plus DRGB_ERR_INVALID if
+ * 0 <= t_begin <= t_end <= n_epochs does not hold. */
+int drgb_embed_epochs(drgb_ctx* ctx, float* Y, float* Y_tmp, const int32_t* row_ptr,
+                      const int32_t* col, const uint32_t* q, int64_t n, float a, float b,
+                      float lr0, int32_t neg, int32_t t_begin, int32_t t_end, int32_t n_epochs,
+                      uint64_t seed, void* stream);
+
+/* ----------------------------------------------------------- full fit */
+
+/* fit_transform(X) -> Y (Section 2.1): k-NN graph, fuzzy graph, a, b fit,
+ * initialisation and p->n_epochs epochs.  X is n x d FP32 on the device,
+ * Y_out n x 2 FP32 on the device.  Synchronous (returns after Y_out is
+ * written and the device status has been checked).  `cb` may be NULL; when
+ * set it is called after every epoch (this costs one host sync per epoch).
+ * Errors: as the steps above; DRGB_ERR_NONFINITE if X holds NaN/Inf. */
+int drgb_fit_transform(drgb_ctx* ctx, const float* X, int64_t n, int32_t d,
+                       const drgb_params* p, float* Y_out, drgb_epoch_cb cb, void* user,
+                       void* stream);
+
+/* Fill *p with the defaults (k 15, 200 epochs, neg 5, lr0 1, min_dist 0.1,
+ * spread 1, init_range 10, seeds 1 and 2, knn_mode auto). */
+int drgb_default_params(drgb_params* p);
+
+/* -------------------------------------------------------- evaluation */
+
+/* k-NN preservation ("kNN-P", Section 3.2): mean over the query rows of
+ * |N_X(i) & N_Y(i)| / k, with exact neighbour sets in X (n x d, FP32 direct
+ * distances) and in Y (n x 2).  Query rows: all rows if n_query <= 0 or
+ * n_query >= n, else the evenly strided rows i_r = floor(r n / n_query),
+ * r < n_query.  Synchronous; *out receives the value. */
+int drgb_eval_recall(drgb_ctx* ctx, const float* X, const float* Y, int64_t n, int32_t d,
+                     int32_t k, int64_t n_query, double* out, void* stream);
+
+/* Trustworthiness (Section 3.2, Venna & Kaski 2006):
+ * 1 - 2 / (m k (2n - 3k - 1)) sum_i sum_{j in N_Y(i) \ N_X(i)} (r_X(i,j) - k)
+ * over the same query rows as drgb_eval_recall (m = number of rows), with
+ * exact FP32 ranks.  Synchronous. */
+int drgb_eval_trust(drgb_ctx* ctx, const float* X, const float* Y, int64_t n, int32_t d,
+                    int32_t k, int64_t n_query, double* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DRGB_H */

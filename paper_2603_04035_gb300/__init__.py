@@ -1,0 +1,312 @@
+"""GB300-native UMAP-style neighbour embedding (the hot path of mlx-vis,
+arXiv 2603.04035): exact k-NN graph, fuzzy simplicial-set graph, a,b fit and
+the synchronous negative-sampling SGD epoch, as hand-written CUDA for sm_103a
+behind the C ABI of include/drgb.h.
+
+This module only marshals arguments: PyTorch provides device memory and
+streams, every step runs in libdrgb's kernels.  There is no CPU fallback; the
+functions raise if the library is not built or no GB300 is present.
+
+Public API (names follow the C ABI):
+
+    knn_graph(X, k)                      -> (idx int32 n x k, dist float32 n x k)
+    fuzzy_weights(idx, dist, n_epochs)   -> Graph(row_ptr, col, w, q)
+    find_ab(spread, min_dist)            -> (a, b)
+    init_embedding(n, init_range, seed)  -> Y float32 n x 2
+    embed_epoch(Y, graph, a, b, lr, neg, epoch, seed) -> Y'
+    embed_epochs(Y, graph, a, b, lr0, neg, t_begin, t_end, n_epochs, seed)  (in place)
+    fit_transform(X, **params)           -> Y
+    eval_recall(X, Y, k, n_query) / eval_trust(X, Y, k, n_query) -> float
+    UMAP(**params).fit_transform(X)      (Section 2.1's class-based API)
+"""
+from __future__ import annotations
+
+import atexit
+import ctypes as C
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+from ._lib import MAX_K, Params  # noqa: F401
+
+__all__ = ["DrgbError", "Graph", "UMAP", "knn_graph", "fuzzy_weights", "find_ab",
+           "init_embedding", "embed_epoch", "embed_epochs", "fit_transform", "eval_recall",
+           "eval_trust", "default_params", "context", "knn_uncertified", "launch_count",
+           "set_profiling", "stage_times", "set_tuning"]
+
+
+class DrgbError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"drgb error {code} ({_lib.ERROR_NAMES.get(code, '?')}): {msg}")
+        self.code = code
+
+
+_contexts: dict[int, int] = {}
+
+
+def _destroy_all():
+    lib = _lib._lib
+    if lib is None:
+        return
+    for h in list(_contexts.values()):
+        lib.drgb_ctx_destroy(h)
+    _contexts.clear()
+
+
+atexit.register(_destroy_all)
+
+
+def context(device: int | None = None) -> int:
+    """Opaque drgb_ctx handle for a CUDA device (created on first use)."""
+    lib = _lib.load()
+    dev = torch.cuda.current_device() if device is None else int(device)
+    h = _contexts.get(dev)
+    if h is None:
+        out = C.c_void_p()
+        rc = lib.drgb_ctx_create(dev, C.byref(out))
+        if rc != 0:
+            raise DrgbError(rc, f"cannot create a context on cuda:{dev} (needs a GB300, sm_103)")
+        h = _contexts[dev] = out.value
+    return h
+
+
+def _check(rc: int, ctx) -> None:
+    if rc != 0:
+        msg = _lib.load().drgb_last_error(ctx)
+        raise DrgbError(rc, msg.decode() if msg else "")
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(dev: torch.device):
+    return C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _cuda(t: torch.Tensor, dtype, name: str, ndim: int | None = None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if ndim is not None and t.dim() != ndim:
+        raise ValueError(f"{name} must have {ndim} dimensions")
+    return t.contiguous()
+
+
+@dataclass
+class Graph:
+    """Head-sorted CSR of the fuzzy graph (device tensors)."""
+    row_ptr: torch.Tensor   # int32 n+1
+    col: torch.Tensor       # int32 nnz
+    w: torch.Tensor         # float32 nnz
+    q: torch.Tensor         # int32 nnz holding uint32 schedule words (< 2^25)
+    rho: torch.Tensor | None = None
+    sigma: torch.Tensor | None = None
+
+    @property
+    def n(self) -> int:
+        return self.row_ptr.numel() - 1
+
+    @property
+    def nnz(self) -> int:
+        return self.col.numel()
+
+
+def default_params() -> dict:
+    p = Params()
+    _lib.load().drgb_default_params(C.byref(p))
+    return {f: getattr(p, f) for f, _ in Params._fields_ if f != "reserved"}
+
+
+def launch_count(device=None) -> int:
+    """Kernels launched so far by the library on this device's context."""
+    return int(_lib.load().drgb_launch_count(context(device)))
+
+
+def set_tuning(param: int, value: int, device=None) -> None:
+    """Set a performance knob of the device's context (see include/drgb.h)."""
+    ctx = context(device)
+    _check(_lib.load().drgb_set_tuning(ctx, param, value), ctx)
+
+
+def set_profiling(on: bool, device=None) -> None:
+    _check(_lib.load().drgb_set_profiling(context(device), int(bool(on))), context(device))
+
+
+STAGES = ("knn", "fuzzy", "init", "epochs")
+
+
+def stage_times(device=None) -> dict:
+    """Per-stage milliseconds of the last profiled fit_transform (synchronous)."""
+    ms = (C.c_float * 8)()
+    ctx = context(device)
+    m = _lib.load().drgb_stage_times(ctx, ms, 8)
+    if m < 0:
+        _check(m, ctx)
+    return {STAGES[i] if i < len(STAGES) else f"stage{i}": ms[i] for i in range(m)}
+
+
+# ---------------------------------------------------------------- k-NN
+def knn_graph(X: torch.Tensor, k: int = 15, mode: int = 0):
+    """Exact k-NN graph of the rows of X (self excluded): (idx int32, dist float32)."""
+    X = _cuda(X, torch.float32, "X", 2)
+    n, d = X.shape
+    idx = torch.empty((n, k), dtype=torch.int32, device=X.device)
+    dist = torch.empty((n, k), dtype=torch.float32, device=X.device)
+    ctx = context(X.device.index)
+    _check(_lib.load().drgb_knn_graph(ctx, _ptr(X), n, d, k, mode, _ptr(idx), _ptr(dist),
+                                      _stream(X.device)), ctx)
+    return idx, dist
+
+
+def knn_uncertified(device=None) -> int:
+    ctx = context(device)
+    out = C.c_int64()
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    _check(_lib.load().drgb_knn_uncertified(ctx, C.byref(out), _stream(dev)), ctx)
+    return out.value
+
+
+# ---------------------------------------------------------------- fuzzy graph
+def fuzzy_weights(idx: torch.Tensor, dist: torch.Tensor, n_epochs: int,
+                  with_rho_sigma: bool = False) -> Graph:
+    idx = _cuda(idx, torch.int32, "idx", 2)
+    dist = _cuda(dist, torch.float32, "dist", 2)
+    n, k = idx.shape
+    dev = idx.device
+    cap = 2 * n * k
+    row_ptr = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    col = torch.empty(cap, dtype=torch.int32, device=dev)
+    w = torch.empty(cap, dtype=torch.float32, device=dev)
+    q = torch.empty(cap, dtype=torch.int32, device=dev)
+    rho = torch.empty(n, dtype=torch.float32, device=dev) if with_rho_sigma else None
+    sigma = torch.empty(n, dtype=torch.float32, device=dev) if with_rho_sigma else None
+    ctx = context(dev.index)
+    _check(_lib.load().drgb_fuzzy_weights(ctx, _ptr(idx), _ptr(dist), n, k, n_epochs, _ptr(row_ptr),
+                                          _ptr(col), _ptr(w), _ptr(q), cap, _ptr(rho), _ptr(sigma),
+                                          _stream(dev)), ctx)
+    nnz = int(row_ptr[n].item())
+    return Graph(row_ptr, col[:nnz], w[:nnz], q[:nnz], rho, sigma)
+
+
+def find_ab(spread: float = 1.0, min_dist: float = 0.1):
+    a, b = C.c_float(), C.c_float()
+    rc = _lib.load().drgb_find_ab(spread, min_dist, C.byref(a), C.byref(b))
+    if rc != 0:
+        raise DrgbError(rc, "find_ab: invalid spread/min_dist")
+    return a.value, b.value
+
+
+# ---------------------------------------------------------------- embedding
+def init_embedding(n: int, init_range: float = 10.0, seed: int = 1, device=None) -> torch.Tensor:
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    Y = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    ctx = context(dev.index)
+    _check(_lib.load().drgb_init_embedding(ctx, n, init_range, seed, _ptr(Y), _stream(dev)), ctx)
+    return Y
+
+
+def _graph_args(g: Graph):
+    return (_ptr(_cuda(g.row_ptr, torch.int32, "row_ptr")), _ptr(_cuda(g.col, torch.int32, "col")),
+            _ptr(_cuda(g.q, torch.int32, "q")))
+
+
+def embed_epoch(Y: torch.Tensor, g: Graph, a: float, b: float, lr: float, neg: int, epoch: int,
+                seed: int, out: torch.Tensor | None = None) -> torch.Tensor:
+    Y = _cuda(Y, torch.float32, "Y", 2)
+    n = Y.shape[0]
+    out = torch.empty_like(Y) if out is None else out
+    ctx = context(Y.device.index)
+    _check(_lib.load().drgb_embed_epoch(ctx, _ptr(Y), _ptr(out), *_graph_args(g), n, a, b, lr, neg,
+                                        epoch, seed, _stream(Y.device)), ctx)
+    return out
+
+
+def embed_epochs(Y: torch.Tensor, g: Graph, a: float, b: float, lr0: float, neg: int, t_begin: int,
+                 t_end: int, n_epochs: int, seed: int, tmp: torch.Tensor | None = None) -> torch.Tensor:
+    """Epochs [t_begin, t_end) of a T-epoch schedule, in place on Y (contiguous)."""
+    if not Y.is_contiguous():
+        raise ValueError("Y must be contiguous (updated in place)")
+    Y = _cuda(Y, torch.float32, "Y", 2)
+    tmp = torch.empty_like(Y) if tmp is None else tmp
+    ctx = context(Y.device.index)
+    _check(_lib.load().drgb_embed_epochs(ctx, _ptr(Y), _ptr(tmp), *_graph_args(g), Y.shape[0], a, b,
+                                         lr0, neg, t_begin, t_end, n_epochs, seed,
+                                         _stream(Y.device)), ctx)
+    return Y
+
+
+def _params(**kw) -> Params:
+    p = Params()
+    _lib.load().drgb_default_params(C.byref(p))
+    alias = {"n_neighbors": "k", "negative_sample_rate": "neg", "learning_rate": "lr0"}
+    for key, v in kw.items():
+        key = alias.get(key, key)
+        if key not in dict(Params._fields_):
+            raise TypeError(f"unknown parameter {key}")
+        setattr(p, key, v)
+    return p
+
+
+def fit_transform(X: torch.Tensor, epoch_callback=None, out: torch.Tensor | None = None,
+                  **params) -> torch.Tensor:
+    """Embed the rows of X (n x d FP32, CUDA) into n x 2; synchronous."""
+    X = _cuda(X, torch.float32, "X", 2)
+    n, d = X.shape
+    p = _params(**params)
+    Y = torch.empty((n, 2), dtype=torch.float32, device=X.device) if out is None else out
+    ctx = context(X.device.index)
+    if epoch_callback is None:
+        cb = _lib.EPOCH_CB()  # NULL function pointer
+    else:
+        def _cb(t, ptr, nn, user):
+            return int(bool(epoch_callback(t, Y)))
+        cb = _lib.EPOCH_CB(_cb)
+    _check(_lib.load().drgb_fit_transform(ctx, _ptr(X), n, d, C.byref(p), _ptr(Y), cb, None,
+                                          _stream(X.device)), ctx)
+    return Y
+
+
+# ---------------------------------------------------------------- metrics
+def eval_recall(X: torch.Tensor, Y: torch.Tensor, k: int = 15, n_query: int = 0) -> float:
+    X = _cuda(X, torch.float32, "X", 2)
+    Y = _cuda(Y, torch.float32, "Y", 2)
+    out = C.c_double()
+    ctx = context(X.device.index)
+    _check(_lib.load().drgb_eval_recall(ctx, _ptr(X), _ptr(Y), X.shape[0], X.shape[1], k, n_query,
+                                        C.byref(out), _stream(X.device)), ctx)
+    return out.value
+
+
+def eval_trust(X: torch.Tensor, Y: torch.Tensor, k: int = 15, n_query: int = 0) -> float:
+    X = _cuda(X, torch.float32, "X", 2)
+    Y = _cuda(Y, torch.float32, "Y", 2)
+    out = C.c_double()
+    ctx = context(X.device.index)
+    _check(_lib.load().drgb_eval_trust(ctx, _ptr(X), _ptr(Y), X.shape[0], X.shape[1], k, n_query,
+                                       C.byref(out), _stream(X.device)), ctx)
+    return out.value
+
+
+class UMAP:
+    """Class-based front end mirroring Section 2.1: instantiate with
+    hyper-parameters, call fit_transform(X) on an n x d array, receive n x 2."""
+
+    def __init__(self, n_neighbors: int = 15, n_epochs: int = 200, min_dist: float = 0.1,
+                 spread: float = 1.0, negative_sample_rate: int = 5, learning_rate: float = 1.0,
+                 init_range: float = 10.0, seed: int = 0, knn_mode: int = 0, epoch_callback=None):
+        self.params = dict(k=n_neighbors, n_epochs=n_epochs, min_dist=min_dist, spread=spread,
+                           neg=negative_sample_rate, lr0=learning_rate, init_range=init_range,
+                           seed_init=seed + 1, seed_neg=seed + 2, knn_mode=knn_mode)
+        self.epoch_callback = epoch_callback
+        self.embedding_ = None
+
+    def fit_transform(self, X) -> torch.Tensor:
+        if not isinstance(X, torch.Tensor):
+            X = torch.as_tensor(X, dtype=torch.float32)
+        if not X.is_cuda:
+            X = X.to("cuda", dtype=torch.float32)
+        self.embedding_ = fit_transform(X, epoch_callback=self.epoch_callback, **self.params)
+        return self.embedding_

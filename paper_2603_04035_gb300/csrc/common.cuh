@@ -1,0 +1,135 @@
+// Shared internals of libdrgb: the context, error plumbing, Philox and small
+// device helpers.  Not part of the public ABI (see include/drgb.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "drgb.h"
+
+namespace drgb {
+
+// ------------------------------------------------------------------ context
+struct Ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t l2_bytes = 0;
+    void* scratch = nullptr;      // grown on demand, 256-byte aligned carve-outs
+    size_t scratch_bytes = 0;
+    int* d_status = nullptr;      // device status word (0 = ok, else DRGB_ERR_*)
+    unsigned long long* d_counter = nullptr;  // diagnostic counter (uncertified rows)
+    unsigned int* d_work = nullptr;           // epoch work counters (self-resetting)
+    int64_t launches = 0;         // kernels launched (host-side count)
+    int epoch_rows = 8;           // rows per warp block of the epoch kernel (tuning)
+    int knn_tile_n = 256;         // database tile width of the tensor-core k-NN (tuning)
+    bool profiling = false;       // record stage events in fit_transform
+    cudaEvent_t stage_ev[8] = {};
+    int stage_marks = 0;
+    std::string err;
+};
+
+// Record stage boundary `idx` on `st` when profiling is enabled.
+int stage_mark(Ctx* c, int idx, cudaStream_t st);
+
+// Record a formatted error message in the context; returns `code`.
+int set_error(Ctx* c, int code, const char* fmt, ...);
+
+// Check a CUDA runtime call; on failure record it and return DRGB_ERR_CUDA.
+#define DRGB_CUDA(ctx, call)                                                          \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return ::drgb::set_error((ctx), DRGB_ERR_CUDA, "%s failed: %s (%s:%d)",   \
+                                     #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define DRGB_CHECK_LAUNCH(ctx)              \
+    do {                                     \
+        ++(ctx)->launches;                   \
+        DRGB_CUDA(ctx, cudaGetLastError());  \
+    } while (0)
+
+// Ensure the context holds at least `bytes` of scratch.  Growing synchronises
+// `stream` first, so that work still using the old buffer has finished.
+int ensure_scratch(Ctx* c, size_t bytes, cudaStream_t stream);
+
+// Bump allocator over the scratch buffer (256-byte aligned slices).
+struct Carve {
+    char* base;
+    size_t off = 0;
+    explicit Carve(void* b) : base(static_cast<char*>(b)) {}
+    template <class T>
+    T* take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T* p = reinterpret_cast<T*>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+    static size_t round(size_t bytes) { return (bytes + 255) & ~size_t(255); }
+};
+
+inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// ------------------------------------------------------------------ device status
+__device__ __forceinline__ void report_status(int* status, int code) {
+    atomicCAS(status, 0, code);
+}
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon et al., SC'11: four 32-bit counter words pass through 10 rounds of two
+// multiply-high/low S-boxes and a word permutation; the two key words are
+// bumped by the Weyl constants between rounds.
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__host__ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += W0;
+            k1 += W1;
+        }
+#ifdef __CUDA_ARCH__
+        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+#else
+        const uint64_t p0 = uint64_t(M0) * c.x, p1 = uint64_t(M1) * c.z;
+        const uint32_t hi0 = uint32_t(p0 >> 32), lo0 = uint32_t(p0);
+        const uint32_t hi1 = uint32_t(p1 >> 32), lo1 = uint32_t(p1);
+#endif
+        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    }
+    return c;
+}
+
+enum : uint32_t { TAG_NEGATIVE = 0u, TAG_INIT = 1u, TAG_MLP = 2u };
+
+// floor(u * n / 2^32): maps a uniform 32-bit word onto [0, n).
+__device__ __forceinline__ int64_t mulshift_index(uint32_t u, int64_t n) {
+    return int64_t((uint64_t(u) * uint64_t(n)) >> 32);
+}
+
+// ------------------------------------------------------------------ launch helpers
+inline int grid_for(int64_t work, int per_block, int max_blocks) {
+    int64_t g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > max_blocks) g = max_blocks;
+    return int(g);
+}
+
+// Exclusive prefix sum of `n` int32 counts into `out` (n + 1 entries, out[n] =
+// total), on `stream`, using `tmp` scratch of scan_scratch_elems(n) ints.
+size_t scan_scratch_elems(int64_t n);
+int exclusive_scan(Ctx* c, const int32_t* in, int32_t* out, int64_t n, int32_t* tmp,
+                   cudaStream_t stream);
+
+}  // namespace drgb
+
+struct drgb_ctx : public drgb::Ctx {};

@@ -1,0 +1,338 @@
+// Context management, error plumbing, device-wide scan and the host a,b fit.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace drgb {
+
+int set_error(Ctx* c, int code, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+int ensure_scratch(Ctx* c, size_t bytes, cudaStream_t stream) {
+    if (bytes <= c->scratch_bytes) return DRGB_OK;
+    if (c->scratch) {
+        DRGB_CUDA(c, cudaStreamSynchronize(stream));
+        DRGB_CUDA(c, cudaFree(c->scratch));
+        c->scratch = nullptr;
+        c->scratch_bytes = 0;
+    }
+    size_t want = bytes + bytes / 8;  // headroom against frequent regrowth
+    cudaError_t e = cudaMalloc(&c->scratch, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(c, DRGB_ERR_CUDA, "scratch allocation of %zu bytes failed: %s", want,
+                         cudaGetErrorString(e));
+    }
+    c->scratch_bytes = want;
+    return DRGB_OK;
+}
+
+int stage_mark(Ctx* c, int idx, cudaStream_t st) {
+    if (!c->profiling || idx < 0 || idx >= 8) return DRGB_OK;
+    if (!c->stage_ev[idx]) DRGB_CUDA(c, cudaEventCreate(&c->stage_ev[idx]));
+    DRGB_CUDA(c, cudaEventRecord(c->stage_ev[idx], st));
+    if (idx + 1 > c->stage_marks) c->stage_marks = idx + 1;
+    return DRGB_OK;
+}
+
+// ------------------------------------------------------------------ scan
+static constexpr int SCAN_THREADS = 256;
+static constexpr int SCAN_PER_THREAD = 8;
+static constexpr int SCAN_BLOCK = SCAN_THREADS * SCAN_PER_THREAD;
+
+__global__ void __launch_bounds__(SCAN_THREADS)
+scan_block_kernel(const int32_t* __restrict__ in, int32_t* __restrict__ out, int64_t n,
+                  int32_t* __restrict__ block_sums) {
+    __shared__ int32_t warp_tot[SCAN_THREADS / 32];
+    const int64_t base = int64_t(blockIdx.x) * SCAN_BLOCK + int64_t(threadIdx.x) * SCAN_PER_THREAD;
+    int32_t v[SCAN_PER_THREAD];
+    int32_t s = 0;
+#pragma unroll
+    for (int t = 0; t < SCAN_PER_THREAD; ++t) {
+        v[t] = (base + t < n) ? in[base + t] : 0;
+        s += v[t];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t wt = lane < SCAN_THREADS / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, wt, o);
+            if (lane >= o) wt += y;
+        }
+        if (lane < SCAN_THREADS / 32) warp_tot[lane] = wt;  // inclusive over warps
+    }
+    __syncthreads();
+    int32_t run = incl - s + (wid ? warp_tot[wid - 1] : 0);
+#pragma unroll
+    for (int t = 0; t < SCAN_PER_THREAD; ++t) {
+        if (base + t < n) out[base + t] = run;
+        run += v[t];
+    }
+    if (threadIdx.x == SCAN_THREADS - 1 && block_sums) block_sums[blockIdx.x] = run;
+}
+
+__global__ void scan_add_kernel(int32_t* __restrict__ out, int64_t n,
+                                const int32_t* __restrict__ offs) {
+    const int64_t i = int64_t(blockIdx.x) * SCAN_BLOCK + threadIdx.x;
+#pragma unroll
+    for (int t = 0; t < SCAN_PER_THREAD; ++t) {
+        int64_t j = i + int64_t(t) * SCAN_THREADS;
+        if (j < n) out[j] += offs[blockIdx.x];
+    }
+}
+
+size_t scan_scratch_elems(int64_t n) {
+    size_t total = 0;
+    int64_t m = n;
+    while (m > 0) {
+        int64_t nb = (m + SCAN_BLOCK - 1) / SCAN_BLOCK;
+        total += size_t(nb) * 2 + 2;
+        if (nb <= 1) break;
+        m = nb;
+    }
+    return total + 2;
+}
+
+// out[0..n] = exclusive scan of in[0..n), out[n] = total.
+static int scan_rec(Ctx* c, const int32_t* in, int32_t* out, int64_t n, int32_t* tmp,
+                    cudaStream_t st) {
+    const int64_t nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    int32_t* sums = tmp;           // nb block totals
+    int32_t* sums_scan = tmp + nb; // nb + 1 scanned totals
+    scan_block_kernel<<<unsigned(nb), SCAN_THREADS, 0, st>>>(in, out, n, sums);
+    DRGB_CHECK_LAUNCH(c);
+    if (nb == 1) {
+        // total = block sum; copy into out[n]
+        DRGB_CUDA(c, cudaMemcpyAsync(out + n, sums, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        return DRGB_OK;
+    }
+    int rc = scan_rec(c, sums, sums_scan, nb, tmp + 2 * nb + 2, st);
+    if (rc) return rc;
+    scan_add_kernel<<<unsigned(nb), SCAN_THREADS, 0, st>>>(out, n, sums_scan);
+    DRGB_CHECK_LAUNCH(c);
+    DRGB_CUDA(c, cudaMemcpyAsync(out + n, sums_scan + nb, sizeof(int32_t),
+                                 cudaMemcpyDeviceToDevice, st));
+    return DRGB_OK;
+}
+
+int exclusive_scan(Ctx* c, const int32_t* in, int32_t* out, int64_t n, int32_t* tmp,
+                   cudaStream_t st) {
+    if (n <= 0) {
+        DRGB_CUDA(c, cudaMemsetAsync(out, 0, sizeof(int32_t), st));
+        return DRGB_OK;
+    }
+    return scan_rec(c, in, out, n, tmp, st);
+}
+
+}  // namespace drgb
+
+using namespace drgb;
+
+extern "C" {
+
+int drgb_version(void) { return 10000; }
+
+int drgb_ctx_create(int device, drgb_ctx** out) {
+    if (!out) return DRGB_ERR_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return DRGB_ERR_DEVICE;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return DRGB_ERR_CUDA;
+    if (!(prop.major == 10 && prop.minor == 3)) return DRGB_ERR_DEVICE;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(device) != cudaSuccess) return DRGB_ERR_CUDA;
+    drgb_ctx* c = new drgb_ctx();
+    c->device = device;
+    c->num_sms = prop.multiProcessorCount;
+    c->l2_bytes = size_t(prop.l2CacheSize);
+    if (cudaMalloc(&c->d_status, 256) != cudaSuccess) {
+        delete c;
+        cudaSetDevice(prev);
+        return DRGB_ERR_CUDA;
+    }
+    cudaMemset(c->d_status, 0, 256);
+    c->d_counter = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(c->d_status) + 128);
+    c->d_work = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(c->d_status) + 192);
+    cudaDeviceSynchronize();
+    cudaSetDevice(prev);
+    *out = c;
+    return DRGB_OK;
+}
+
+int drgb_ctx_destroy(drgb_ctx* c) {
+    if (!c) return DRGB_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    if (c->scratch) cudaFree(c->scratch);
+    if (c->d_status) cudaFree(c->d_status);
+    for (auto& e : c->stage_ev)
+        if (e) cudaEventDestroy(e);
+    cudaSetDevice(prev);
+    delete c;
+    return DRGB_OK;
+}
+
+const char* drgb_last_error(const drgb_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int64_t drgb_ctx_scratch_bytes(const drgb_ctx* c) { return c ? int64_t(c->scratch_bytes) : 0; }
+
+int64_t drgb_launch_count(const drgb_ctx* c) { return c ? c->launches : 0; }
+
+int drgb_set_tuning(drgb_ctx* c, int32_t param, int32_t value) {
+    if (!c) return DRGB_ERR_INVALID;
+    switch (param) {
+        case DRGB_TUNE_EPOCH_ROWS:
+            if (value != 4 && value != 8 && value != 16 && value != 31)
+                return set_error(c, DRGB_ERR_INVALID, "epoch rows must be 4, 8, 16 or 31");
+            c->epoch_rows = value;
+            return DRGB_OK;
+        default:
+            return set_error(c, DRGB_ERR_INVALID, "unknown tuning parameter %d", param);
+    }
+}
+
+int drgb_set_profiling(drgb_ctx* c, int on) {
+    if (!c) return DRGB_ERR_INVALID;
+    c->profiling = on != 0;
+    c->stage_marks = 0;
+    return DRGB_OK;
+}
+
+int drgb_stage_times(drgb_ctx* c, float* ms, int max) {
+    if (!c || !ms || max < 0) return DRGB_ERR_INVALID;
+    int m = 0;
+    for (int s = 0; s + 1 < c->stage_marks && m < max; ++s, ++m) {
+        DRGB_CUDA(c, cudaEventSynchronize(c->stage_ev[s + 1]));
+        DRGB_CUDA(c, cudaEventElapsedTime(&ms[m], c->stage_ev[s], c->stage_ev[s + 1]));
+    }
+    return m;
+}
+
+int drgb_sync(drgb_ctx* c, void* stream) {
+    if (!c) return DRGB_ERR_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DRGB_CUDA(c, cudaStreamSynchronize(st));
+    int status = 0;
+    DRGB_CUDA(c, cudaMemcpy(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status) {
+        DRGB_CUDA(c, cudaMemset(c->d_status, 0, sizeof(int)));
+        return set_error(c, status, "device-side error %d reported by a kernel", status);
+    }
+    return DRGB_OK;
+}
+
+int drgb_default_params(drgb_params* p) {
+    if (!p) return DRGB_ERR_INVALID;
+    std::memset(p, 0, sizeof(*p));
+    p->k = 15;
+    p->n_epochs = 200;
+    p->neg = 5;
+    p->lr0 = 1.0f;
+    p->min_dist = 0.1f;
+    p->spread = 1.0f;
+    p->init_range = 10.0f;
+    p->seed_init = 1;
+    p->seed_neg = 2;
+    p->knn_mode = 0;
+    return DRGB_OK;
+}
+
+// Gauss-Newton least squares for Phi(x) = 1 / (1 + a x^(2b)) against the UMAP
+// target curve on 300 points of [0, 3 spread]; each step is halved until the
+// squared residual decreases.
+int drgb_find_ab(float spread, float min_dist, float* a_out, float* b_out) {
+    if (!a_out || !b_out || !(spread > 0.f) || !(min_dist >= 0.f)) return DRGB_ERR_INVALID;
+    const int G = 300;
+    double xs[G], ys[G], lx[G];
+    for (int t = 0; t < G; ++t) {
+        xs[t] = 3.0 * spread * t / (G - 1);
+        ys[t] = xs[t] < min_dist ? 1.0 : std::exp(-(xs[t] - min_dist) / spread);
+        lx[t] = xs[t] > 0 ? std::log(xs[t]) : 0.0;
+    }
+    auto cost = [&](double a, double b) {
+        double s = 0;
+        for (int t = 0; t < G; ++t) {
+            double p = xs[t] > 0 ? std::exp(2.0 * b * lx[t]) : 0.0;
+            double r = 1.0 / (1.0 + a * p) - ys[t];
+            s += r * r;
+        }
+        return s;
+    };
+    double a = 1.0, b = 1.0, f = cost(a, b);
+    for (int it = 0; it < 200; ++it) {
+        double JtJ00 = 0, JtJ01 = 0, JtJ11 = 0, g0 = 0, g1 = 0;
+        for (int t = 0; t < G; ++t) {
+            if (!(xs[t] > 0)) {
+                double r = 1.0 - ys[t];
+                (void)r;  // derivative is zero at x = 0
+                continue;
+            }
+            double p = std::exp(2.0 * b * lx[t]);
+            double den = 1.0 + a * p;
+            double r = 1.0 / den - ys[t];
+            double ja = -p / (den * den);
+            double jb = -a * p * 2.0 * lx[t] / (den * den);
+            JtJ00 += ja * ja;
+            JtJ01 += ja * jb;
+            JtJ11 += jb * jb;
+            g0 += ja * r;
+            g1 += jb * r;
+        }
+        double det = JtJ00 * JtJ11 - JtJ01 * JtJ01;
+        if (!(std::fabs(det) > 0)) break;
+        double da = -(JtJ11 * g0 - JtJ01 * g1) / det;
+        double db = -(-JtJ01 * g0 + JtJ00 * g1) / det;
+        double lam = 1.0, fn = f, an = a, bn = b;
+        bool moved = false;
+        while (lam > 1e-12) {
+            an = a + lam * da;
+            bn = b + lam * db;
+            if (an > 0 && bn > 0) {
+                fn = cost(an, bn);
+                if (fn < f) {
+                    moved = true;
+                    break;
+                }
+            }
+            lam *= 0.5;
+        }
+        if (!moved) break;
+        bool done = (f - fn) <= 1e-14 * (f > 1e-300 ? f : 1e-300);
+        a = an;
+        b = bn;
+        f = fn;
+        if (done) break;
+    }
+    *a_out = float(a);
+    *b_out = float(b);
+    return DRGB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,28 @@
+// Internal interface of the epoch kernels.
+#pragma once
+#include "common.cuh"
+
+namespace drgb {
+
+struct EpochArgs {
+    const float2* __restrict__ Y_in;
+    float2* __restrict__ Y_out;
+    const int32_t* __restrict__ row_ptr;
+    const int32_t* __restrict__ col;
+    const uint32_t* __restrict__ q;
+    int64_t n;
+    float a, b, lr;
+    int neg;
+    uint32_t t;
+    uint32_t k0, k1;
+    int* status;          // device status word (malformed CSR is reported here)
+    unsigned int* work;   // [0] next row block, [1] finished CTAs; zero between launches
+};
+
+int launch_epoch(Ctx* c, const EpochArgs& A, int rows_per_warp, cudaStream_t st);
+int launch_init(Ctx* c, float2* Y, int64_t n, float range, uint64_t seed, cudaStream_t st);
+int run_epochs(Ctx* c, float2* Y, float2* Y_tmp, const int32_t* rp, const int32_t* col,
+               const uint32_t* q, int64_t n, float a, float b, float lr0, int neg, int t_begin,
+               int t_end, int T, uint64_t seed, int rows_per_warp, cudaStream_t st);
+
+}  // namespace drgb

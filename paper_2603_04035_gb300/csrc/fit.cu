@@ -1,0 +1,99 @@
+// fit_transform(X) -> Y: the whole hot path on one stream (Section 2.1, the
+// public API; Section 3, the timed fit_transform).  k-NN graph -> fuzzy graph
+// -> a, b -> initialisation -> T epochs (one captured graph), all enqueued
+// before the single synchronisation at the end.
+#include "common.cuh"
+#include "epoch.cuh"
+#include "graph.cuh"
+#include "knn.cuh"
+
+namespace drgb {
+
+struct FitBuffers {
+    int32_t* idx;
+    float* dist;
+    int32_t* row_ptr;
+    int32_t* col;
+    float* w;
+    uint32_t* q;
+    float2* Y_tmp;
+    void* fuzzy_scratch;
+};
+
+static size_t fit_bytes(int64_t n, int k) {
+    const size_t nk = size_t(n) * k;
+    return Carve::round(nk * 4) * 2 + Carve::round((n + 1) * 4) + Carve::round(2 * nk * 4) * 3 +
+           Carve::round(n * 8) + fuzzy_scratch_bytes(n, k) + 4096;
+}
+
+static FitBuffers carve_fit(void* base, int64_t n, int k) {
+    const size_t nk = size_t(n) * k;
+    Carve cv(base);
+    FitBuffers b;
+    b.idx = cv.take<int32_t>(nk);
+    b.dist = cv.take<float>(nk);
+    b.row_ptr = cv.take<int32_t>(n + 1);
+    b.col = cv.take<int32_t>(2 * nk);
+    b.w = cv.take<float>(2 * nk);
+    b.q = cv.take<uint32_t>(2 * nk);
+    b.Y_tmp = cv.take<float2>(n);
+    b.fuzzy_scratch = cv.take<char>(fuzzy_scratch_bytes(n, k));
+    return b;
+}
+
+}  // namespace drgb
+
+using namespace drgb;
+
+extern "C" int drgb_fit_transform(drgb_ctx* c, const float* X, int64_t n, int32_t d,
+                                  const drgb_params* p, float* Y_out, drgb_epoch_cb cb, void* user,
+                                  void* stream) {
+    if (!c) return DRGB_ERR_INVALID;
+    if (!p || !Y_out) return set_error(c, DRGB_ERR_INVALID, "fit_transform: NULL pointer");
+    int rc = check_knn_args(c, X, n, d, p->k, Y_out, Y_out);
+    if (rc) return rc;
+    if (!aligned(Y_out, 8)) return set_error(c, DRGB_ERR_INVALID, "fit_transform: Y_out misaligned");
+    if (p->n_epochs < 1 || p->neg < 0 || p->neg > 64 || !(p->init_range > 0.f) || n > (INT32_MAX / 2) / p->k)
+        return set_error(c, DRGB_ERR_INVALID, "fit_transform: bad parameters");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int k = p->k;
+    rc = ensure_scratch(c, fit_bytes(n, k), st);
+    if (rc) return rc;
+    FitBuffers b = carve_fit(c->scratch, n, k);
+
+    float a = 0.f, bb = 0.f;
+    rc = drgb_find_ab(p->spread, p->min_dist, &a, &bb);
+    if (rc) return set_error(c, rc, "fit_transform: bad spread/min_dist");
+
+    c->stage_marks = 0;
+    rc = launch_nonfinite_scan(c, X, n * d, st);
+    if (rc) return rc;
+    if ((rc = stage_mark(c, 0, st))) return rc;
+    rc = drgb_knn_graph(c, X, n, d, k, p->knn_mode, b.idx, b.dist, stream);
+    if (rc) return rc;
+    if ((rc = stage_mark(c, 1, st))) return rc;
+    rc = build_fuzzy_graph(c, b.idx, b.dist, n, k, p->n_epochs, b.row_ptr, b.col, b.w, b.q, nullptr,
+                           nullptr, b.fuzzy_scratch, st);
+    if (rc) return rc;
+    if ((rc = stage_mark(c, 2, st))) return rc;
+    float2* Y = reinterpret_cast<float2*>(Y_out);
+    rc = launch_init(c, Y, n, p->init_range, p->seed_init, st);
+    if (rc) return rc;
+    if ((rc = stage_mark(c, 3, st))) return rc;
+    if (!cb) {
+        rc = run_epochs(c, Y, b.Y_tmp, b.row_ptr, b.col, b.q, n, a, bb, p->lr0, p->neg, 0, p->n_epochs,
+                        p->n_epochs, p->seed_neg, 0, st);
+        if (rc) return rc;
+    } else {
+        for (int t = 0; t < p->n_epochs; ++t) {
+            rc = run_epochs(c, Y, b.Y_tmp, b.row_ptr, b.col, b.q, n, a, bb, p->lr0, p->neg, t, t + 1,
+                            p->n_epochs, p->seed_neg, 0, st);
+            if (rc) return rc;
+            rc = drgb_sync(c, stream);
+            if (rc) return rc;
+            if (cb(t, Y_out, n, user)) break;
+        }
+    }
+    if ((rc = stage_mark(c, 4, st))) return rc;
+    return drgb_sync(c, stream);
+}

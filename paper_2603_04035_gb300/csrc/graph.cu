@@ -1,0 +1,317 @@
+// Fuzzy simplicial-set graph: per-row rho/sigma and directed weights, then the
+// fuzzy union of both directions as a head-sorted CSR with integer schedule
+// words.  Everything is deterministic: the in-lists built with atomics are
+// re-sorted by source before use, so the output does not depend on the order
+// in which atomics resolved.
+//
+// Passes (n rows, k neighbours, m_j = in-degree of j):
+//   1 rows      rho, sigma (64 bisection steps), w_{j|i}; out-list sorted by column
+//   2 indegree  histogram of tails
+//   3 scan      in_ptr
+//   4 scatter   in_src[in_ptr[j] + slot] = p   (p = i*k + s with idx[p] = j)
+//   5 sort      each in-list by p (rank sort, warp per row)
+//   6 merge     union of out-list and in-list by column -> tmp (cap k + m_i per row), w_max
+//   7 count     entries kept (T q >= 2^24)
+//   8 scan      row_ptr
+//   9 fill      col, w, q
+#include "common.cuh"
+#include "graph.cuh"
+
+namespace drgb {
+
+static constexpr uint32_t Q_ONE = 1u << 24;
+
+// ---------------------------------------------------------------- pass 1
+__global__ void fuzzy_rows_kernel(const int32_t* __restrict__ idx, const float* __restrict__ dist,
+                                  int64_t n, int k, float target, float* __restrict__ w_dir,
+                                  int32_t* __restrict__ out_col, float* __restrict__ out_w,
+                                  float* __restrict__ rho_out, float* __restrict__ sigma_out,
+                                  int* __restrict__ status) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        float dr[DRGB_MAX_K];
+        int32_t jr[DRGB_MAX_K];
+        float mean = 0.f;
+        bool bad = false;
+        for (int s = 0; s < k; ++s) {
+            dr[s] = dist[i * k + s];
+            jr[s] = idx[i * k + s];
+            mean += dr[s];
+            bad |= !(dr[s] >= 0.f && dr[s] < INFINITY) || jr[s] < 0 || jr[s] >= n || jr[s] == i;
+        }
+        if (bad) report_status(status, DRGB_ERR_INVALID);
+        mean /= float(k);
+        const float rho = dr[0];
+        float lo = 0.f, hi = INFINITY, mid = 1.f;
+        for (int it = 0; it < 64; ++it) {
+            float psum = 0.f;
+            for (int s = 0; s < k; ++s) psum += expf(-fmaxf(0.f, dr[s] - rho) / mid);
+            if (psum > target) {
+                hi = mid;
+            } else {
+                lo = mid;
+            }
+            mid = (hi == INFINITY) ? mid * 2.f : 0.5f * (lo + hi);
+        }
+        const float sigma = fmaxf(mid, 1e-3f * mean);
+        if (rho_out) rho_out[i] = rho;
+        if (sigma_out) sigma_out[i] = sigma;
+        float wr[DRGB_MAX_K];
+        for (int s = 0; s < k; ++s) {
+            const float ex = dr[s] - rho;
+            wr[s] = ex > 0.f ? expf(-ex / sigma) : 1.f;
+            w_dir[i * k + s] = wr[s];
+        }
+        // out-list sorted by column (insertion sort; k <= DRGB_MAX_K)
+        for (int s = 1; s < k; ++s) {
+            int32_t jj = jr[s];
+            float ww = wr[s];
+            int t = s - 1;
+            while (t >= 0 && jr[t] > jj) {
+                jr[t + 1] = jr[t];
+                wr[t + 1] = wr[t];
+                --t;
+            }
+            jr[t + 1] = jj;
+            wr[t + 1] = ww;
+        }
+        for (int s = 0; s < k; ++s) {
+            out_col[i * k + s] = jr[s];
+            out_w[i * k + s] = wr[s];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- passes 2, 4
+__global__ void indegree_kernel(const int32_t* __restrict__ idx, int64_t n, int k,
+                                int32_t* __restrict__ in_cnt) {
+    const int64_t nk = n * k;
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < nk;
+         p += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t j = idx[p];
+        if (j >= 0 && j < n && j != p / k) atomicAdd(&in_cnt[j], 1);
+    }
+}
+
+__global__ void in_scatter_kernel(const int32_t* __restrict__ idx, int64_t n, int k,
+                                  const int32_t* __restrict__ in_ptr, int32_t* __restrict__ in_fill,
+                                  int32_t* __restrict__ in_src) {
+    const int64_t nk = n * k;
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < nk;
+         p += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t j = idx[p];
+        if (j >= 0 && j < n && j != p / k) {
+            const int32_t slot = atomicAdd(&in_fill[j], 1);
+            in_src[in_ptr[j] + slot] = int32_t(p);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- pass 5
+// Warp per row: every element's destination is its rank (the p values of one
+// row are distinct), so the result is the ascending order regardless of the
+// order the scatter produced.
+__global__ void in_sort_kernel(const int32_t* __restrict__ in_ptr, const int32_t* __restrict__ src,
+                               int32_t* __restrict__ dst, int64_t n) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t j = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n; j += warps) {
+        const int32_t b = in_ptr[j], m = in_ptr[j + 1] - b;
+        for (int32_t a = lane; a < m; a += 32) {
+            const int32_t x = src[b + a];
+            int32_t rank = 0;
+            for (int32_t t = 0; t < m; ++t) rank += src[b + t] < x;
+            dst[b + rank] = x;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- pass 6
+__device__ __forceinline__ float fuzzy_union(float a, float b) {
+    // a + b - ab, written symmetrically in (a, b) so that w_ij == w_ji exactly
+    // and exactly 1 whenever either side is 1.
+    const float hi = fmaxf(a, b), lo = fminf(a, b);
+    return fmaf(lo, 1.0f - hi, hi);
+}
+
+__global__ void merge_kernel(const int32_t* __restrict__ out_col, const float* __restrict__ out_w,
+                             const int32_t* __restrict__ in_ptr, const int32_t* __restrict__ in_sorted,
+                             const float* __restrict__ w_dir, int64_t n, int k,
+                             int32_t* __restrict__ tcol, float* __restrict__ tw,
+                             int32_t* __restrict__ tcnt, unsigned int* __restrict__ wmax_bits) {
+    float local_max = 0.f;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t base = i * k + in_ptr[i];
+        const int32_t* oc = out_col + i * k;
+        const float* ow = out_w + i * k;
+        const int32_t ib = in_ptr[i], ie = in_ptr[i + 1];
+        int a = 0, bpos = ib, c = 0;
+        // skip invalid out entries (reported by pass 1)
+        while (a < k || bpos < ie) {
+            int32_t ca = INT32_MAX, cb = INT32_MAX;
+            if (a < k) {
+                ca = oc[a];
+                if (ca < 0 || ca >= n || ca == i) {
+                    ++a;
+                    continue;
+                }
+            }
+            if (bpos < ie) cb = int32_t(in_sorted[bpos] / k);
+            float w;
+            int32_t col;
+            if (ca == cb) {
+                w = fuzzy_union(ow[a], w_dir[in_sorted[bpos]]);
+                col = ca;
+                ++a;
+                ++bpos;
+            } else if (ca < cb) {
+                w = ow[a];
+                col = ca;
+                ++a;
+            } else {
+                w = w_dir[in_sorted[bpos]];
+                col = cb;
+                ++bpos;
+            }
+            tcol[base + c] = col;
+            tw[base + c] = w;
+            ++c;
+            local_max = fmaxf(local_max, w);
+        }
+        tcnt[i] = c;
+    }
+    // non-negative floats order like their bit patterns
+    for (int o = 16; o > 0; o >>= 1) local_max = fmaxf(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(wmax_bits, __float_as_uint(local_max));
+}
+
+__device__ __forceinline__ uint32_t schedule_word(float w, float w_max) {
+    return __float2uint_rn(float(Q_ONE) * (w / w_max));
+}
+
+// ---------------------------------------------------------------- passes 7, 9
+__global__ void prune_count_kernel(const int32_t* __restrict__ in_ptr, const float* __restrict__ tw,
+                                   const int32_t* __restrict__ tcnt, int64_t n, int k, int T,
+                                   const unsigned int* __restrict__ wmax_bits,
+                                   int32_t* __restrict__ keep_cnt) {
+    const float w_max = __uint_as_float(*wmax_bits);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t base = i * k + in_ptr[i];
+        int32_t c = 0;
+        for (int32_t t = 0; t < tcnt[i]; ++t)
+            c += uint64_t(T) * schedule_word(tw[base + t], w_max) >= Q_ONE;
+        keep_cnt[i] = c;
+    }
+}
+
+__global__ void fill_kernel(const int32_t* __restrict__ in_ptr, const int32_t* __restrict__ tcol,
+                            const float* __restrict__ tw, const int32_t* __restrict__ tcnt,
+                            int64_t n, int k, int T, const unsigned int* __restrict__ wmax_bits,
+                            const int32_t* __restrict__ row_ptr, int32_t* __restrict__ col,
+                            float* __restrict__ w, uint32_t* __restrict__ q) {
+    const float w_max = __uint_as_float(*wmax_bits);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t base = i * k + in_ptr[i];
+        int64_t o = row_ptr[i];
+        for (int32_t t = 0; t < tcnt[i]; ++t) {
+            const float wt = tw[base + t];
+            const uint32_t qt = schedule_word(wt, w_max);
+            if (uint64_t(T) * qt >= Q_ONE) {
+                col[o] = tcol[base + t];
+                w[o] = wt;
+                q[o] = qt;
+                ++o;
+            }
+        }
+    }
+}
+
+size_t fuzzy_scratch_bytes(int64_t n, int k) {
+    const size_t nk = size_t(n) * k;
+    size_t b = 0;
+    b += Carve::round(nk * 4) * 3;          // w_dir, out_col, out_w
+    b += Carve::round((n + 1) * 4) * 4;     // in_cnt, in_ptr, in_fill, keep_cnt
+    b += Carve::round(nk * 4) * 2;          // in_src, in_sorted
+    b += Carve::round(2 * nk * 4) * 2;      // tcol, tw
+    b += Carve::round(n * 4);               // tcnt
+    b += Carve::round(256);                 // w_max
+    b += Carve::round(scan_scratch_elems(n) * 4);
+    return b + 4096;
+}
+
+int build_fuzzy_graph(Ctx* c, const int32_t* idx, const float* dist, int64_t n, int k, int T,
+                      int32_t* row_ptr, int32_t* col, float* w, uint32_t* q, float* rho,
+                      float* sigma, void* scratch, cudaStream_t st) {
+    const size_t nk = size_t(n) * k;
+    Carve cv(scratch);
+    float* w_dir = cv.take<float>(nk);
+    int32_t* out_col = cv.take<int32_t>(nk);
+    float* out_w = cv.take<float>(nk);
+    int32_t* in_cnt = cv.take<int32_t>(n + 1);
+    int32_t* in_ptr = cv.take<int32_t>(n + 1);
+    int32_t* in_fill = cv.take<int32_t>(n + 1);
+    int32_t* keep_cnt = cv.take<int32_t>(n + 1);
+    int32_t* in_src = cv.take<int32_t>(nk);
+    int32_t* in_sorted = cv.take<int32_t>(nk);
+    int32_t* tcol = cv.take<int32_t>(2 * nk);
+    float* tw = cv.take<float>(2 * nk);
+    int32_t* tcnt = cv.take<int32_t>(n);
+    unsigned int* wmax = cv.take<unsigned int>(64);
+    int32_t* scan_tmp = cv.take<int32_t>(scan_scratch_elems(n));
+
+    const int TB = 256;
+    const int gmax = c->num_sms * 16;
+    const float target = float(std::log2(double(k)));
+    fuzzy_rows_kernel<<<grid_for(n, 128, gmax), 128, 0, st>>>(idx, dist, n, k, target, w_dir, out_col,
+                                                             out_w, rho, sigma, c->d_status);
+    DRGB_CHECK_LAUNCH(c);
+    DRGB_CUDA(c, cudaMemsetAsync(in_cnt, 0, (n + 1) * 4, st));
+    DRGB_CUDA(c, cudaMemsetAsync(in_fill, 0, (n + 1) * 4, st));
+    DRGB_CUDA(c, cudaMemsetAsync(wmax, 0, 4, st));
+    indegree_kernel<<<grid_for(int64_t(nk), TB, gmax), TB, 0, st>>>(idx, n, k, in_cnt);
+    DRGB_CHECK_LAUNCH(c);
+    int rc = exclusive_scan(c, in_cnt, in_ptr, n, scan_tmp, st);
+    if (rc) return rc;
+    in_scatter_kernel<<<grid_for(int64_t(nk), TB, gmax), TB, 0, st>>>(idx, n, k, in_ptr, in_fill, in_src);
+    DRGB_CHECK_LAUNCH(c);
+    in_sort_kernel<<<grid_for(n, TB / 32, gmax), TB, 0, st>>>(in_ptr, in_src, in_sorted, n);
+    DRGB_CHECK_LAUNCH(c);
+    merge_kernel<<<grid_for(n, TB, gmax), TB, 0, st>>>(out_col, out_w, in_ptr, in_sorted, w_dir, n, k,
+                                                      tcol, tw, tcnt, wmax);
+    DRGB_CHECK_LAUNCH(c);
+    prune_count_kernel<<<grid_for(n, TB, gmax), TB, 0, st>>>(in_ptr, tw, tcnt, n, k, T, wmax, keep_cnt);
+    DRGB_CHECK_LAUNCH(c);
+    rc = exclusive_scan(c, keep_cnt, row_ptr, n, scan_tmp, st);
+    if (rc) return rc;
+    fill_kernel<<<grid_for(n, TB, gmax), TB, 0, st>>>(in_ptr, tcol, tw, tcnt, n, k, T, wmax, row_ptr,
+                                                     col, w, q);
+    DRGB_CHECK_LAUNCH(c);
+    return DRGB_OK;
+}
+
+}  // namespace drgb
+
+using namespace drgb;
+
+extern "C" int drgb_fuzzy_weights(drgb_ctx* c, const int32_t* idx, const float* dist, int64_t n,
+                                  int32_t k, int32_t n_epochs, int32_t* row_ptr, int32_t* col,
+                                  float* w, uint32_t* q, int64_t cap, float* rho, float* sigma,
+                                  void* stream) {
+    if (!c) return DRGB_ERR_INVALID;
+    if (!idx || !dist || !row_ptr || !col || !w || !q)
+        return set_error(c, DRGB_ERR_INVALID, "fuzzy_weights: NULL pointer");
+    if (k < 1 || k > DRGB_MAX_K || n < k + 1 || n > (INT32_MAX / 2) / k || n_epochs < 1)
+        return set_error(c, DRGB_ERR_INVALID, "fuzzy_weights: bad n=%lld k=%d n_epochs=%d",
+                         (long long)n, k, n_epochs);
+    if (cap < 2 * n * k)
+        return set_error(c, DRGB_ERR_WORKSPACE, "fuzzy_weights: cap %lld < 2nk = %lld",
+                         (long long)cap, (long long)(2 * n * k));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = ensure_scratch(c, fuzzy_scratch_bytes(n, k), st);
+    if (rc) return rc;
+    return build_fuzzy_graph(c, idx, dist, n, k, n_epochs, row_ptr, col, w, q, rho, sigma,
+                             c->scratch, st);
+}

@@ -1,0 +1,334 @@
+// Exact k-NN by an FP32 scan (SIMT), and the FP32 rank counts used by the
+// trustworthiness metric.
+//
+// One thread owns one query row and keeps its best K (distance, index) pairs
+// sorted in registers.  The database is streamed through shared memory in
+// tiles of 32 points x 32 dimensions; every thread reads the same tile element
+// (a broadcast), so the tile costs no bank conflicts.  Squared distances are
+// evaluated directly as sum_c (x_qc - x_pc)^2 in dimension order, so the
+// result is the exact FP32 ranking (ties resolved by lower index because the
+// scan visits points in increasing index order and only strictly smaller
+// distances displace a kept entry).
+#include "common.cuh"
+#include "knn.cuh"
+
+namespace drgb {
+
+static constexpr int KNN_THREADS = 128;
+static constexpr int TP = 32;  // points per tile
+static constexpr int DC = 32;  // dimensions per tile
+
+template <int K>
+__device__ __forceinline__ void topk_insert(float (&D)[K], int32_t (&I)[K], float d, int32_t j) {
+    // precondition: d < D[K-1]
+#pragma unroll
+    for (int s = K - 1; s > 0; --s) {
+        const bool shift = d < D[s - 1];
+        const bool place = !shift && d < D[s];
+        D[s] = shift ? D[s - 1] : (place ? d : D[s]);
+        I[s] = shift ? I[s - 1] : (place ? j : I[s]);
+    }
+    if (d < D[0]) {
+        D[0] = d;
+        I[0] = j;
+    }
+}
+
+// Accumulate squared distances between this thread's query and TP database
+// points starting at p0, over all d dimensions.
+__device__ __forceinline__ void tile_distances(const float* __restrict__ X, int64_t n, int d,
+                                               int64_t qi, bool qvalid, int64_t p0, float* s_db,
+                                               float (&acc)[TP]) {
+#pragma unroll
+    for (int p = 0; p < TP; ++p) acc[p] = 0.f;
+    for (int c0 = 0; c0 < d; c0 += DC) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < TP * DC; t += blockDim.x) {
+            const int p = t / DC, cc = t % DC;
+            const int64_t gp = p0 + p;
+            const int gc = c0 + cc;
+            s_db[t] = (gp < n && gc < d) ? X[gp * d + gc] : 0.f;
+        }
+        __syncthreads();
+        float qv[DC];
+#pragma unroll
+        for (int cc = 0; cc < DC; ++cc) qv[cc] = (qvalid && c0 + cc < d) ? X[qi * d + c0 + cc] : 0.f;
+#pragma unroll 4
+        for (int p = 0; p < TP; ++p) {
+            float a = acc[p];
+#pragma unroll
+            for (int cc = 0; cc < DC; ++cc) {
+                const float df = qv[cc] - s_db[p * DC + cc];
+                a = fmaf(df, df, a);
+            }
+            acc[p] = a;
+        }
+    }
+}
+
+// Query rows: rows[r] (int64), or rows32[r] (int32), or r.  With n_rows_dev
+// the number of rows is read on the device (blocks past it exit at once) and
+// results go to row rows32[r] of the outputs instead of row r.
+//
+// With p_end > 0 the scan covers only database points [p_begin, p_end) and the
+// k best of that range are written as partial list blockIdx.y of row r
+// (idx_out/dist_out + (blockIdx.y * n_rows + r) * k, squared distances).
+template <int K>
+__global__ void __launch_bounds__(KNN_THREADS)
+knn_exact_kernel(const float* __restrict__ X, int64_t n, int d, int k,
+                 const int64_t* __restrict__ rows, int64_t n_rows, int32_t* __restrict__ idx_out,
+                 float* __restrict__ dist_out, int write_sqrt, const int32_t* __restrict__ rows32,
+                 const int32_t* __restrict__ n_rows_dev, int64_t chunk = 0) {
+    __shared__ __align__(16) float s_db[TP * DC];
+    if (n_rows_dev) {
+        n_rows = *n_rows_dev;
+        if (int64_t(blockIdx.x) * KNN_THREADS >= n_rows) return;  // whole block idle
+    }
+    const int64_t r = int64_t(blockIdx.x) * KNN_THREADS + threadIdx.x;
+    const bool valid = r < n_rows;
+    const int64_t qi = valid ? (rows ? rows[r] : (rows32 ? int64_t(rows32[r]) : r)) : 0;
+    int64_t orow = (n_rows_dev && !chunk) ? qi : r;
+    int64_t p_begin = 0, p_end = n;
+    if (chunk) {
+        p_begin = int64_t(blockIdx.y) * chunk;
+        p_end = p_begin + chunk < n ? p_begin + chunk : n;
+        orow = int64_t(blockIdx.y) * n_rows + r;
+    }
+    float D[K];
+    int32_t I[K];
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+        D[s] = INFINITY;
+        I[s] = -1;
+    }
+    float acc[TP];
+    for (int64_t p0 = p_begin; p0 < p_end; p0 += TP) {
+        tile_distances(X, p_end, d, qi, valid, p0, s_db, acc);
+#pragma unroll
+        for (int p = 0; p < TP; ++p) {
+            const int64_t gp = p0 + p;
+            if (acc[p] < D[K - 1] && gp < p_end && gp != qi) topk_insert<K>(D, I, acc[p], int32_t(gp));
+        }
+    }
+    if (valid) {
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            if (s < k) {
+                idx_out[orow * k + s] = I[s];
+                dist_out[orow * k + s] = write_sqrt ? sqrtf(D[s]) : D[s];
+            }
+        }
+    }
+}
+
+// Merge the C partial k-lists (squared distances, ascending) of each listed
+// row into its final k nearest, ordered by (distance, index).
+template <int K>
+__global__ void merge_partials_kernel(const int32_t* __restrict__ pidx, const float* __restrict__ pd2,
+                                      int64_t cnt, int C, int k, const int32_t* __restrict__ rows32,
+                                      int32_t* __restrict__ idx_out, float* __restrict__ dist_out) {
+    for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < cnt; r += int64_t(gridDim.x) * blockDim.x) {
+        float D[K];
+        int32_t I[K];
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            D[s] = INFINITY;
+            I[s] = INT32_MAX;
+        }
+        for (int c = 0; c < C; ++c) {
+            for (int s = 0; s < k; ++s) {
+                const float a = pd2[(int64_t(c) * cnt + r) * k + s];
+                const int32_t j = pidx[(int64_t(c) * cnt + r) * k + s];
+                if (j < 0 || !(a < D[K - 1] || (a == D[K - 1] && j < I[K - 1]))) continue;
+#pragma unroll
+                for (int t = K - 1; t > 0; --t) {
+                    const bool shift = a < D[t - 1] || (a == D[t - 1] && j < I[t - 1]);
+                    const bool place = !shift && (a < D[t] || (a == D[t] && j < I[t]));
+                    D[t] = shift ? D[t - 1] : (place ? a : D[t]);
+                    I[t] = shift ? I[t - 1] : (place ? j : I[t]);
+                }
+                if (a < D[0] || (a == D[0] && j < I[0])) {
+                    D[0] = a;
+                    I[0] = j;
+                }
+            }
+        }
+        const int64_t row = rows32[r];
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            if (s < k) {
+                idx_out[row * k + s] = I[s];
+                dist_out[row * k + s] = sqrtf(D[s]);
+            }
+        }
+    }
+}
+
+size_t knn_rows_scratch_bytes(int64_t max_rows, int k, int num_sms) {
+    (void)num_sms;
+    return 2 * Carve::round(size_t(max_rows) * 64 * k * 4) + 1024;
+}
+
+int launch_knn_exact_rows(Ctx* c, const float* X, int64_t n, int d, int k, const int32_t* rows32,
+                          const int32_t* n_rows_dev, int64_t max_rows, int32_t* idx_out,
+                          float* dist_out, cudaStream_t st, void* part_scratch, size_t part_bytes) {
+    // The number of rows is small in practice; read it and spread the scan
+    // over database chunks so that the rows are not serialised on a few SMs.
+    int32_t cnt32 = 0;
+    DRGB_CUDA(c, cudaMemcpyAsync(&cnt32, n_rows_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    DRGB_CUDA(c, cudaStreamSynchronize(st));
+    const int64_t cnt = cnt32 < max_rows ? cnt32 : max_rows;
+    if (cnt <= 0) return DRGB_OK;
+    const int row_blocks = int((cnt + KNN_THREADS - 1) / KNN_THREADS);
+    int C = (4 * c->num_sms + row_blocks - 1) / row_blocks;
+    const int64_t max_c = (n + 255) / 256;               // at least 256 points per chunk
+    if (C > max_c) C = int(max_c);
+    if (C > 64) C = 64;
+    const size_t need = 2 * Carve::round(size_t(cnt) * C * k * 4);
+    if (C <= 1 || part_scratch == nullptr || need > part_bytes) {
+        const int blocks = row_blocks;
+        if (k <= 16)
+            knn_exact_kernel<16><<<blocks, KNN_THREADS, 0, st>>>(X, n, d, k, nullptr, cnt, idx_out, dist_out, 1,
+                                                                rows32, n_rows_dev);
+        else
+            knn_exact_kernel<32><<<blocks, KNN_THREADS, 0, st>>>(X, n, d, k, nullptr, cnt, idx_out, dist_out, 1,
+                                                                rows32, n_rows_dev);
+        DRGB_CHECK_LAUNCH(c);
+        return DRGB_OK;
+    }
+    Carve cv(part_scratch);
+    int32_t* pidx = cv.take<int32_t>(size_t(cnt) * C * k);
+    float* pd2 = cv.take<float>(size_t(cnt) * C * k);
+    const int64_t chunk = (n + C - 1) / C;
+    dim3 grid(row_blocks, C);
+    if (k <= 16)
+        knn_exact_kernel<16><<<grid, KNN_THREADS, 0, st>>>(X, n, d, k, nullptr, cnt, pidx, pd2, 0, rows32,
+                                                          nullptr, chunk);
+    else
+        knn_exact_kernel<32><<<grid, KNN_THREADS, 0, st>>>(X, n, d, k, nullptr, cnt, pidx, pd2, 0, rows32,
+                                                          nullptr, chunk);
+    DRGB_CHECK_LAUNCH(c);
+    const int mb = grid_for(cnt, 128, c->num_sms * 4);
+    if (k <= 16)
+        merge_partials_kernel<16><<<mb, 128, 0, st>>>(pidx, pd2, cnt, C, k, rows32, idx_out, dist_out);
+    else
+        merge_partials_kernel<32><<<mb, 128, 0, st>>>(pidx, pd2, cnt, C, k, rows32, idx_out, dist_out);
+    DRGB_CHECK_LAUNCH(c);
+    return DRGB_OK;
+}
+
+int launch_knn_exact(Ctx* c, const float* X, int64_t n, int d, int k, const int64_t* rows,
+                     int64_t n_rows, int32_t* idx_out, float* dist_out, bool write_sqrt,
+                     cudaStream_t st) {
+    const int blocks = int((n_rows + KNN_THREADS - 1) / KNN_THREADS);
+    if (blocks < 1) return DRGB_OK;
+    if (k <= 16)
+        knn_exact_kernel<16><<<blocks, KNN_THREADS, 0, st>>>(X, n, d, k, rows, n_rows, idx_out, dist_out,
+                                                            write_sqrt, nullptr, nullptr);
+    else
+        knn_exact_kernel<32><<<blocks, KNN_THREADS, 0, st>>>(X, n, d, k, rows, n_rows, idx_out, dist_out,
+                                                            write_sqrt, nullptr, nullptr);
+    DRGB_CHECK_LAUNCH(c);
+    return DRGB_OK;
+}
+
+// For query row r (point qi) and its k targets tgt[r][s], count the points l != qi
+// that precede the target in the FP32 (distance, index) order: rank - 1.
+template <int K>
+__global__ void __launch_bounds__(KNN_THREADS)
+rank_kernel(const float* __restrict__ X, int64_t n, int d, int k, const int64_t* __restrict__ rows,
+            int64_t n_rows, const int32_t* __restrict__ tgt, int64_t* __restrict__ excess_out) {
+    __shared__ __align__(16) float s_db[TP * DC];
+    const int64_t r = int64_t(blockIdx.x) * KNN_THREADS + threadIdx.x;
+    const bool valid = r < n_rows;
+    const int64_t qi = valid ? (rows ? rows[r] : r) : 0;
+    float td[K];
+    int32_t tj[K];
+    int32_t cnt[K];
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+        tj[s] = (valid && s < k) ? tgt[r * k + s] : -1;
+        cnt[s] = 0;
+        td[s] = -1.f;  // filled during the scan when the target itself is met
+    }
+    // pass 1: distances to the targets (same formula and order as the scan)
+    for (int s = 0; s < K; ++s) {
+        if (s >= k || tj[s] < 0) continue;
+        float a = 0.f;
+        for (int cc = 0; cc < d; ++cc) {
+            const float df = X[qi * d + cc] - X[int64_t(tj[s]) * d + cc];
+            a = fmaf(df, df, a);
+        }
+        td[s] = a;
+    }
+    float acc[TP];
+    for (int64_t p0 = 0; p0 < n; p0 += TP) {
+        tile_distances(X, n, d, qi, valid, p0, s_db, acc);
+#pragma unroll
+        for (int p = 0; p < TP; ++p) {
+            const int64_t gp = p0 + p;
+            if (gp >= n || gp == qi) continue;
+#pragma unroll
+            for (int s = 0; s < K; ++s)
+                cnt[s] += (acc[p] < td[s]) || (acc[p] == td[s] && gp < tj[s]);
+        }
+    }
+    if (valid) {
+        int64_t ex = 0;
+#pragma unroll
+        for (int s = 0; s < K; ++s)
+            if (s < k && tj[s] >= 0 && cnt[s] + 1 > k) ex += cnt[s] + 1 - k;
+        excess_out[r] = ex;
+    }
+}
+
+int launch_rank(Ctx* c, const float* X, int64_t n, int d, int k, const int64_t* rows,
+                int64_t n_rows, const int32_t* tgt, int64_t* excess_out, cudaStream_t st) {
+    const int blocks = int((n_rows + KNN_THREADS - 1) / KNN_THREADS);
+    if (blocks < 1) return DRGB_OK;
+    if (k <= 16)
+        rank_kernel<16><<<blocks, KNN_THREADS, 0, st>>>(X, n, d, k, rows, n_rows, tgt, excess_out);
+    else
+        rank_kernel<32><<<blocks, KNN_THREADS, 0, st>>>(X, n, d, k, rows, n_rows, tgt, excess_out);
+    DRGB_CHECK_LAUNCH(c);
+    return DRGB_OK;
+}
+
+__global__ void nonfinite_scan_kernel(const float* __restrict__ X, int64_t count, int* status) {
+    bool bad = false;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
+         i += int64_t(gridDim.x) * blockDim.x)
+        bad |= !isfinite(X[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) report_status(status, DRGB_ERR_NONFINITE);
+}
+
+int launch_nonfinite_scan(Ctx* c, const float* X, int64_t count, cudaStream_t st) {
+    nonfinite_scan_kernel<<<grid_for(count, 256, c->num_sms * 8), 256, 0, st>>>(X, count, c->d_status);
+    DRGB_CHECK_LAUNCH(c);
+    return DRGB_OK;
+}
+
+int check_knn_args(Ctx* c, const float* X, int64_t n, int d, int k, const void* idx_out,
+                   const void* dist_out) {
+    if (!c) return DRGB_ERR_INVALID;
+    if (!X || !idx_out || !dist_out) return set_error(c, DRGB_ERR_INVALID, "knn_graph: NULL pointer");
+    if (!aligned(X, 16)) return set_error(c, DRGB_ERR_INVALID, "knn_graph: X must be 16-byte aligned");
+    if (k < 1 || k > DRGB_MAX_K || d < 1 || n < int64_t(k) + 1 || n > INT32_MAX)
+        return set_error(c, DRGB_ERR_INVALID, "knn_graph: bad sizes n=%lld d=%d k=%d", (long long)n, d, k);
+    return DRGB_OK;
+}
+
+}  // namespace drgb
+
+using namespace drgb;
+
+extern "C" int drgb_knn_graph(drgb_ctx* c, const float* X, int64_t n, int32_t d, int32_t k,
+                              int32_t mode, int32_t* idx_out, float* dist_out, void* stream) {
+    int rc = check_knn_args(c, X, n, d, k, idx_out, dist_out);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (mode == 2 || mode == 3) return knn_tc(c, X, n, d, k, mode == 3, idx_out, dist_out, st);
+    if (mode == 0 && knn_tc_preferred(n, d, k)) return knn_tc(c, X, n, d, k, true, idx_out, dist_out, st);
+    if (mode != 0 && mode != 1) return set_error(c, DRGB_ERR_INVALID, "knn_graph: bad mode %d", mode);
+    return launch_knn_exact(c, X, n, d, k, nullptr, n, idx_out, dist_out, true, st);
+}

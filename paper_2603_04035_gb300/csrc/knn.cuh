@@ -1,0 +1,31 @@
+// Internal interface of the k-NN kernels.
+#pragma once
+#include "common.cuh"
+
+namespace drgb {
+
+int check_knn_args(Ctx* c, const float* X, int64_t n, int d, int k, const void* idx_out,
+                   const void* dist_out);
+// Exact FP32 scan for the given query rows (rows == nullptr: rows 0..n_rows-1).
+int launch_knn_exact(Ctx* c, const float* X, int64_t n, int d, int k, const int64_t* rows,
+                     int64_t n_rows, int32_t* idx_out, float* dist_out, bool write_sqrt,
+                     cudaStream_t st);
+// Exact FP32 scan of the rows listed in rows32[0 .. *n_rows_dev) (at most
+// max_rows); results are written to those rows.  Synchronises `st` once to
+// read the count, then splits the scan over database chunks (partial lists in
+// part_scratch, merged by a second kernel).
+int launch_knn_exact_rows(Ctx* c, const float* X, int64_t n, int d, int k, const int32_t* rows32,
+                          const int32_t* n_rows_dev, int64_t max_rows, int32_t* idx_out,
+                          float* dist_out, cudaStream_t st, void* part_scratch, size_t part_bytes);
+size_t knn_rows_scratch_bytes(int64_t max_rows, int k, int num_sms);
+// Per query row: sum over its k targets of max(0, rank_X - k).
+int launch_rank(Ctx* c, const float* X, int64_t n, int d, int k, const int64_t* rows,
+                int64_t n_rows, const int32_t* tgt, int64_t* excess_out, cudaStream_t st);
+int launch_nonfinite_scan(Ctx* c, const float* X, int64_t count, cudaStream_t st);
+
+// BF16 tensor-core candidate generation + FP32 re-rank (knn_tc.cu).
+bool knn_tc_preferred(int64_t n, int d, int k);
+int knn_tc(Ctx* c, const float* X, int64_t n, int d, int k, bool f16, int32_t* idx_out, float* dist_out,
+           cudaStream_t st);
+
+}  // namespace drgb

@@ -1,0 +1,701 @@
+// Exact k-NN through a BF16 tensor-core distance GEMM (tcgen05, TMEM, TMA),
+// a fused per-row top-k' selection, an FP32 re-rank of the candidates and a
+// certificate that proves the candidate set holds the exact FP32 k nearest.
+//
+// Stage (A1): the columns are centred (distances are translation invariant,
+// centring shrinks the rounding error), scaled by a power of two S, rounded to
+// the 16-bit operand type and written as two K = 64 operand matrices
+//     XA_i = [ x~_i, C, C, C, 0 ... ]       XB_j = [ -2 x~_j, h_j, m_j, l_j, 0 ... ]
+// where C (h + m + l) is a three-way 16-bit split of n_j = |x~_j|^2 (FP32).
+// The tensor-core product XA_i . XB_j is then s_ij = n_j - 2 x~_i . x~_j, and
+// the squared distance between the rounded points is n_i + s_ij.  For a fixed
+// query row i, ordering by s is ordering by distance, so the epilogue needs
+// no norms at all.  Two operand types share the code: BF16 (S = C = 1) and
+// FP16 (S scales max |x - mean| to 2^10, C = 2^15), whose 11-bit significand
+// leaves an 8x smaller rounding residual at the same tensor-core rate.
+//
+// GEMM + select (A2): one CTA owns 128 query rows (TMEM lanes) and streams all
+// database tiles of 256 rows.  Warp 0 issues TMA loads into a 4-stage ring,
+// warp 1 issues 4 MMAs (M128 N256 K16) per tile into one of two TMEM
+// accumulators, and 8 epilogue warps (two per TMEM lane quarter, one per
+// column half) read the accumulator with tcgen05.ld, reject a 32-column chunk
+// with one min-reduction unless it can enter the row's list, and keep the
+// best 32 (s, j) pairs per row sorted in registers.
+//
+// Re-rank + certify (A3): exact FP32 squared distances sum_c (x_ic - x_jc)^2
+// of the 32 candidates (the same arithmetic as the FP32 scan), top-k by
+// (distance, index).  With delta_i = |x_i - x~_i| (BF16 rounding residual)
+// and eps_i bounding the FP32 accumulation error, every point outside the
+// list is at distance >= sqrt(n_i + s_thr - eps_i) - delta_i - delta_max.
+// If that bound exceeds the k-th exact distance the row is certified; other
+// rows are recomputed by the exact FP32 scan.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+#include "knn.cuh"
+
+namespace drgb {
+
+static constexpr int TC_BM = 128;
+static constexpr int TC_BN = 256;
+static constexpr int TC_K = 64;
+static constexpr int TC_STAGES = 4;
+static constexpr int TC_KP = 32;                 // candidates kept per row
+static constexpr int TC_EPI_WARPS = 8;
+static constexpr int TC_THREADS = 64 + TC_EPI_WARPS * 32;
+static constexpr int TC_A_BYTES = TC_BM * TC_K * 2;   // 16 KiB
+static constexpr int TC_B_BYTES = TC_BN * TC_K * 2;   // 32 KiB
+static constexpr int TC_TMEM_COLS = 512;               // two 256-column accumulators
+static constexpr int TC_QCAP = 16;                     // per-thread candidate queue slots
+static constexpr size_t TC_QUEUE_BYTES = size_t(TC_EPI_WARPS) * 32 * TC_QCAP * 8;
+static constexpr size_t TC_SMEM = 1024 + TC_A_BYTES + TC_STAGES * TC_B_BYTES + 256 + TC_QUEUE_BYTES;
+static constexpr unsigned long long TC_TIMEOUT_NS = 2000000000ull;  // 2 s per wait
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long global_timer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after TC_TIMEOUT_NS or when another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          int* status) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = global_timer();
+    while (true) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (global_timer() - t0 > TC_TIMEOUT_NS) {
+            *abort_flag = 1;
+            report_status(status, DRGB_ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte
+// swizzle layout: rows of 128 B, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= uint64_t((addr & 0x3FFFFu) >> 4);        // start address
+    d |= uint64_t(1) << 16;                       // leading byte offset (unused for this layout)
+    d |= uint64_t(1024 >> 4) << 32;               // stride byte offset: next 8-row group
+    d |= uint64_t(1) << 46;                       // descriptor version
+    d |= uint64_t(2) << 61;                       // 128-byte swizzle
+    return d;
+}
+// Instruction descriptor (kind::f16): D = F32, A = B = BF16 (format 1) or
+// FP16 (format 0), both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_f16kind(int M, int N, bool f16) {
+    return (1u << 4) | (f16 ? 0u : (1u << 7) | (1u << 10)) | (uint32_t(N >> 3) << 17) |
+           (uint32_t(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16kind(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+// 32 lanes x 32 consecutive FP32 columns; waits for completion.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Sorted insertion into an ascending list (precondition: v < L[KP-1]); an
+// equal value keeps the earlier (smaller) index first.
+__device__ __forceinline__ void list_insert(float (&L)[TC_KP], int32_t (&I)[TC_KP], float v, int32_t j) {
+#pragma unroll
+    for (int s = TC_KP - 1; s > 0; --s) {
+        const bool shift = v < L[s - 1];
+        const bool place = !shift && v < L[s];
+        L[s] = shift ? L[s - 1] : (place ? v : L[s]);
+        I[s] = shift ? I[s - 1] : (place ? j : I[s]);
+    }
+    if (v < L[0]) {
+        L[0] = v;
+        I[0] = j;
+    }
+}
+
+// ------------------------------------------------------------------ A1: staging
+typedef uint16_t op16;  // raw 16-bit operand (BF16 or FP16 bits)
+
+template <bool F16>
+__device__ __forceinline__ op16 to_op(float v) {
+    if constexpr (F16) return __half_as_ushort(__float2half_rn(v));
+    else return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+template <bool F16>
+__device__ __forceinline__ float from_op(op16 b) {
+    if constexpr (F16) return __half2float(__ushort_as_half(b));
+    else return __bfloat162float(__ushort_as_bfloat16(b));
+}
+
+// Power-of-two operand scale: FP16 maps max |x - mean| to at most 2^10.
+template <bool F16>
+__device__ __forceinline__ float operand_scale(const unsigned int* maxbits) {
+    if constexpr (!F16) return 1.0f;
+    const float amax = __uint_as_float(maxbits[2]);
+    if (!(amax > 0.f)) return 1.0f;
+    int e;
+    frexpf(amax, &e);                      // amax < 2^e
+    return ldexpf(1.0f, e - 10);
+}
+
+__global__ void tc_absmax_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ mean,
+                                 unsigned int* __restrict__ maxbits) {
+    float m = 0.f;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n * d; t += int64_t(gridDim.x) * blockDim.x)
+        m = fmaxf(m, fabsf(X[t] - mean[t % d]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&maxbits[2], __float_as_uint(m));
+}
+
+__global__ void tc_colsum_kernel(const float* __restrict__ X, int64_t n, int d, float* __restrict__ partial) {
+    // partial[blockIdx.x * d + c] = sum over this block's rows of X[., c]; thread c strides rows
+    for (int c = threadIdx.x; c < d; c += blockDim.x) {
+        float s = 0.f;
+        for (int64_t i = blockIdx.x; i < n; i += gridDim.x) s += X[i * d + c];
+        partial[int64_t(blockIdx.x) * d + c] = s;
+    }
+}
+
+__global__ void tc_mean_kernel(const float* __restrict__ partial, int nblk, int d, int64_t n,
+                               float* __restrict__ mean) {
+    for (int c = threadIdx.x; c < d; c += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += partial[int64_t(b) * d + c];
+        mean[c] = float(s / double(n));
+    }
+}
+
+// Warp per row: lanes own dimensions (lane, lane + 32).  Norms and residuals
+// are stored in the original units (the scale S is a power of two).
+template <bool F16>
+__global__ void tc_stage_kernel(const float* __restrict__ X, int64_t n, int64_t n_pad, int d,
+                                const float* __restrict__ mean, op16* __restrict__ XA,
+                                op16* __restrict__ XB, float* __restrict__ norm,
+                                float* __restrict__ resid, unsigned int* __restrict__ maxbits) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    const float S = operand_scale<F16>(maxbits), inv_S = 1.0f / S;
+    const float C = F16 ? 32768.0f : 1.0f, inv_C = 1.0f / C;
+    float nmax = 0.f, rmax = 0.f;
+    for (int64_t i = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n_pad; i += warps) {
+        float xc[2], xb[2];
+        float sq = 0.f, rs = 0.f, cs = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            float v = 0.f;
+            if (i < n && c < d) v = (X[i * d + c] - mean[c]) * inv_S;
+            xc[h] = v;
+            xb[h] = from_op<F16>(to_op<F16>(v));
+            sq = fmaf(xb[h], xb[h], sq);
+            const float r = v - xb[h];
+            rs = fmaf(r, r, rs);
+            cs = fmaf(v, v, cs);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            rs += __shfl_xor_sync(0xffffffffu, rs, o);
+            cs += __shfl_xor_sync(0xffffffffu, cs, o);
+        }
+        // three-way split of n / C (huge for padding rows: never selected)
+        const float nv = i < n ? sq * inv_C : (F16 ? 65504.0f : 3.0e38f);
+        const op16 nh = to_op<F16>(nv);
+        const float r1 = nv - from_op<F16>(nh);
+        const op16 nm = to_op<F16>(r1);
+        const op16 nl = to_op<F16>(r1 - from_op<F16>(nm));
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            op16 a = to_op<F16>(xb[h]);
+            op16 b = to_op<F16>(-2.0f * xb[h]);
+            if (c == d || c == d + 1 || c == d + 2) {
+                a = to_op<F16>(C);
+                b = c == d ? nh : (c == d + 1 ? nm : nl);
+            }
+            XA[i * TC_K + c] = a;
+            XB[i * TC_K + c] = b;
+        }
+        if (lane == 0) {
+            // residual norm, widened by the FP32 rounding of the centring and
+            // scaling and (FP16) by a possible flush of subnormal operands
+            const float flush = F16 ? 6.2e-5f * sqrtf(float(d)) : 0.f;
+            const float delta = (sqrtf(rs) * (1.0f + 1e-6f) + 2.4e-7f * sqrtf(cs) + flush) * S;
+            if (i < n) {
+                norm[i] = sq * S * S;
+                resid[i] = delta;
+                nmax = fmaxf(nmax, sq * S * S);
+                rmax = fmaxf(rmax, delta);
+            }
+        }
+    }
+    if (lane == 0) {
+        atomicMax(&maxbits[0], __float_as_uint(nmax));
+        atomicMax(&maxbits[1], __float_as_uint(rmax));
+    }
+}
+
+// ------------------------------------------------------------------ A2: GEMM + top-k'
+struct TcParams {
+    int64_t n;
+    int n_tiles;
+    int32_t* cand_idx;   // n x TC_KP
+    float* cand_s;       // n x TC_KP
+    int* status;
+};
+
+template <bool F16>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams P) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* sA = base;
+    uint8_t* sB = base + TC_A_BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + TC_STAGES * TC_B_BYTES);
+    uint64_t* full = bars;                       // [TC_STAGES]
+    uint64_t* empty = bars + TC_STAGES;          // [TC_STAGES]
+    uint64_t* a_full = bars + 2 * TC_STAGES;     // [1]
+    uint64_t* acc_full = a_full + 1;             // [2]
+    uint64_t* acc_empty = acc_full + 2;          // [2]
+    uint64_t* mma_done = acc_empty + 2;          // [1]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    // per epilogue thread: a queue of candidates that passed the threshold
+    float* q_s = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bars) + 256);
+    int32_t* q_j = reinterpret_cast<int32_t*>(q_s + TC_EPI_WARPS * 32 * TC_QCAP);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t q0 = int64_t(blockIdx.x) * TC_BM;
+    const int T = P.n_tiles;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(a_full, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], TC_EPI_WARPS);
+        }
+        mbar_init(mma_done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(TC_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            mbar_expect_tx(a_full, TC_A_BYTES);
+            tma_load_2d(sA, &tmA, 0, int(q0), a_full);
+            int t = 0;
+            for (; t < T; ++t) {
+                const int s = t % TC_STAGES;
+                if (t >= TC_STAGES && !mbar_wait(&empty[s], ((t / TC_STAGES) & 1) ^ 1, abort_flag, P.status))
+                    break;
+                mbar_expect_tx(&full[s], TC_B_BYTES);
+                tma_load_2d(sB + s * TC_B_BYTES, &tmB, 0, t * TC_BN, &full[s]);
+            }
+            if (t < T) {
+                // aborted: let the loads already issued land before the CTA exits
+                for (int u = (t > TC_STAGES ? t - TC_STAGES : 0); u < t; ++u) {
+                    const unsigned long long t0 = global_timer();
+                    while (!mbar_try(&full[u % TC_STAGES], (u / TC_STAGES) & 1) &&
+                           global_timer() - t0 < 100000000ull) {
+                    }
+                }
+                mbar_try(a_full, 0);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_f16kind(TC_BM, TC_BN, F16);
+            const uint64_t adesc = sdesc_sw128(smem_u32(sA));
+            bool ok = mbar_wait(a_full, 0, abort_flag, P.status);
+            for (int t = 0; ok && t < T; ++t) {
+                const int s = t % TC_STAGES, buf = t & 1, use = t >> 1;
+                if (t >= 2 && !mbar_wait(&acc_empty[buf], (use & 1) ^ 1, abort_flag, P.status)) break;
+                tc_fence_after();
+                if (!mbar_wait(&full[s], (t / TC_STAGES) & 1, abort_flag, P.status)) break;
+                tc_fence_after();
+                const uint64_t bdesc = sdesc_sw128(smem_u32(sB + s * TC_B_BYTES));
+#pragma unroll
+                for (int k = 0; k < TC_K / 16; ++k)  // K step of 16 BF16 = 32 bytes = 2 descriptor units
+                    mma_f16kind(tmem + uint32_t(buf * TC_BN), adesc + 2 * k, bdesc + 2 * k, idesc, k > 0);
+                mma_commit(&empty[s]);
+                mma_commit(&acc_full[buf]);
+            }
+            // every MMA issued above has completed once this barrier fires
+            mma_commit(mma_done);
+            const unsigned long long t0 = global_timer();
+            while (!mbar_try(mma_done, 0) && global_timer() - t0 < 100000000ull) {
+            }
+        }
+    } else {
+        // ---------------- epilogue: warps 2..9
+        const int e = warp - 2;
+        const int quarter = warp & 3;             // TMEM lanes [32 quarter, 32 quarter + 32)
+        const int half = e >> 2;                  // columns [128 half, 128 half + 128) of a tile
+        const int row = quarter * 32 + lane;
+        float L[TC_KP];
+        int32_t I[TC_KP];
+#pragma unroll
+        for (int s = 0; s < TC_KP; ++s) {
+            L[s] = INFINITY;
+            I[s] = -1;
+        }
+        // Candidates below the row's current threshold L[KP-1] are appended to
+        // this thread's queue (slot s at q_*[s * 256 + tid], conflict-free);
+        // when any lane of the warp has 8 or more queued, all lanes merge
+        // their queues into their sorted lists in lockstep, so an insertion
+        // pass serves all 32 rows of the warp at once.
+        const int qb = e * 32 + lane;
+        int qn = 0;
+        auto flush = [&]() {
+            const int qmax = __reduce_max_sync(0xffffffffu, qn);
+            for (int s = 0; s < qmax; ++s) {
+                if (s < qn) {
+                    const float x = q_s[s * (TC_EPI_WARPS * 32) + qb];
+                    if (x < L[TC_KP - 1]) list_insert(L, I, x, q_j[s * (TC_EPI_WARPS * 32) + qb]);
+                }
+            }
+            qn = 0;
+        };
+        for (int t = 0; t < T; ++t) {
+            const int buf = t & 1, use = t >> 1;
+            if (!mbar_wait(&acc_full[buf], use & 1, abort_flag, P.status)) break;
+            tc_fence_after();
+            const uint32_t tbase = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(buf * TC_BN + half * 128);
+            const int32_t j0 = t * TC_BN + half * 128;
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
+                float v[32];
+                __syncwarp();
+                tmem_ld32(tbase + c * 32, v);
+                const float thr = L[TC_KP - 1];
+                float gm[4];
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    gm[g] = fminf(fminf(fminf(v[8 * g], v[8 * g + 1]), fminf(v[8 * g + 2], v[8 * g + 3])),
+                                  fminf(fminf(v[8 * g + 4], v[8 * g + 5]), fminf(v[8 * g + 6], v[8 * g + 7])));
+                }
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    if (__any_sync(0xffffffffu, gm[g] < thr)) {
+                        if (gm[g] < thr) {
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                if (v[8 * g + u] < thr) {
+                                    q_s[qn * (TC_EPI_WARPS * 32) + qb] = v[8 * g + u];
+                                    q_j[qn * (TC_EPI_WARPS * 32) + qb] = j0 + c * 32 + 8 * g + u;
+                                    ++qn;
+                                }
+                            }
+                        }
+                        if (__any_sync(0xffffffffu, qn > TC_QCAP - 8)) flush();
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        }
+        flush();
+        // merge the two column halves of each row through shared memory (the
+        // B ring is idle once the last accumulator has been read)
+        float* ms = reinterpret_cast<float*>(sB);                 // [2][128][TC_KP]
+        int32_t* mi = reinterpret_cast<int32_t*>(sB + 2 * TC_BM * TC_KP * 4);
+        asm volatile("bar.sync 1, %0;" ::"r"(TC_EPI_WARPS * 32) : "memory");
+#pragma unroll
+        for (int s = 0; s < TC_KP; ++s) {
+            ms[(half * TC_BM + row) * TC_KP + s] = L[s];
+            mi[(half * TC_BM + row) * TC_KP + s] = I[s];
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(TC_EPI_WARPS * 32) : "memory");
+        const int64_t g = q0 + row;
+        if (half == 0 && g < P.n && !*abort_flag) {
+            const float* As = ms + row * TC_KP;
+            const int32_t* Ai = mi + row * TC_KP;
+            const float* Bs = ms + (TC_BM + row) * TC_KP;
+            const int32_t* Bi = mi + (TC_BM + row) * TC_KP;
+            int a = 0, b = 0;
+            for (int o = 0; o < TC_KP; ++o) {
+                const bool take_a = (As[a] < Bs[b]) || (As[a] == Bs[b] && uint32_t(Ai[a]) <= uint32_t(Bi[b]));
+                P.cand_s[g * TC_KP + o] = take_a ? As[a] : Bs[b];
+                P.cand_idx[g * TC_KP + o] = take_a ? Ai[a] : Bi[b];
+                if (take_a) ++a; else ++b;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ------------------------------------------------------------------ A3: re-rank + certify
+template <int K, bool F16>
+__global__ void tc_rerank_kernel(const float* __restrict__ X, int64_t n, int d, int k,
+                                 const int32_t* __restrict__ cand_idx, const float* __restrict__ cand_s,
+                                 const float* __restrict__ norm, const float* __restrict__ resid,
+                                 const unsigned int* __restrict__ maxbits, int32_t* __restrict__ idx_out,
+                                 float* __restrict__ dist_out, int32_t* __restrict__ fail_rows,
+                                 int32_t* __restrict__ fail_count) {
+    const float n_max = __uint_as_float(maxbits[0]);
+    const float r_max = __uint_as_float(maxbits[1]);
+    const float S = operand_scale<F16>(maxbits);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        float D[K];
+        int32_t J[K];
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            D[s] = INFINITY;
+            J[s] = INT32_MAX;
+        }
+        int valid = 0;
+        for (int s = 0; s < TC_KP; ++s) {
+            const int32_t j = cand_idx[i * TC_KP + s];
+            if (j < 0 || j >= n || j == i) continue;
+            ++valid;
+            float a = 0.f;
+            for (int c = 0; c < d; ++c) {
+                const float df = X[i * d + c] - X[int64_t(j) * d + c];
+                a = fmaf(df, df, a);
+            }
+            if (a < D[K - 1] || (a == D[K - 1] && j < J[K - 1])) {
+#pragma unroll
+                for (int t = K - 1; t > 0; --t) {
+                    const bool shift = a < D[t - 1] || (a == D[t - 1] && j < J[t - 1]);
+                    const bool place = !shift && (a < D[t] || (a == D[t] && j < J[t]));
+                    D[t] = shift ? D[t - 1] : (place ? a : D[t]);
+                    J[t] = shift ? J[t - 1] : (place ? j : J[t]);
+                }
+                if (a < D[0] || (a == D[0] && j < J[0])) {
+                    D[0] = a;
+                    J[0] = j;
+                }
+            }
+        }
+        // certificate
+        const float s_thr = cand_s[i * TC_KP + TC_KP - 1] * (S * S);
+        const float ni = norm[i];
+        const float eps = 6.103515625e-05f * (ni + n_max);  // 2^-14 (n_i + n_max)
+        const float lb2 = ni + s_thr - eps;
+        const float lb = sqrtf(fmaxf(lb2, 0.f)) - resid[i] - r_max;
+        float dk2 = 0.f;
+#pragma unroll
+        for (int s = 0; s < K; ++s)
+            if (s == k - 1) dk2 = D[s];
+        const float dk = sqrtf(dk2);
+        const bool ok = valid >= k && lb > dk * (1.0f + 3.8e-6f);
+        if (!ok) {
+            const int32_t pos = atomicAdd(fail_count, 1);
+            fail_rows[pos] = int32_t(i);
+        }
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            if (s < k) {
+                idx_out[i * k + s] = J[s];
+                dist_out[i * k + s] = sqrtf(D[s]);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+static int make_map(Ctx* c, CUtensorMap* map, const void* base, int64_t rows, int box_rows, bool f16) {
+    auto fn = encode_fn();
+    if (!fn) return set_error(c, DRGB_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    const cuuint64_t dims[2] = {cuuint64_t(TC_K), cuuint64_t(rows)};
+    const cuuint64_t strides[1] = {cuuint64_t(TC_K * 2)};
+    const cuuint32_t box[2] = {cuuint32_t(TC_K), cuuint32_t(box_rows)};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(c, DRGB_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
+    return DRGB_OK;
+}
+
+bool knn_tc_preferred(int64_t n, int d, int k) { return n >= 4096 && d + 3 <= TC_K && k < TC_KP; }
+
+// partial lists of the exact re-scan of uncertified rows (up to this many bytes)
+static constexpr size_t TC_PART_BYTES = size_t(64) << 20;
+
+static size_t tc_scratch_bytes(int64_t n, int d, int64_t n_pad, int nblk) {
+    return Carve::round(size_t(nblk) * d * 4) + Carve::round(d * 4) + 2 * Carve::round(n_pad * TC_K * 2) +
+           2 * Carve::round(n_pad * 4) + Carve::round(64) + 2 * Carve::round(n_pad * TC_KP * 4) +
+           Carve::round(n * 4) + Carve::round(64) + TC_PART_BYTES + 8192;
+}
+
+template <bool F16>
+static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t* idx_out, float* dist_out,
+                       cudaStream_t st) {
+    if (d + 3 > TC_K || k >= TC_KP)
+        return set_error(c, DRGB_ERR_INVALID, "knn_graph: tensor-core mode needs d <= %d and k < %d", TC_K - 3,
+                         TC_KP);
+    const int64_t n_pad = (n + TC_BN - 1) / TC_BN * TC_BN;
+    const int nblk = 256;
+    int rc = ensure_scratch(c, tc_scratch_bytes(n, d, n_pad, nblk), st);
+    if (rc) return rc;
+    Carve cv(c->scratch);
+    float* partial = cv.take<float>(size_t(nblk) * d);
+    float* mean = cv.take<float>(d);
+    op16* XA = cv.take<op16>(n_pad * TC_K);
+    op16* XB = cv.take<op16>(n_pad * TC_K);
+    float* norm = cv.take<float>(n_pad);
+    float* resid = cv.take<float>(n_pad);
+    unsigned int* maxbits = cv.take<unsigned int>(16);
+    int32_t* cand_idx = cv.take<int32_t>(n_pad * TC_KP);
+    float* cand_s = cv.take<float>(n_pad * TC_KP);
+    int32_t* fail_rows = cv.take<int32_t>(n);
+    int32_t* fail_count = cv.take<int32_t>(16);
+    void* part = cv.take<char>(TC_PART_BYTES);
+
+    DRGB_CUDA(c, cudaMemsetAsync(maxbits, 0, 64, st));
+    DRGB_CUDA(c, cudaMemsetAsync(fail_count, 0, 64, st));
+    tc_colsum_kernel<<<nblk, 64, 0, st>>>(X, n, d, partial);
+    DRGB_CHECK_LAUNCH(c);
+    tc_mean_kernel<<<1, 64, 0, st>>>(partial, nblk, d, n, mean);
+    DRGB_CHECK_LAUNCH(c);
+    if (F16) {
+        tc_absmax_kernel<<<grid_for(n * d, 256, c->num_sms * 8), 256, 0, st>>>(X, n, d, mean, maxbits);
+        DRGB_CHECK_LAUNCH(c);
+    }
+    tc_stage_kernel<F16><<<grid_for(n_pad, 8, c->num_sms * 16), 256, 0, st>>>(X, n, n_pad, d, mean, XA, XB,
+                                                                              norm, resid, maxbits);
+    DRGB_CHECK_LAUNCH(c);
+
+    CUtensorMap mA, mB;
+    if ((rc = make_map(c, &mA, XA, n_pad, TC_BM, F16))) return rc;
+    if ((rc = make_map(c, &mB, XB, n_pad, TC_BN, F16))) return rc;
+    static bool attr_set = false;
+    if (!attr_set) {
+        DRGB_CUDA(c, cudaFuncSetAttribute(knn_tc_kernel<F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          int(TC_SMEM)));
+        attr_set = true;
+    }
+    TcParams P;
+    P.n = n;
+    P.n_tiles = int(n_pad / TC_BN);
+    P.cand_idx = cand_idx;
+    P.cand_s = cand_s;
+    P.status = c->d_status;
+    const int grid = int((n + TC_BM - 1) / TC_BM);
+    knn_tc_kernel<F16><<<grid, TC_THREADS, TC_SMEM, st>>>(mA, mB, P);
+    DRGB_CHECK_LAUNCH(c);
+
+    const int rb = grid_for(n, 128, c->num_sms * 8);
+    if (k <= 16)
+        tc_rerank_kernel<16, F16><<<rb, 128, 0, st>>>(X, n, d, k, cand_idx, cand_s, norm, resid, maxbits, idx_out,
+                                                 dist_out, fail_rows, fail_count);
+    else
+        tc_rerank_kernel<32, F16><<<rb, 128, 0, st>>>(X, n, d, k, cand_idx, cand_s, norm, resid, maxbits, idx_out,
+                                                 dist_out, fail_rows, fail_count);
+    DRGB_CHECK_LAUNCH(c);
+    // exact FP32 scan of the uncertified rows (row list and count on the device)
+    DRGB_CUDA(c, cudaMemcpyAsync(c->d_counter, fail_count, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    rc = launch_knn_exact_rows(c, X, n, d, k, fail_rows, fail_count, n, idx_out, dist_out, st, part,
+                               TC_PART_BYTES);
+    return rc;
+}
+
+int knn_tc(Ctx* c, const float* X, int64_t n, int d, int k, bool f16, int32_t* idx_out, float* dist_out,
+           cudaStream_t st) {
+    return f16 ? knn_tc_impl<true>(c, X, n, d, k, idx_out, dist_out, st)
+               : knn_tc_impl<false>(c, X, n, d, k, idx_out, dist_out, st);
+}
+
+}  // namespace drgb
+
+extern "C" int drgb_knn_uncertified(drgb_ctx* c, int64_t* count, void* stream) {
+    if (!c || !count) return DRGB_ERR_INVALID;
+    int32_t v = 0;
+    DRGB_CUDA(c, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    DRGB_CUDA(c, cudaMemcpy(&v, c->d_counter, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    *count = v;
+    return DRGB_OK;
+}

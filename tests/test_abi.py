@@ -1,0 +1,100 @@
+"""The C ABI library builds, loads and exports every declared entry point;
+host-side behaviour that needs no GPU (not gpu)."""
+import ctypes as C
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from oracle import curve
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2603_04035_gb300 import _lib, build
+    build.build()
+    return _lib.load()
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(drgb_\w+)\s*\(", src))
+    return sorted(n for n in names if n != "drgb_epoch_cb")
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_declares_every_symbol():
+    from paper_2603_04035_gb300 import _lib
+    assert set(declared_symbols()) <= set(_lib.SIGNATURES)
+
+
+def test_version_and_defaults(lib):
+    from paper_2603_04035_gb300 import _lib
+    assert lib.drgb_version() >= 10000
+    p = _lib.Params()
+    assert lib.drgb_default_params(C.byref(p)) == 0
+    assert (p.k, p.n_epochs, p.neg, p.lr0, p.init_range) == (15, 200, 5, 1.0, 10.0)
+    assert lib.drgb_default_params(None) == _lib.ERR_INVALID
+
+
+@pytest.mark.parametrize("spread,min_dist", [(1.0, 0.1), (1.0, 0.5), (2.0, 0.25), (1.0, 0.01)])
+def test_host_find_ab_matches_oracle(lib, spread, min_dist):
+    a, b = C.c_float(), C.c_float()
+    assert lib.drgb_find_ab(spread, min_dist, C.byref(a), C.byref(b)) == 0
+    a_o, b_o = curve.find_ab(spread, np.float32(min_dist).item())
+    assert abs(a.value - a_o) < 1e-5 * a_o and abs(b.value - b_o) < 1e-5 * b_o
+
+
+def test_find_ab_rejects_bad_arguments(lib):
+    from paper_2603_04035_gb300 import _lib
+    a, b = C.c_float(), C.c_float()
+    assert lib.drgb_find_ab(0.0, 0.1, C.byref(a), C.byref(b)) == _lib.ERR_INVALID
+    assert lib.drgb_find_ab(1.0, -0.1, C.byref(a), C.byref(b)) == _lib.ERR_INVALID
+    assert lib.drgb_find_ab(1.0, 0.1, None, C.byref(b)) == _lib.ERR_INVALID
+
+
+def test_null_context_is_rejected_without_touching_a_gpu(lib):
+    from paper_2603_04035_gb300 import _lib
+    E = _lib.ERR_INVALID
+    assert lib.drgb_knn_graph(None, None, 10, 2, 3, 0, None, None, None) == E
+    assert lib.drgb_fuzzy_weights(None, None, None, 10, 3, 10, None, None, None, None, 60, None,
+                                  None, None) == E
+    assert lib.drgb_embed_epoch(None, None, None, None, None, None, 10, 1.0, 1.0, 1.0, 5, 0, 0,
+                                None) == E
+    assert lib.drgb_embed_epochs(None, None, None, None, None, None, 10, 1.0, 1.0, 1.0, 5, 0, 1, 1,
+                                 0, None) == E
+    assert lib.drgb_init_embedding(None, 10, 10.0, 0, None, None) == E
+    assert lib.drgb_fit_transform(None, None, 10, 2, None, None, _lib.EPOCH_CB(), None, None) == E
+    assert lib.drgb_sync(None, None) == E
+    assert lib.drgb_ctx_create(0, None) == E
+    assert lib.drgb_ctx_destroy(None) == 0
+    assert lib.drgb_last_error(None) == b"null context"
+
+
+@pytest.mark.skipif(os.path.exists("/dev/nvidia0"), reason="host has a GPU")
+def test_ctx_create_without_gpu_reports_device_error(lib):
+    from paper_2603_04035_gb300 import _lib
+    h = C.c_void_p()
+    assert lib.drgb_ctx_create(0, C.byref(h)) == _lib.ERR_DEVICE
+    assert h.value is None
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2603_04035_gb300")
+    for path in glob.glob(os.path.join(pkg, "**", "*.*"), recursive=True):
+        if path.endswith((".py", ".cu", ".cuh", ".h")):
+            text = open(path).read()
+            assert "oracle" not in re.sub(r"#.*|//.*", "", text).replace("oracle.", ""), path
+            assert "import oracle" not in text and "from oracle" not in text, path

@@ -1,7 +1,6 @@
 """Pins for the oracle's a,b fit, initialisation and SGD epoch (not gpu)."""
 import numpy as np
 import pytest
-import sympy
 from scipy.optimize import curve_fit
 
 import datagen
@@ -92,6 +91,7 @@ def test_epoch_force_matches_central_differences():
 
 
 def test_coefficients_equal_symbolic_gradient():
+    sympy = pytest.importorskip("sympy")
     a, b = sympy.Rational(1577, 1000), sympy.Rational(895, 1000)
     x, y = sympy.symbols("x y", real=True)
     d = x ** 2 + y ** 2  # Y_i - Y_j = (x, y)

@@ -3,7 +3,6 @@ import itertools
 
 import numpy as np
 import pytest
-from sklearn.neighbors import NearestNeighbors
 
 import datagen
 from oracle import knn as oknn
@@ -32,6 +31,7 @@ def test_matches_python_loops_tiny():
 
 @pytest.mark.parametrize("n,d,k", [(500, 50, 15), (1200, 3, 15), (300, 100, 7)])
 def test_matches_sklearn_brute(n, d, k):
+    NearestNeighbors = pytest.importorskip("sklearn.neighbors").NearestNeighbors
     X, _ = datagen.mixture(n, d, 10, seed=n)
     idx, dist = oknn.knn(X, k)
     nn = NearestNeighbors(n_neighbors=k + 1, algorithm="brute").fit(X.astype(np.float64))

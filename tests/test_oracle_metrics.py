@@ -1,7 +1,6 @@
 """Pins for the oracle's quality metrics (not gpu)."""
 import numpy as np
 import pytest
-from sklearn.manifold import trustworthiness as sk_trust
 
 import datagen
 from oracle import knn as oknn, metrics
@@ -9,6 +8,7 @@ from oracle import knn as oknn, metrics
 
 @pytest.mark.parametrize("k", [5, 15])
 def test_trustworthiness_matches_sklearn(k):
+    sk_trust = pytest.importorskip("sklearn.manifold").trustworthiness
     X, _ = datagen.mixture(400, 20, 4, seed=1)
     Y = np.random.default_rng(2).normal(size=(400, 2)) + X[:, :2]
     ny = metrics.knn_2d(Y, k)
