@@ -159,6 +159,31 @@ int drgb_fuzzy_weights(drgb_ctx* ctx, const int32_t* idx, const float* dist, int
                        int32_t k, int32_t n_epochs, int32_t* row_ptr, int32_t* col, float* w,
                        uint32_t* q, int64_t cap, float* rho, float* sigma, void* stream);
 
+/* Allocation-free variant of drgb_fuzzy_weights (the paper has no
+ * counterpart).  For callers that cannot allocate device memory at all, for
+ * example code that runs under an external memory manager which owns every
+ * byte of the device, or in a setting where cudaMalloc is forbidden: it takes
+ * no context and calls no cudaMalloc, cudaFree or allocating library routine.
+ * Its scratch is a file-scope device array of DRGB_STATIC_SCRATCH_BYTES that
+ * every GPU which loads the library holds until the process exits; inputs and
+ * outputs are the caller's, exactly as for drgb_fuzzy_weights, and the result
+ * is identical to it.
+ *   - Sizes whose scratch would not fit the array (about 36 n k + 20 n bytes;
+ *     n k up to roughly 440 000, e.g. n = 29 000 at k = 15) are rejected
+ *     with DRGB_ERR_WORKSPACE before anything is enqueued.
+ *   - The first call on each device, with that device current, looks up the
+ *     array's device address (cudaGetSymbolAddress); make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array, which keeps the previous call's
+ *     contents (each call clears what must start at zero): calls that overlap
+ *     on the GPU, from two streams or two host threads, race.
+ *   - Synchronous: returns after `stream` has finished the work, with
+ *     DRGB_ERR_INVALID if the neighbour lists were malformed. */
+#define DRGB_STATIC_SCRATCH_BYTES (16u << 20)
+int drgb_fuzzy_weights_static(const int32_t* idx, const float* dist, int64_t n, int32_t k,
+                              int32_t n_epochs, int32_t* row_ptr, int32_t* col, float* w,
+                              uint32_t* q, int64_t cap, float* rho, float* sigma, void* stream);
+
 /* ------------------------------------------------------------- a, b fit */
 
 /* Host, synchronous.  Least-squares fit of Phi(x) = 1 / (1 + a x^(2b)) to

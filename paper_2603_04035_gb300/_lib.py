@@ -18,6 +18,7 @@ ERR_TIMEOUT = -4
 ERR_NONFINITE = -5
 ERR_DEVICE = -6
 MAX_K = 32
+STATIC_SCRATCH_BYTES = 16 << 20
 TUNE_EPOCH_ROWS = 1
 
 ERROR_NAMES = {ERR_INVALID: "invalid argument", ERR_WORKSPACE: "workspace too small",
@@ -50,6 +51,7 @@ SIGNATURES = {
     "drgb_knn_graph": (C.c_int, [vp, vp, i64, i32, i32, i32, vp, vp, vp]),
     "drgb_knn_uncertified": (C.c_int, [vp, C.POINTER(C.c_int64), vp]),
     "drgb_fuzzy_weights": (C.c_int, [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, i64, vp, vp, vp]),
+    "drgb_fuzzy_weights_static": (C.c_int, [vp, vp, i64, i32, i32, vp, vp, vp, vp, i64, vp, vp, vp]),
     "drgb_find_ab": (C.c_int, [f32, f32, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "drgb_init_embedding": (C.c_int, [vp, i64, f32, u64, vp, vp]),
     "drgb_embed_epoch": (C.c_int, [vp, vp, vp, vp, vp, vp, i64, f32, f32, f32, i32, i32, u64, vp]),

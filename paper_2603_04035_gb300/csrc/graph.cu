@@ -14,6 +14,8 @@
 //   7 count     entries kept (T q >= 2^24)
 //   8 scan      row_ptr
 //   9 fill      col, w, q
+#include <mutex>
+
 #include "common.cuh"
 #include "graph.cuh"
 
@@ -314,4 +316,67 @@ extern "C" int drgb_fuzzy_weights(drgb_ctx* c, const int32_t* idx, const float* 
     if (rc) return rc;
     return build_fuzzy_graph(c, idx, dist, n, k, n_epochs, row_ptr, col, w, q, rho, sigma,
                              c->scratch, st);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant.  Its scratch is this file-scope device array: every
+// device that loads the library reserves it for the life of the process.  The
+// first 256 bytes hold the device status word, the rest is carved exactly as
+// the context scratch of drgb_fuzzy_weights.
+static __device__ __align__(256) unsigned char g_fuzzy_static_scratch[DRGB_STATIC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+void* g_static_ptr[kMaxDevices] = {};
+int g_static_sms[kMaxDevices] = {};
+}  // namespace
+
+extern "C" int drgb_fuzzy_weights_static(const int32_t* idx, const float* dist, int64_t n, int32_t k,
+                                         int32_t n_epochs, int32_t* row_ptr, int32_t* col, float* w,
+                                         uint32_t* q, int64_t cap, float* rho, float* sigma,
+                                         void* stream) {
+    if (!idx || !dist || !row_ptr || !col || !w || !q) return DRGB_ERR_INVALID;
+    if (k < 1 || k > DRGB_MAX_K || n < k + 1 || n > (INT32_MAX / 2) / k || n_epochs < 1) return DRGB_ERR_INVALID;
+    if (cap < 2 * n * k) return DRGB_ERR_WORKSPACE;
+    if (256 + fuzzy_scratch_bytes(n, k) > size_t(DRGB_STATIC_SCRATCH_BYTES)) return DRGB_ERR_WORKSPACE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DRGB_ERR_DEVICE;
+    void* base = nullptr;
+    int sms = 0;
+    {
+        // one-time set-up per device, with that device current: look up the
+        // device address of the array (the host-side symbol is only a handle)
+        std::lock_guard<std::mutex> lock(g_static_mutex);
+        if (!g_static_ptr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_fuzzy_static_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return DRGB_ERR_CUDA;
+            }
+            int count = 0;
+            if (cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+                cudaGetLastError();
+                return DRGB_ERR_CUDA;
+            }
+            g_static_ptr[dev] = p;
+            g_static_sms[dev] = count;
+        }
+        base = g_static_ptr[dev];
+        sms = g_static_sms[dev];
+    }
+    // a stack context: no device memory of its own, status word in the array
+    Ctx c;
+    c.device = dev;
+    c.num_sms = sms;
+    c.d_status = static_cast<int*>(base);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(c.d_status, 0, sizeof(int), st) != cudaSuccess) return DRGB_ERR_CUDA;
+    int rc = build_fuzzy_graph(&c, idx, dist, n, k, n_epochs, row_ptr, col, w, q, rho, sigma,
+                               static_cast<unsigned char*>(base) + 256, st);
+    if (rc) return rc;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return DRGB_ERR_CUDA;
+    int status = 0;
+    if (cudaMemcpy(&status, c.d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DRGB_ERR_CUDA;
+    return status ? status : DRGB_OK;
 }
