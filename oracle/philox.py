@@ -10,8 +10,8 @@ that the round structure can be checked against numpy's Philox bit generator.
 
 How the method consumes it:
 
-* negative sample j' of CSR entry e at epoch t (BASELINE north star, "Philox
-  stream keyed by (seed, epoch, edge, j)"): key = (seed lo, seed hi), counter
+* negative sample j' of CSR entry e at epoch t (a stream keyed by seed,
+  epoch, edge and sample number): key = (seed lo, seed hi), counter
   = (e, t, j' // 4, 0), word j' % 4 -> u; the sampled point is (u * n) >> 32.
 * initial coordinates of point i: key = (seed lo, seed hi), counter =
   (i, 0, 0, 1); words 0 and 1 give x and y.
