@@ -61,8 +61,12 @@ typedef struct drgb_params {
     uint64_t seed_init;   /* Philox key of the initialisation */
     uint64_t seed_neg;    /* Philox key of the negative samples */
     int32_t knn_mode;     /* 0 auto, 1 exact FP32 scan, 2 BF16 / 3 FP16 tensor-core + FP32 re-rank */
-    int32_t reserved;
+    int32_t flags;        /* DRGB_FLAG_* bits */
 } drgb_params;
+
+/* drgb_params.flags: time the epoch schedules on the actual graph before the
+ * loop and keep the fastest (results are identical for every schedule). */
+#define DRGB_FLAG_AUTOTUNE 1
 
 /* Called after each epoch by fit_transform (Section 2.1, epoch_callback).
  * Y_dev is the current device embedding (n x 2, valid during the call only);
@@ -96,9 +100,15 @@ int64_t drgb_ctx_scratch_bytes(const drgb_ctx* ctx);
 int64_t drgb_launch_count(const drgb_ctx* ctx);
 
 /* Tuning knobs (performance only; results do not depend on them):
- *   DRGB_TUNE_EPOCH_ROWS  rows per warp block of the epoch kernel: 4, 8, 16, 31
- * Returns DRGB_ERR_INVALID for an unknown parameter or value. */
+ *   DRGB_TUNE_EPOCH_ROWS      rows per warp block of the epoch kernel: 4, 8, 16, 31
+ *   DRGB_TUNE_EPOCH_PREFETCH  q chunks (32 entries each) loaded per scan step: 4, 8, 16
+ *   DRGB_TUNE_EPOCH_DYNAMIC   1: row blocks handed out by an atomic counter; 0: static
+ * Supported (rows, prefetch) pairs: (4,4) (4,8) (8,4) (8,8) (8,16) (16,4)
+ * (16,8) (16,16) (31,16).  Returns DRGB_ERR_INVALID for an unknown parameter
+ * or value; an unsupported pair is reported by the next epoch launch. */
 #define DRGB_TUNE_EPOCH_ROWS 1
+#define DRGB_TUNE_EPOCH_PREFETCH 2
+#define DRGB_TUNE_EPOCH_DYNAMIC 3
 int drgb_set_tuning(drgb_ctx* ctx, int32_t param, int32_t value);
 
 /* Stage timing of drgb_fit_transform.  When enabled (on != 0), each fit
@@ -245,6 +255,35 @@ int drgb_embed_epochs(drgb_ctx* ctx, float* Y, float* Y_tmp, const int32_t* row_
 int drgb_fit_transform(drgb_ctx* ctx, const float* X, int64_t n, int32_t d,
                        const drgb_params* p, float* Y_out, drgb_epoch_cb cb, void* user,
                        void* stream);
+
+/* Batched form (a project addition; the paper embeds one data set at a
+ * time): `count` independent instances embedded together.  Instance b is rows
+ * offsets[b] .. offsets[b+1]-1 of X_cat ((sum n_b) x d FP32, device, 4-byte
+ * aligned) and of Y_cat ((sum n_b) x 2 FP32, device).  `offsets` is a HOST
+ * array of count + 1 int64 with offsets[0] = 0; seeds_init / seeds_neg are
+ * optional HOST arrays of per-instance Philox keys (NULL: every instance uses
+ * p->seed_init / p->seed_neg).  Each instance's k-NN graph is computed on its
+ * own rows, the fuzzy graph of all instances is built in one pass, and each
+ * of the p->n_epochs epochs is one launch over all rows (the loop is one
+ * captured CUDA graph).  Instance b's result is bit-identical to
+ * drgb_fit_transform of its rows alone with the same parameters and seeds.
+ * Synchronous.  Errors: DRGB_ERR_INVALID (an instance with fewer than k + 1
+ * rows, bad offsets or parameters), plus those of drgb_fit_transform. */
+int drgb_fit_transform_batched(drgb_ctx* ctx, const float* X_cat, const int64_t* offsets,
+                               int32_t count, int32_t d, const drgb_params* p,
+                               const uint64_t* seeds_init, const uint64_t* seeds_neg, float* Y_cat,
+                               void* stream);
+
+/* Epoch-schedule autotuner: times every supported (rows per block, q
+ * prefetch, scheduling) choice for `trials` epochs of the given graph on a
+ * scratch copy of Y (n x 2, device; not modified), keeps the fastest in the
+ * context (see drgb_set_tuning) and returns it in choice[0..2] (rows,
+ * prefetch, dynamic) with its time per epoch.  Every choice gives
+ * bit-identical results.  Synchronous. */
+int drgb_autotune_epoch(drgb_ctx* ctx, const float* Y, const int32_t* row_ptr, const int32_t* col,
+                        const uint32_t* q, int64_t n, float a, float b, int32_t neg, int32_t n_epochs,
+                        uint64_t seed, int32_t trials, int32_t* choice, float* us_per_epoch,
+                        void* stream);
 
 /* Fill *p with the defaults (k 15, 200 epochs, neg 5, lr0 1, min_dist 0.1,
  * spread 1, init_range 10, seeds 1 and 2, knn_mode auto). */

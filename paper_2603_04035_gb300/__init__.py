@@ -33,7 +33,8 @@ from ._lib import MAX_K, Params  # noqa: F401
 __all__ = ["DrgbError", "Graph", "UMAP", "knn_graph", "fuzzy_weights", "find_ab",
            "init_embedding", "embed_epoch", "embed_epochs", "fit_transform", "eval_recall",
            "eval_trust", "default_params", "context", "knn_uncertified", "launch_count",
-           "set_profiling", "stage_times", "set_tuning"]
+           "set_profiling", "stage_times", "set_tuning", "fit_transform_batched",
+           "autotune_epoch"]
 
 
 class DrgbError(RuntimeError):
@@ -117,7 +118,7 @@ class Graph:
 def default_params() -> dict:
     p = Params()
     _lib.load().drgb_default_params(C.byref(p))
-    return {f: getattr(p, f) for f, _ in Params._fields_ if f != "reserved"}
+    return {f: getattr(p, f) for f, _ in Params._fields_}
 
 
 def launch_count(device=None) -> int:
@@ -267,6 +268,40 @@ def fit_transform(X: torch.Tensor, epoch_callback=None, out: torch.Tensor | None
     _check(_lib.load().drgb_fit_transform(ctx, _ptr(X), n, d, C.byref(p), _ptr(Y), cb, None,
                                           _stream(X.device)), ctx)
     return Y
+
+
+def fit_transform_batched(X_cat: torch.Tensor, offsets, seeds_init=None, seeds_neg=None,
+                          autotune: bool = False, out: torch.Tensor | None = None, **params) -> torch.Tensor:
+    """Embed many instances at once: rows offsets[b]:offsets[b+1] of X_cat are
+    instance b.  Each instance's result equals fit_transform of its rows alone
+    with seeds (seeds_init[b], seeds_neg[b]).  Synchronous."""
+    X_cat = _cuda(X_cat, torch.float32, "X_cat", 2)
+    off = [int(v) for v in offsets]
+    count = len(off) - 1
+    p = _params(**params)
+    if autotune:
+        p.flags |= _lib.FLAG_AUTOTUNE
+    Y = torch.empty((X_cat.shape[0], 2), dtype=torch.float32, device=X_cat.device) if out is None else out
+    off_arr = (C.c_int64 * (count + 1))(*off)
+    si = (C.c_uint64 * count)(*[int(v) for v in seeds_init]) if seeds_init is not None else None
+    sn = (C.c_uint64 * count)(*[int(v) for v in seeds_neg]) if seeds_neg is not None else None
+    ctx = context(X_cat.device.index)
+    _check(_lib.load().drgb_fit_transform_batched(ctx, _ptr(X_cat), off_arr, count, X_cat.shape[1], C.byref(p),
+                                                  si, sn, _ptr(Y), _stream(X_cat.device)), ctx)
+    return Y
+
+
+def autotune_epoch(Y: torch.Tensor, g: Graph, a: float, b: float, neg: int = 5, n_epochs: int = 200,
+                   seed: int = 2, trials: int = 3):
+    """Time the epoch schedules on this graph; keeps and returns the fastest
+    ((rows, prefetch, dynamic), microseconds per epoch)."""
+    Y = _cuda(Y, torch.float32, "Y", 2)
+    choice = (C.c_int32 * 3)()
+    us = C.c_float()
+    ctx = context(Y.device.index)
+    _check(_lib.load().drgb_autotune_epoch(ctx, _ptr(Y), *_graph_args(g), Y.shape[0], a, b, neg, n_epochs, seed,
+                                           trials, choice, C.byref(us), _stream(Y.device)), ctx)
+    return (choice[0], choice[1], choice[2]), us.value
 
 
 # ---------------------------------------------------------------- metrics

@@ -20,6 +20,9 @@ ERR_DEVICE = -6
 MAX_K = 32
 STATIC_SCRATCH_BYTES = 16 << 20
 TUNE_EPOCH_ROWS = 1
+TUNE_EPOCH_PREFETCH = 2
+TUNE_EPOCH_DYNAMIC = 3
+FLAG_AUTOTUNE = 1
 
 ERROR_NAMES = {ERR_INVALID: "invalid argument", ERR_WORKSPACE: "workspace too small",
                ERR_CUDA: "CUDA error", ERR_TIMEOUT: "device timeout",
@@ -30,7 +33,7 @@ class Params(C.Structure):
     _fields_ = [("k", C.c_int32), ("n_epochs", C.c_int32), ("neg", C.c_int32),
                 ("lr0", C.c_float), ("min_dist", C.c_float), ("spread", C.c_float),
                 ("init_range", C.c_float), ("seed_init", C.c_uint64), ("seed_neg", C.c_uint64),
-                ("knn_mode", C.c_int32), ("reserved", C.c_int32)]
+                ("knn_mode", C.c_int32), ("flags", C.c_int32)]
 
 
 EPOCH_CB = C.CFUNCTYPE(C.c_int, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p)
@@ -59,6 +62,10 @@ SIGNATURES = {
                                     u64, vp]),
     "drgb_fit_transform": (C.c_int, [vp, vp, i64, i32, C.POINTER(Params), vp, EPOCH_CB, vp, vp]),
     "drgb_default_params": (C.c_int, [C.POINTER(Params)]),
+    "drgb_fit_transform_batched": (C.c_int, [vp, vp, C.POINTER(C.c_int64), i32, i32, C.POINTER(Params),
+                                             C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), vp, vp]),
+    "drgb_autotune_epoch": (C.c_int, [vp, vp, vp, vp, vp, i64, f32, f32, i32, i32, u64, i32,
+                                      C.POINTER(C.c_int32), C.POINTER(C.c_float), vp]),
     "drgb_eval_recall": (C.c_int, [vp, vp, vp, i64, i32, i32, i64, C.POINTER(C.c_double), vp]),
     "drgb_eval_trust": (C.c_int, [vp, vp, vp, i64, i32, i32, i64, C.POINTER(C.c_double), vp]),
 }

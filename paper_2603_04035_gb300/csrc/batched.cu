@@ -1,0 +1,231 @@
+// Batched form: many independent instances of uneven size embedded together.
+// The concatenated instances form one block-diagonal problem: each instance's
+// k-NN graph is computed separately (rows of one instance only see that
+// instance), its indices are made global, the fuzzy graph of the whole
+// concatenation is built at once (its rows never cross instances), and every
+// epoch runs as one launch over all rows with instance-local entry numbers,
+// negative ranges and Philox keys.  Every arithmetic step of a row is the one a
+// single-instance fit performs, so each instance's embedding is bit-identical
+// to fitting it alone with the same seeds.  The epoch loop of all instances is
+// one captured CUDA graph.
+//
+// Also here: the epoch schedule autotuner, which times every supported
+// (rows per block, q prefetch, scheduling) choice on the actual graph; all of
+// them give bit-identical results, so it changes speed only.
+#include <vector>
+
+#include "common.cuh"
+#include "epoch.cuh"
+#include "graph.cuh"
+#include "knn.cuh"
+
+namespace drgb {
+
+__global__ void globalize_idx_kernel(int32_t* __restrict__ idx, int64_t n_total, int k, int count,
+                                     const int64_t* __restrict__ inst_off) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n_total;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        int lo = 0, hi = count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (inst_off[mid] <= i) lo = mid; else hi = mid - 1;
+        }
+        const int32_t off = int32_t(inst_off[lo]);
+        for (int s = 0; s < k; ++s) idx[i * k + s] += off;
+    }
+}
+
+struct Choice {
+    int rows, pf, dyn;
+};
+static const Choice kChoices[] = {{4, 4, 1},  {4, 8, 1},  {8, 4, 1},  {8, 8, 1},  {8, 16, 1},
+                                  {16, 4, 1}, {16, 8, 1}, {16, 16, 1}, {4, 8, 0}, {8, 8, 0},
+                                  {16, 8, 0}, {16, 16, 0}, {31, 16, 0}};
+
+// Time `trials` epochs per choice (starting at epoch t0 of a T-epoch schedule)
+// on a scratch copy of Y; keep the fastest choice in the context.
+int autotune_epoch(Ctx* c, const float2* Y, float2* Ya, float2* Yb, const int32_t* rp, const int32_t* col,
+                   const uint32_t* q, int64_t n, float a, float b, int neg, int T, uint64_t seed, int trials,
+                   cudaStream_t st, int count, const int64_t* inst_off, const uint64_t* inst_seed,
+                   float* best_us) {
+    cudaEvent_t e0, e1;
+    DRGB_CUDA(c, cudaEventCreate(&e0));
+    DRGB_CUDA(c, cudaEventCreate(&e1));
+    float best = 1e30f;
+    Choice keep{c->epoch_rows, c->epoch_prefetch, c->epoch_dynamic};
+    int rc = DRGB_OK;
+    for (const Choice& ch : kChoices) {
+        c->epoch_rows = ch.rows;
+        c->epoch_prefetch = ch.pf;
+        c->epoch_dynamic = ch.dyn;
+        EpochArgs A;
+        A.row_ptr = rp;
+        A.col = col;
+        A.q = q;
+        A.n = n;
+        A.a = a;
+        A.b = b;
+        A.neg = neg;
+        A.k0 = uint32_t(seed);
+        A.k1 = uint32_t(seed >> 32);
+        A.status = c->d_status;
+        A.work = c->d_work;
+        A.count = count;
+        A.inst_off = inst_off;
+        A.inst_seed = inst_seed;
+        if (cudaMemcpyAsync(Ya, Y, size_t(n) * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+            rc = set_error(c, DRGB_ERR_CUDA, "autotune: copy failed");
+            break;
+        }
+        for (int r = 0; r <= trials && rc == DRGB_OK; ++r) {  // first launch warms up
+            if (r == 1) cudaEventRecord(e0, st);
+            A.Y_in = (r & 1) ? Yb : Ya;
+            A.Y_out = (r & 1) ? Ya : Yb;
+            A.t = uint32_t(r % T);
+            A.lr = 1.0f;
+            rc = launch_epoch(c, A, 0, st);
+        }
+        if (rc) break;
+        cudaEventRecord(e1, st);
+        DRGB_CUDA(c, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const float us = ms * 1000.f / float(trials);
+        if (us < best) {
+            best = us;
+            keep = ch;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->epoch_rows = keep.rows;
+    c->epoch_prefetch = keep.pf;
+    c->epoch_dynamic = keep.dyn;
+    if (best_us) *best_us = best;
+    return rc;
+}
+
+}  // namespace drgb
+
+using namespace drgb;
+
+extern "C" {
+
+int drgb_fit_transform_batched(drgb_ctx* c, const float* X_cat, const int64_t* offsets, int32_t count,
+                               int32_t d, const drgb_params* p, const uint64_t* seeds_init,
+                               const uint64_t* seeds_neg, float* Y_cat, void* stream) {
+    if (!c) return DRGB_ERR_INVALID;
+    if (!X_cat || !offsets || !p || !Y_cat || count < 1)
+        return set_error(c, DRGB_ERR_INVALID, "fit_transform_batched: NULL pointer or count < 1");
+    const int k = p->k;
+    if (k < 1 || k > DRGB_MAX_K || d < 1 || p->n_epochs < 1 || p->neg < 0 || p->neg > 64 ||
+        !(p->init_range > 0.f) || p->knn_mode < 0 || p->knn_mode > 3 || !aligned(Y_cat, 8) ||
+        !aligned(X_cat, 4))
+        return set_error(c, DRGB_ERR_INVALID, "fit_transform_batched: bad parameters");
+    if (offsets[0] != 0) return set_error(c, DRGB_ERR_INVALID, "fit_transform_batched: offsets[0] != 0");
+    int64_t max_n = 0;
+    for (int b = 0; b < count; ++b) {
+        const int64_t nb = offsets[b + 1] - offsets[b];
+        if (nb < int64_t(k) + 1)
+            return set_error(c, DRGB_ERR_INVALID, "fit_transform_batched: instance %d has %lld < k + 1 rows", b,
+                             (long long)nb);
+        max_n = nb > max_n ? nb : max_n;
+    }
+    const int64_t N = offsets[count];
+    if (N > (INT32_MAX / 2) / k) return set_error(c, DRGB_ERR_INVALID, "fit_transform_batched: too many rows");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    // scratch: per-row buffers of the concatenation, then the k-NN region for
+    // the largest instance
+    size_t knn_bytes = 0;
+    for (int b = 0; b < count; ++b) {
+        const size_t kb = knn_scratch_bytes(offsets[b + 1] - offsets[b], d, k, p->knn_mode);
+        knn_bytes = kb > knn_bytes ? kb : knn_bytes;
+    }
+    const size_t Nk = size_t(N) * k;
+    const size_t main_bytes = Carve::round(Nk * 4) * 2 + Carve::round((N + 1) * 4) + Carve::round(2 * Nk * 4) * 3 +
+                              Carve::round(N * 8) * 2 + Carve::round((count + 1) * 8) + 2 * Carve::round(count * 8) +
+                              Carve::round(fuzzy_scratch_bytes(N, k)) + 8192;
+    int rc = ensure_scratch(c, Carve::round(main_bytes) + knn_bytes, st);
+    if (rc) return rc;
+    Carve cv(c->scratch);
+    int32_t* idx = cv.take<int32_t>(Nk);
+    float* dist = cv.take<float>(Nk);
+    int32_t* row_ptr = cv.take<int32_t>(N + 1);
+    int32_t* col = cv.take<int32_t>(2 * Nk);
+    float* w = cv.take<float>(2 * Nk);
+    uint32_t* q = cv.take<uint32_t>(2 * Nk);
+    float2* Y_tmp = cv.take<float2>(N);
+    float2* Y_tune = cv.take<float2>(N);
+    int64_t* d_off = cv.take<int64_t>(count + 1);
+    uint64_t* d_seed_init = cv.take<uint64_t>(count);
+    uint64_t* d_seed_neg = cv.take<uint64_t>(count);
+    void* fz = cv.take<char>(fuzzy_scratch_bytes(N, k));
+    void* knn_scratch = static_cast<char*>(c->scratch) + Carve::round(main_bytes);
+
+    std::vector<uint64_t> si(count), sn(count);
+    for (int b = 0; b < count; ++b) {
+        si[b] = seeds_init ? seeds_init[b] : p->seed_init;
+        sn[b] = seeds_neg ? seeds_neg[b] : p->seed_neg;
+    }
+    DRGB_CUDA(c, cudaMemcpyAsync(d_off, offsets, (count + 1) * 8, cudaMemcpyHostToDevice, st));
+    DRGB_CUDA(c, cudaMemcpyAsync(d_seed_init, si.data(), count * 8, cudaMemcpyHostToDevice, st));
+    DRGB_CUDA(c, cudaMemcpyAsync(d_seed_neg, sn.data(), count * 8, cudaMemcpyHostToDevice, st));
+
+    float a = 0.f, bb = 0.f;
+    if ((rc = drgb_find_ab(p->spread, p->min_dist, &a, &bb))) return set_error(c, rc, "bad spread/min_dist");
+    c->stage_marks = 0;
+    if ((rc = launch_nonfinite_scan(c, X_cat, N * d, st))) return rc;
+    if ((rc = stage_mark(c, 0, st))) return rc;
+    for (int b = 0; b < count; ++b) {
+        const int64_t off = offsets[b], nb = offsets[b + 1] - off;
+        rc = knn_run(c, X_cat + off * d, nb, d, k, p->knn_mode, idx + off * k, dist + off * k, st, knn_scratch);
+        if (rc) return rc;
+    }
+    globalize_idx_kernel<<<grid_for(N, 256, c->num_sms * 8), 256, 0, st>>>(idx, N, k, count, d_off);
+    DRGB_CHECK_LAUNCH(c);
+    if ((rc = stage_mark(c, 1, st))) return rc;
+    rc = build_fuzzy_graph(c, idx, dist, N, k, p->n_epochs, row_ptr, col, w, q, nullptr, nullptr, fz, st);
+    if (rc) return rc;
+    if ((rc = stage_mark(c, 2, st))) return rc;
+    float2* Y = reinterpret_cast<float2*>(Y_cat);
+    if ((rc = launch_init_batched(c, Y, N, p->init_range, count, d_off, d_seed_init, st))) return rc;
+    if (p->flags & DRGB_FLAG_AUTOTUNE) {
+        float us = 0.f;
+        rc = autotune_epoch(c, Y, Y_tune, Y_tmp, row_ptr, col, q, N, a, bb, p->neg, p->n_epochs, 0, 3, st, count,
+                            d_off, d_seed_neg, &us);
+        if (rc) return rc;
+    }
+    if ((rc = stage_mark(c, 3, st))) return rc;
+    rc = run_epochs(c, Y, Y_tmp, row_ptr, col, q, N, a, bb, p->lr0, p->neg, 0, p->n_epochs, p->n_epochs, 0, 0, st,
+                    count, d_off, d_seed_neg);
+    if (rc) return rc;
+    if ((rc = stage_mark(c, 4, st))) return rc;
+    return drgb_sync(c, stream);
+}
+
+int drgb_autotune_epoch(drgb_ctx* c, const float* Y, const int32_t* row_ptr, const int32_t* col,
+                        const uint32_t* q, int64_t n, float a, float b, int32_t neg, int32_t n_epochs,
+                        uint64_t seed, int32_t trials, int32_t* choice, float* us_per_epoch, void* stream) {
+    if (!c) return DRGB_ERR_INVALID;
+    if (!Y || !row_ptr || !col || !q || n < 1 || n > INT32_MAX || neg < 0 || neg > 64 || n_epochs < 1 ||
+        trials < 1 || !aligned(Y, 8))
+        return set_error(c, DRGB_ERR_INVALID, "autotune_epoch: bad arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = ensure_scratch(c, 2 * Carve::round(size_t(n) * 8), st);
+    if (rc) return rc;
+    Carve cv(c->scratch);
+    float2* Ya = cv.take<float2>(n);
+    float2* Yb = cv.take<float2>(n);
+    rc = autotune_epoch(c, reinterpret_cast<const float2*>(Y), Ya, Yb, row_ptr, col, q, n, a, b, neg, n_epochs, seed,
+                        trials, st, 0, nullptr, nullptr, us_per_epoch);
+    if (rc) return rc;
+    if (choice) {
+        choice[0] = c->epoch_rows;
+        choice[1] = c->epoch_prefetch;
+        choice[2] = c->epoch_dynamic;
+    }
+    return drgb_sync(c, stream);
+}
+
+}  // extern "C"

@@ -24,7 +24,9 @@ struct Ctx {
     unsigned long long* d_counter = nullptr;  // diagnostic counter (uncertified rows)
     unsigned int* d_work = nullptr;           // epoch work counters (self-resetting)
     int64_t launches = 0;         // kernels launched (host-side count)
-    int epoch_rows = 8;           // rows per warp block of the epoch kernel (tuning)
+    int epoch_rows = 4;           // rows per warp block of the epoch kernel (tuning)
+    int epoch_prefetch = 8;       // q chunks loaded per scan step (tuning)
+    int epoch_dynamic = 1;        // dynamic (1) or static (0) row-block assignment (tuning)
     int knn_tile_n = 256;         // database tile width of the tensor-core k-NN (tuning)
     bool profiling = false;       // record stage events in fit_transform
     cudaEvent_t stage_ev[8] = {};

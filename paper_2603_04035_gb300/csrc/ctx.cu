@@ -213,6 +213,14 @@ int drgb_set_tuning(drgb_ctx* c, int32_t param, int32_t value) {
                 return set_error(c, DRGB_ERR_INVALID, "epoch rows must be 4, 8, 16 or 31");
             c->epoch_rows = value;
             return DRGB_OK;
+        case DRGB_TUNE_EPOCH_PREFETCH:
+            if (value != 4 && value != 8 && value != 16)
+                return set_error(c, DRGB_ERR_INVALID, "epoch prefetch must be 4, 8 or 16");
+            c->epoch_prefetch = value;
+            return DRGB_OK;
+        case DRGB_TUNE_EPOCH_DYNAMIC:
+            c->epoch_dynamic = value != 0;
+            return DRGB_OK;
         default:
             return set_error(c, DRGB_ERR_INVALID, "unknown tuning parameter %d", param);
     }

@@ -22,6 +22,23 @@ __global__ void init_embedding_kernel(float2* __restrict__ Y, int64_t n, float r
     }
 }
 
+__global__ void init_batched_kernel(float2* __restrict__ Y, int64_t n, float range, int count,
+                                    const int64_t* __restrict__ inst_off, const uint64_t* __restrict__ inst_seed) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        int lo = 0, hi = count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (inst_off[mid] <= i) lo = mid; else hi = mid - 1;
+        }
+        const uint64_t seed = inst_seed[lo];
+        U4 r = philox4x32_10(U4{uint32_t(i - inst_off[lo]), 0u, 0u, TAG_INIT}, uint32_t(seed), uint32_t(seed >> 32));
+        const float s = 5.9604644775390625e-08f;  // 2^-24
+        float ux = float(r.x >> 8) * s, uy = float(r.y >> 8) * s;
+        Y[i] = make_float2(fmaf(ux, 2.0f * range, -range), fmaf(uy, 2.0f * range, -range));
+    }
+}
+
 __device__ __forceinline__ float clip4(float v) { return fminf(4.0f, fmaxf(-4.0f, v)); }
 
 __device__ __forceinline__ float hw_ex2(float x) {
@@ -42,8 +59,8 @@ __device__ __forceinline__ float pow_pos(float d, float b) { return hw_ex2(b * h
 // parameter (a tuning knob: fewer rows give more warps, more rows fill the
 // per-warp queue of active entries better).
 static constexpr int EPOCH_WARPS = 8;
-static constexpr int Q_PREFETCH = 4;  // 32-entry chunks whose q words are loaded together
-static constexpr int QCAP = 32 + 32 * Q_PREFETCH;  // queue slots per warp
+static constexpr int QPF_MAX = 16;                 // most 32-entry chunks whose q words load together
+static constexpr int QCAP = 32 + 32 * QPF_MAX;     // queue slots per warp
 static constexpr unsigned FULL = 0xffffffffu;
 
 // Force on head i from one active entry e = (i, j) and its negatives, summed in
@@ -51,12 +68,23 @@ static constexpr unsigned FULL = 0xffffffffu;
 // eight negatives are drawn before any gather, so their loads, the col[e]
 // load and the Y_j load overlap; further negatives (neg > 8) follow in groups
 // of four.
+// Instance-local view of a row: rows [off, off + n) with entries from eoff on,
+// negatives drawn under Philox key (k0, k1).  A single instance has off = 0,
+// n = A.n, eoff = 0 and the call's key.
+struct RowInst {
+    int64_t off;
+    uint32_t n;
+    int32_t eoff;
+    uint32_t k0, k1;
+};
+
 __device__ __forceinline__ float2 entry_force(const EpochArgs& A, int32_t e, int64_t i, float2 yi,
-                                              float two_ab, float two_b) {
+                                              float two_ab, float two_b, const RowInst& R) {
     const int32_t j = A.col[e];
-    const uint32_t n32 = uint32_t(A.n), i32 = uint32_t(i);
-    const U4 r0 = philox4x32_10(U4{uint32_t(e), A.t, 0u, TAG_NEGATIVE}, A.k0, A.k1);
-    const U4 r1 = A.neg > 4 ? philox4x32_10(U4{uint32_t(e), A.t, 1u, TAG_NEGATIVE}, A.k0, A.k1) : r0;
+    const uint32_t n32 = R.n, i32 = uint32_t(i - R.off), e32 = uint32_t(e - R.eoff);
+    const float2* Yb = A.Y_in + R.off;
+    const U4 r0 = philox4x32_10(U4{e32, A.t, 0u, TAG_NEGATIVE}, R.k0, R.k1);
+    const U4 r1 = A.neg > 4 ? philox4x32_10(U4{e32, A.t, 1u, TAG_NEGATIVE}, R.k0, R.k1) : r0;
     const uint32_t u[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
     bool ok[8];
     float2 ym[8];
@@ -64,9 +92,9 @@ __device__ __forceinline__ float2 entry_force(const EpochArgs& A, int32_t e, int
     for (int w = 0; w < 8; ++w) {
         const uint32_t m = __umulhi(u[w], n32);  // floor(u n / 2^32)
         ok[w] = (w < A.neg) && (m != i32);
-        ym[w] = ok[w] ? A.Y_in[m] : yi;
+        ym[w] = ok[w] ? Yb[m] : yi;
     }
-    const bool j_ok = uint32_t(j) < n32;
+    const bool j_ok = uint64_t(uint32_t(j)) < uint64_t(A.n);
     if (!j_ok) {  // malformed CSR: report and skip the entry
         report_status(A.status, DRGB_ERR_INVALID);
         return make_float2(0.f, 0.f);
@@ -95,7 +123,7 @@ __device__ __forceinline__ float2 entry_force(const EpochArgs& A, int32_t e, int
     for (int w = 0; w < 8; ++w)
         if (ok[w]) repel(ym[w]);
     for (int g = 2; g * 4 < A.neg; ++g) {
-        const U4 r = philox4x32_10(U4{uint32_t(e), A.t, uint32_t(g), TAG_NEGATIVE}, A.k0, A.k1);
+        const U4 r = philox4x32_10(U4{e32, A.t, uint32_t(g), TAG_NEGATIVE}, R.k0, R.k1);
         const uint32_t v[4] = {r.x, r.y, r.z, r.w};
         bool okg[4];
         float2 yg[4];
@@ -103,7 +131,7 @@ __device__ __forceinline__ float2 entry_force(const EpochArgs& A, int32_t e, int
         for (int w = 0; w < 4; ++w) {
             const uint32_t m = __umulhi(v[w], n32);
             okg[w] = (g * 4 + w < A.neg) && (m != i32);
-            yg[w] = okg[w] ? A.Y_in[m] : yi;
+            yg[w] = okg[w] ? Yb[m] : yi;
         }
 #pragma unroll
         for (int w = 0; w < 4; ++w)
@@ -123,7 +151,7 @@ __device__ __forceinline__ float2 entry_force(const EpochArgs& A, int32_t e, int
 // all lanes work although only about a quarter of the entries fire in an
 // epoch.  The lane that owns a row then adds that row's forces in entry order,
 // which makes each row's sum independent of how entries fell into batches.
-template <int EPOCH_ROWS>
+template <int EPOCH_ROWS, int Q_PREFETCH, bool DYNAMIC>
 __global__ void __launch_bounds__(EPOCH_WARPS * 32, 4)
 embed_epoch_kernel(EpochArgs A) {
     __shared__ int32_t s_rp[EPOCH_WARPS][EPOCH_ROWS + 1];
@@ -132,20 +160,44 @@ embed_epoch_kernel(EpochArgs A) {
     __shared__ int32_t s_qh[EPOCH_WARPS][QCAP];
     __shared__ float2 s_term[EPOCH_WARPS][32];
     __shared__ int32_t s_seg[EPOCH_WARPS][32];   // per owner row: first queue slot | count << 8
+    __shared__ RowInst s_inst[EPOCH_WARPS][EPOCH_ROWS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     const float two_ab = 2.0f * A.a * A.b, two_b = 2.0f * A.b;
     const uint64_t t0 = A.t, t1 = uint64_t(A.t) + 1;
     const int64_t n_blocks = (A.n + EPOCH_ROWS - 1) / EPOCH_ROWS;
+    int64_t rb_static = int64_t(blockIdx.x) * EPOCH_WARPS + w;
     for (;;) {
         int64_t rb = 0;
-        if (lane == 0) rb = atomicAdd(A.work, 1u);
-        rb = __shfl_sync(FULL, rb, 0);
+        if (DYNAMIC) {
+            if (lane == 0) rb = atomicAdd(A.work, 1u);
+            rb = __shfl_sync(FULL, rb, 0);
+        } else {
+            rb = rb_static;
+            rb_static += int64_t(gridDim.x) * EPOCH_WARPS;
+        }
         if (rb >= n_blocks) break;
         const int64_t r0 = rb * EPOCH_ROWS;
         const int nr = int(A.n - r0 < EPOCH_ROWS ? A.n - r0 : EPOCH_ROWS);
         if (lane <= nr) s_rp[w][lane] = A.row_ptr[r0 + lane];
-        if (lane < nr) s_y[w][lane] = A.Y_in[r0 + lane];
+        if (lane < nr) {
+            s_y[w][lane] = A.Y_in[r0 + lane];
+            RowInst R{0, uint32_t(A.n), 0, A.k0, A.k1};
+            if (A.count > 0) {
+                const int64_t i = r0 + lane;
+                int lo = 0, hi = A.count - 1;  // instance b with inst_off[b] <= i
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (A.inst_off[mid] <= i) lo = mid; else hi = mid - 1;
+                }
+                R.off = A.inst_off[lo];
+                R.n = uint32_t(A.inst_off[lo + 1] - R.off);
+                R.eoff = A.row_ptr[R.off];
+                R.k0 = uint32_t(A.inst_seed[lo]);
+                R.k1 = uint32_t(A.inst_seed[lo] >> 32);
+            }
+            s_inst[w][lane] = R;
+        }
         __syncwarp();
         const int32_t e_begin = s_rp[w][0], e_end = s_rp[w][nr];
         float ax = 0.f, ay = 0.f;
@@ -154,7 +206,7 @@ embed_epoch_kernel(EpochArgs A) {
         auto process = [&](int cnt) {
             float2 f = make_float2(0.f, 0.f);
             const int h = lane < cnt ? s_qh[w][lane] : -1 - lane;
-            if (lane < cnt) f = entry_force(A, s_qe[w][lane], r0 + h, s_y[w][h], two_ab, two_b);
+            if (lane < cnt) f = entry_force(A, s_qe[w][lane], r0 + h, s_y[w][h], two_ab, two_b, s_inst[w][h]);
             s_term[w][lane] = f;
             s_seg[w][lane] = 0;
             __syncwarp();
@@ -221,6 +273,7 @@ embed_epoch_kernel(EpochArgs A) {
         __syncwarp();
     }
     // the last CTA to finish resets the work counter for the next launch
+    if (!DYNAMIC) return;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -238,13 +291,32 @@ int launch_epoch(Ctx* c, const EpochArgs& A, int rows, cudaStream_t st) {
     const int64_t row_blocks = (A.n + rows - 1) / rows;
     const int blocks = grid_for(row_blocks, EPOCH_WARPS, c->num_sms * 4);
     if (!A.work) return set_error(c, DRGB_ERR_INVALID, "epoch: no work counter");
-    switch (rows) {
-        case 4: embed_epoch_kernel<4><<<blocks, threads, 0, st>>>(A); break;
-        case 8: embed_epoch_kernel<8><<<blocks, threads, 0, st>>>(A); break;
-        case 16: embed_epoch_kernel<16><<<blocks, threads, 0, st>>>(A); break;
-        case 31: embed_epoch_kernel<31><<<blocks, threads, 0, st>>>(A); break;
-        default: return set_error(c, DRGB_ERR_INVALID, "epoch rows per block must be 4, 8, 16 or 31");
+    const int pf = c->epoch_prefetch;
+    const bool dyn = c->epoch_dynamic != 0;
+#define DRGB_EPOCH_CASE(R, P)                                                           \
+    if (rows == R && pf == P) {                                                        \
+        if (dyn) embed_epoch_kernel<R, P, true><<<blocks, threads, 0, st>>>(A);        \
+        else embed_epoch_kernel<R, P, false><<<blocks, threads, 0, st>>>(A);           \
+        DRGB_CHECK_LAUNCH(c);                                                          \
+        return DRGB_OK;                                                                \
     }
+    DRGB_EPOCH_CASE(4, 4)
+    DRGB_EPOCH_CASE(4, 8)
+    DRGB_EPOCH_CASE(8, 4)
+    DRGB_EPOCH_CASE(8, 8)
+    DRGB_EPOCH_CASE(8, 16)
+    DRGB_EPOCH_CASE(16, 4)
+    DRGB_EPOCH_CASE(16, 8)
+    DRGB_EPOCH_CASE(16, 16)
+    DRGB_EPOCH_CASE(31, 16)
+#undef DRGB_EPOCH_CASE
+    return set_error(c, DRGB_ERR_INVALID, "epoch: unsupported rows/prefetch combination %d/%d", rows, pf);
+}
+
+int launch_init_batched(Ctx* c, float2* Y, int64_t n_total, float range, int count,
+                        const int64_t* inst_off, const uint64_t* inst_seed, cudaStream_t st) {
+    int blocks = grid_for(n_total, 256, c->num_sms * 16);
+    init_batched_kernel<<<blocks, 256, 0, st>>>(Y, n_total, range, count, inst_off, inst_seed);
     DRGB_CHECK_LAUNCH(c);
     return DRGB_OK;
 }
@@ -261,7 +333,8 @@ int launch_init(Ctx* c, float2* Y, int64_t n, float range, uint64_t seed, cudaSt
 // graph (on a private stream) and the graph is launched on `st`.
 int run_epochs(Ctx* c, float2* Y, float2* Y_tmp, const int32_t* rp, const int32_t* col,
                const uint32_t* q, int64_t n, float a, float b, float lr0, int neg, int t_begin,
-               int t_end, int T, uint64_t seed, int rows_per_warp, cudaStream_t st) {
+               int t_end, int T, uint64_t seed, int rows_per_warp, cudaStream_t st, int count,
+               const int64_t* inst_off, const uint64_t* inst_seed) {
     if (t_end <= t_begin) return DRGB_OK;
     cudaStream_t cap;
     DRGB_CUDA(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
@@ -292,6 +365,9 @@ int run_epochs(Ctx* c, float2* Y, float2* Y_tmp, const int32_t* rp, const int32_
         A.k1 = uint32_t(seed >> 32);
         A.status = c->d_status;
         A.work = c->d_work;
+        A.count = count;
+        A.inst_off = inst_off;
+        A.inst_seed = inst_seed;
         rc = launch_epoch(c, A, rows_per_warp, cap);
         float2* tmp = src;
         src = dst;

@@ -17,12 +17,28 @@ struct EpochArgs {
     uint32_t k0, k1;
     int* status;          // device status word (malformed CSR is reported here)
     unsigned int* work;   // [0] next row block, [1] finished CTAs; zero between launches
+    // Batched form (count > 0): rows [inst_off[b], inst_off[b+1]) form instance b,
+    // whose entries, negatives and Philox key (inst_seed[b]) are instance-local.
+    int count = 0;
+    const int64_t* inst_off = nullptr;
+    const uint64_t* inst_seed = nullptr;
 };
 
 int launch_epoch(Ctx* c, const EpochArgs& A, int rows_per_warp, cudaStream_t st);
 int launch_init(Ctx* c, float2* Y, int64_t n, float range, uint64_t seed, cudaStream_t st);
 int run_epochs(Ctx* c, float2* Y, float2* Y_tmp, const int32_t* rp, const int32_t* col,
                const uint32_t* q, int64_t n, float a, float b, float lr0, int neg, int t_begin,
-               int t_end, int T, uint64_t seed, int rows_per_warp, cudaStream_t st);
+               int t_end, int T, uint64_t seed, int rows_per_warp, cudaStream_t st,
+               int count = 0, const int64_t* inst_off = nullptr, const uint64_t* inst_seed = nullptr);
+// Time every supported epoch schedule on this graph (Ya, Yb: n-float2 scratch)
+// and keep the fastest in the context; results do not depend on the choice.
+int autotune_epoch(Ctx* c, const float2* Y, float2* Ya, float2* Yb, const int32_t* rp, const int32_t* col,
+                   const uint32_t* q, int64_t n, float a, float b, int neg, int T, uint64_t seed, int trials,
+                   cudaStream_t st, int count, const int64_t* inst_off, const uint64_t* inst_seed,
+                   float* best_us);
+// Batched initialisation: row i of instance b gets Philox counter (i - inst_off[b], 0, 0, 1)
+// under key inst_seed[b].
+int launch_init_batched(Ctx* c, float2* Y, int64_t n_total, float range, int count,
+                        const int64_t* inst_off, const uint64_t* inst_seed, cudaStream_t st);
 
 }  // namespace drgb

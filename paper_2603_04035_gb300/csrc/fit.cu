@@ -17,15 +17,17 @@ struct FitBuffers {
     float* w;
     uint32_t* q;
     float2* Y_tmp;
+    float2* Y_tune;
     void* fuzzy_scratch;
 };
 
 static size_t fit_bytes(int64_t n, int k) {
     const size_t nk = size_t(n) * k;
     return Carve::round(nk * 4) * 2 + Carve::round((n + 1) * 4) + Carve::round(2 * nk * 4) * 3 +
-           Carve::round(n * 8) + fuzzy_scratch_bytes(n, k) + 4096;
+           Carve::round(n * 8) * 2 + Carve::round(fuzzy_scratch_bytes(n, k)) + 4096;
 }
 
+// Fit buffers first, then the k-NN scratch region (disjoint from them).
 static FitBuffers carve_fit(void* base, int64_t n, int k) {
     const size_t nk = size_t(n) * k;
     Carve cv(base);
@@ -37,6 +39,7 @@ static FitBuffers carve_fit(void* base, int64_t n, int k) {
     b.w = cv.take<float>(2 * nk);
     b.q = cv.take<uint32_t>(2 * nk);
     b.Y_tmp = cv.take<float2>(n);
+    b.Y_tune = cv.take<float2>(n);
     b.fuzzy_scratch = cv.take<char>(fuzzy_scratch_bytes(n, k));
     return b;
 }
@@ -57,9 +60,12 @@ extern "C" int drgb_fit_transform(drgb_ctx* c, const float* X, int64_t n, int32_
         return set_error(c, DRGB_ERR_INVALID, "fit_transform: bad parameters");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int k = p->k;
-    rc = ensure_scratch(c, fit_bytes(n, k), st);
+    if (p->knn_mode < 0 || p->knn_mode > 3) return set_error(c, DRGB_ERR_INVALID, "fit_transform: bad knn_mode");
+    const size_t fb = Carve::round(fit_bytes(n, k));
+    rc = ensure_scratch(c, fb + knn_scratch_bytes(n, d, k, p->knn_mode), st);
     if (rc) return rc;
     FitBuffers b = carve_fit(c->scratch, n, k);
+    void* knn_scratch = static_cast<char*>(c->scratch) + fb;
 
     float a = 0.f, bb = 0.f;
     rc = drgb_find_ab(p->spread, p->min_dist, &a, &bb);
@@ -69,7 +75,7 @@ extern "C" int drgb_fit_transform(drgb_ctx* c, const float* X, int64_t n, int32_
     rc = launch_nonfinite_scan(c, X, n * d, st);
     if (rc) return rc;
     if ((rc = stage_mark(c, 0, st))) return rc;
-    rc = drgb_knn_graph(c, X, n, d, k, p->knn_mode, b.idx, b.dist, stream);
+    rc = knn_run(c, X, n, d, k, p->knn_mode, b.idx, b.dist, st, knn_scratch);
     if (rc) return rc;
     if ((rc = stage_mark(c, 1, st))) return rc;
     rc = build_fuzzy_graph(c, b.idx, b.dist, n, k, p->n_epochs, b.row_ptr, b.col, b.w, b.q, nullptr,
@@ -79,6 +85,12 @@ extern "C" int drgb_fit_transform(drgb_ctx* c, const float* X, int64_t n, int32_
     float2* Y = reinterpret_cast<float2*>(Y_out);
     rc = launch_init(c, Y, n, p->init_range, p->seed_init, st);
     if (rc) return rc;
+    if (p->flags & DRGB_FLAG_AUTOTUNE) {
+        float us = 0.f;
+        rc = autotune_epoch(c, Y, b.Y_tune, b.Y_tmp, b.row_ptr, b.col, b.q, n, a, bb, p->neg, p->n_epochs,
+                            p->seed_neg, 3, st, 0, nullptr, nullptr, &us);
+        if (rc) return rc;
+    }
     if ((rc = stage_mark(c, 3, st))) return rc;
     if (!cb) {
         rc = run_epochs(c, Y, b.Y_tmp, b.row_ptr, b.col, b.q, n, a, bb, p->lr0, p->neg, 0, p->n_epochs,

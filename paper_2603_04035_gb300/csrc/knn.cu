@@ -322,13 +322,36 @@ int check_knn_args(Ctx* c, const float* X, int64_t n, int d, int k, const void* 
 
 using namespace drgb;
 
+namespace drgb {
+
+int knn_resolve_mode(int64_t n, int d, int k, int mode) {
+    if (mode == 0) return knn_tc_preferred(n, d, k) ? 3 : 1;
+    return mode;
+}
+
+size_t knn_scratch_bytes(int64_t n, int d, int k, int mode) {
+    (void)k;
+    const int m = knn_resolve_mode(n, d, k, mode);
+    return (m == 2 || m == 3) ? knn_tc_scratch_bytes(n, d) : 0;
+}
+
+int knn_run(Ctx* c, const float* X, int64_t n, int d, int k, int mode, int32_t* idx_out, float* dist_out,
+            cudaStream_t st, void* scratch) {
+    const int m = knn_resolve_mode(n, d, k, mode);
+    if (m == 2 || m == 3) return knn_tc(c, X, n, d, k, m == 3, idx_out, dist_out, st, scratch);
+    if (m != 1) return set_error(c, DRGB_ERR_INVALID, "knn_graph: bad mode %d", mode);
+    return launch_knn_exact(c, X, n, d, k, nullptr, n, idx_out, dist_out, true, st);
+}
+
+}  // namespace drgb
+
 extern "C" int drgb_knn_graph(drgb_ctx* c, const float* X, int64_t n, int32_t d, int32_t k,
                               int32_t mode, int32_t* idx_out, float* dist_out, void* stream) {
     int rc = check_knn_args(c, X, n, d, k, idx_out, dist_out);
     if (rc) return rc;
+    if (mode < 0 || mode > 3) return set_error(c, DRGB_ERR_INVALID, "knn_graph: bad mode %d", mode);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (mode == 2 || mode == 3) return knn_tc(c, X, n, d, k, mode == 3, idx_out, dist_out, st);
-    if (mode == 0 && knn_tc_preferred(n, d, k)) return knn_tc(c, X, n, d, k, true, idx_out, dist_out, st);
-    if (mode != 0 && mode != 1) return set_error(c, DRGB_ERR_INVALID, "knn_graph: bad mode %d", mode);
-    return launch_knn_exact(c, X, n, d, k, nullptr, n, idx_out, dist_out, true, st);
+    const size_t bytes = knn_scratch_bytes(n, d, k, mode);
+    if (bytes && (rc = ensure_scratch(c, bytes, st))) return rc;
+    return knn_run(c, X, n, d, k, mode, idx_out, dist_out, st, c->scratch);
 }

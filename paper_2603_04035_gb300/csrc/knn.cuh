@@ -25,7 +25,16 @@ int launch_nonfinite_scan(Ctx* c, const float* X, int64_t count, cudaStream_t st
 
 // BF16 tensor-core candidate generation + FP32 re-rank (knn_tc.cu).
 bool knn_tc_preferred(int64_t n, int d, int k);
+size_t knn_tc_scratch_bytes(int64_t n, int d);
+// `scratch` must hold knn_tc_scratch_bytes(n, d) bytes (256-byte aligned).
 int knn_tc(Ctx* c, const float* X, int64_t n, int d, int k, bool f16, int32_t* idx_out, float* dist_out,
-           cudaStream_t st);
+           cudaStream_t st, void* scratch);
+
+// k-NN graph with the mode resolved (0 = auto); `scratch` holds
+// knn_scratch_bytes(n, d, k, mode) bytes (may be null when that is 0).
+int knn_resolve_mode(int64_t n, int d, int k, int mode);
+size_t knn_scratch_bytes(int64_t n, int d, int k, int mode);
+int knn_run(Ctx* c, const float* X, int64_t n, int d, int k, int mode, int32_t* idx_out, float* dist_out,
+            cudaStream_t st, void* scratch);
 
 }  // namespace drgb

@@ -611,17 +611,23 @@ static size_t tc_scratch_bytes(int64_t n, int d, int64_t n_pad, int nblk) {
            Carve::round(n * 4) + Carve::round(64) + TC_PART_BYTES + 8192;
 }
 
+static constexpr int TC_COLSUM_BLOCKS = 256;
+
+size_t knn_tc_scratch_bytes(int64_t n, int d) {
+    const int64_t n_pad = (n + TC_BN - 1) / TC_BN * TC_BN;
+    return tc_scratch_bytes(n, d, n_pad, TC_COLSUM_BLOCKS);
+}
+
 template <bool F16>
 static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t* idx_out, float* dist_out,
-                       cudaStream_t st) {
+                       cudaStream_t st, void* scratch) {
     if (d + 3 > TC_K || k >= TC_KP)
         return set_error(c, DRGB_ERR_INVALID, "knn_graph: tensor-core mode needs d <= %d and k < %d", TC_K - 3,
                          TC_KP);
     const int64_t n_pad = (n + TC_BN - 1) / TC_BN * TC_BN;
-    const int nblk = 256;
-    int rc = ensure_scratch(c, tc_scratch_bytes(n, d, n_pad, nblk), st);
-    if (rc) return rc;
-    Carve cv(c->scratch);
+    const int nblk = TC_COLSUM_BLOCKS;
+    int rc = DRGB_OK;
+    Carve cv(scratch);
     float* partial = cv.take<float>(size_t(nblk) * d);
     float* mean = cv.take<float>(d);
     op16* XA = cv.take<op16>(n_pad * TC_K);
@@ -684,9 +690,9 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
 }
 
 int knn_tc(Ctx* c, const float* X, int64_t n, int d, int k, bool f16, int32_t* idx_out, float* dist_out,
-           cudaStream_t st) {
-    return f16 ? knn_tc_impl<true>(c, X, n, d, k, idx_out, dist_out, st)
-               : knn_tc_impl<false>(c, X, n, d, k, idx_out, dist_out, st);
+           cudaStream_t st, void* scratch) {
+    return f16 ? knn_tc_impl<true>(c, X, n, d, k, idx_out, dist_out, st, scratch)
+               : knn_tc_impl<false>(c, X, n, d, k, idx_out, dist_out, st, scratch);
 }
 
 }  // namespace drgb
