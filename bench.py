@@ -378,13 +378,74 @@ def roofline(args, n, d, nnz, updates, stage_acc, steps, peaks, peak_src):
             "traffic": kernel_traffic("knn_tc_kernel", "paper_2603_04035_gb300/csrc/knn_tc.cu")}
 
 
+# ---------------------------------------------------------------- batched form
+def run_batched(args):
+    """256 uneven instances in one batched call vs 256 sequential plain fits."""
+    import torch
+    import datagen
+    import paper_2603_04035_gb300 as drgb
+
+    dev = torch.device("cuda", 0)
+    X, off = datagen.batched(256, 50, seed=0)
+    T = 300
+    count = len(off) - 1
+    si = [1 + 10 * b for b in range(count)]
+    sn = [2 + 10 * b for b in range(count)]
+    Xd = torch.from_numpy(X).to(dev)
+    Y = torch.empty((X.shape[0], 2), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    params = dict(k=K_NN, n_epochs=T, neg=NEG, knn_mode=args.knn_mode)
+    drgb.fit_transform_batched(Xd, off, si, sn, autotune=True, out=Y, **params)  # tunes the schedule
+    for _ in range(max(0, args.warmup - 1)):
+        drgb.fit_transform_batched(Xd, off, si, sn, out=Y, **params)
+    launches0 = drgb.launch_count()
+    ms = []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            drgb.fit_transform_batched(Xd, off, si, sn, out=Y, **params)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    launches = drgb.launch_count() - launches0
+    Yb = Y.clone()
+    # 256 sequential plain fits of the same instances (one timed pass)
+    torch.cuda.synchronize()
+    flush.fill_(1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    outs = []
+    for b in range(count):
+        outs.append(drgb.fit_transform(Xd[off[b]:off[b + 1]], seed_init=si[b], seed_neg=sn[b], **params))
+    e1.record()
+    e1.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    identical = all(torch.equal(Yb[off[b]:off[b + 1]], outs[b]) for b in range(count))
+    n_tot = int(off[-1])
+    step_ms = float(np.mean(ms))
+    line = {"metric": METRIC, "value": n_tot / (step_ms / 1e3), "unit": "points/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched: {count} Gaussian-mixture instances, n_b ~ logU[1e3, 5e4] "
+                                   f"(sum {n_tot}), d=50, k={K_NN}, {T} epochs, {NEG} negatives",
+                       "l2": "256 MiB buffer written between timed steps"},
+            "sequential_plain": {"value": n_tot / (seq_ms / 1e3), "unit": "points/s", "ms": seq_ms},
+            "speedup_vs_sequential": seq_ms / step_ms,
+            "bit_identical_to_sequential": identical,
+            "gpu_launches": int(launches), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["70k", "2k"], default="70k")
+    ap.add_argument("--workload", choices=["70k", "2k", "batched"], default="70k")
     ap.add_argument("--knn-mode", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -392,6 +453,8 @@ def main():
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_ours(args)
 
 

@@ -124,7 +124,7 @@ int drgb_stage_times(drgb_ctx* ctx, float* ms, int max);
 /* Exact k-nearest-neighbour graph (Section 2.2: "k-nearest neighbor search is
  * the first stage of every method"; the paper uses approximate NNDescent, this
  * library returns the exact graph).
- *   X        n x d FP32, row-major (16-byte aligned).
+ *   X        n x d FP32, row-major (4-byte aligned).
  *   idx_out  n x k int32: the k nearest OTHER points of each row (self
  *            excluded), ordered by FP32 squared distance sum_c (x_ic - x_jc)^2
  *            evaluated directly (not by the expansion), ties by lower index.
@@ -137,7 +137,7 @@ int drgb_stage_times(drgb_ctx* ctx, float* ms, int max);
  * FP32 k nearest are recomputed by the exact scan, so every mode returns the
  * same exact result.
  * Errors: DRGB_ERR_INVALID if n < k + 1, k < 1, k > DRGB_MAX_K, d < 1,
- * a pointer is NULL or X is not 16-byte aligned. */
+ * a pointer is NULL or X is not 4-byte aligned. */
 int drgb_knn_graph(drgb_ctx* ctx, const float* X, int64_t n, int32_t d, int32_t k,
                    int32_t mode, int32_t* idx_out, float* dist_out, void* stream);
 
@@ -284,6 +284,67 @@ int drgb_autotune_epoch(drgb_ctx* ctx, const float* Y, const int32_t* row_ptr, c
                         const uint32_t* q, int64_t n, float a, float b, int32_t neg, int32_t n_epochs,
                         uint64_t seed, int32_t trials, int32_t* choice, float* us_per_epoch,
                         void* stream);
+
+/* ---------------------------------------------------- learned embedder */
+
+/* Learned parametric form (a project addition; the paper has no learned
+ * embedder): an MLP d -> 256 -> 256 -> 2 with exact-erf GELU, BF16 weights
+ * and activations, FP32 accumulation (tcgen05 tensor cores) and FP32 master
+ * weights, trained by Adam on the UMAP cross-entropy of the fuzzy graph's
+ * edges (Section 2.5's loss, with Phi clamped to [1e-4, 1 - 1e-4]).
+ * Parameters are one FP32 device vector of drgb_mlp_param_count() floats:
+ * W1 [256][64] (input columns >= d stay 0), b1 [256], W2 [256][256], b2 [256],
+ * W3 [2][256], b3 [2]; weights are (out, in) row-major. */
+typedef struct drgb_mlp_params {
+    int32_t steps;        /* optimiser steps */
+    int32_t batch_edges;  /* edges per step (4096) */
+    int32_t neg;          /* negatives per edge (5), 0..8 */
+    float lr;             /* Adam learning rate (1e-3) */
+    float beta1, beta2;   /* Adam moments (0.9, 0.999) */
+    float eps;            /* Adam epsilon (1e-8) */
+    uint64_t seed;        /* Philox key of edge and negative sampling */
+} drgb_mlp_params;
+
+int64_t drgb_mlp_param_count(void);
+
+/* Initialise params (device, drgb_mlp_param_count floats): weights uniform in
+ * +-1/sqrt(fan_in) from Philox under `seed`, biases 0.  Errors: d outside 1..64. */
+int drgb_mlp_init(drgb_ctx* ctx, float* params, int32_t d, uint64_t seed, void* stream);
+
+/* Sample one batch (test aid): for edge slot s, draw CSR entries e uniformly
+ * (Philox4x32-10 at counter (step, s, try, 2), word 0 -> e = (u n_nz) >> 32)
+ * and accept the first whose word 1 >> 8 is below q_e (so edges are drawn
+ * proportional to q = 2^24 w; at most 64 tries); then rows[s R] = head(e),
+ * rows[s R + 1] = col[e], rows[s R + 2 + t] = (u n) >> 32 with u = word
+ * (t mod 4) at counter (step, s, 64 + t div 4, 2); R = 2 + neg.
+ * rows: device int32 [n_edges R].  Synchronous. */
+int drgb_mlp_sample(drgb_ctx* ctx, const int32_t* row_ptr, const int32_t* col, const uint32_t* q,
+                    int64_t n, int64_t nnz, int32_t n_edges, int32_t neg, uint32_t step, uint64_t seed,
+                    int32_t* rows, void* stream);
+
+/* Gradient of the mean batch loss for explicit rows (device int32 [n_edges
+ * (2 + neg)], layout as drgb_mlp_sample) of X (n x d FP32 device): writes
+ * grad_out (device FP32, drgb_mlp_param_count) and, if loss_out (device
+ * float) is given, the loss.  Synchronous. */
+int drgb_mlp_grad(drgb_ctx* ctx, const float* params, const float* X, int64_t n, int32_t d,
+                  const int32_t* rows, int32_t n_edges, int32_t neg, float a, float b, float* grad_out,
+                  float* loss_out, void* stream);
+
+/* mp->steps Adam steps on batches sampled as in drgb_mlp_sample (step s of
+ * this call uses counter s) from the CSR (row_ptr, col, q; nnz entries) over
+ * X (n x d).  params, adam_m, adam_v: device FP32 vectors updated in place
+ * (zero the moments before the first call).  losses: device float[steps]
+ * receiving each step's mean batch loss (nullable).  One step is captured as
+ * a CUDA graph and replayed.  Synchronous. */
+int drgb_mlp_train(drgb_ctx* ctx, const float* X, int64_t n, int32_t d, const int32_t* row_ptr,
+                   const int32_t* col, const uint32_t* q, int64_t nnz, float a, float b,
+                   const drgb_mlp_params* mp, float* params, float* adam_m, float* adam_v,
+                   float* losses, void* stream);
+
+/* Embed n new points: Y (n x 2 FP32, device) = MLP(X) for X (n x d FP32,
+ * device), in chunks of 65536 rows on the tensor cores.  Asynchronous. */
+int drgb_mlp_embed(drgb_ctx* ctx, const float* params, const float* X, int64_t n, int32_t d, float* Y,
+                   void* stream);
 
 /* Fill *p with the defaults (k 15, 200 epochs, neg 5, lr0 1, min_dist 0.1,
  * spread 1, init_range 10, seeds 1 and 2, knn_mode auto). */

@@ -32,4 +32,4 @@ something other than itself (library routines, closed forms, finite
 differences, invariants or published constants).  ``sgd.fit`` is a chaotic
 iteration and is pinned only through its parts and through statistics.
 """
-from . import knn, fuzzy, curve, philox, sgd, metrics  # noqa: F401
+from . import knn, fuzzy, curve, philox, sgd, metrics, mlp  # noqa: F401

@@ -34,7 +34,8 @@ __all__ = ["DrgbError", "Graph", "UMAP", "knn_graph", "fuzzy_weights", "find_ab"
            "init_embedding", "embed_epoch", "embed_epochs", "fit_transform", "eval_recall",
            "eval_trust", "default_params", "context", "knn_uncertified", "launch_count",
            "set_profiling", "stage_times", "set_tuning", "fit_transform_batched",
-           "autotune_epoch"]
+           "autotune_epoch", "mlp_param_count", "mlp_init", "mlp_sample", "mlp_grad", "mlp_train",
+           "mlp_embed", "ParametricUMAP"]
 
 
 class DrgbError(RuntimeError):
@@ -302,6 +303,91 @@ def autotune_epoch(Y: torch.Tensor, g: Graph, a: float, b: float, neg: int = 5, 
     _check(_lib.load().drgb_autotune_epoch(ctx, _ptr(Y), *_graph_args(g), Y.shape[0], a, b, neg, n_epochs, seed,
                                            trials, choice, C.byref(us), _stream(Y.device)), ctx)
     return (choice[0], choice[1], choice[2]), us.value
+
+
+# ---------------------------------------------------------------- learned embedder
+def mlp_param_count() -> int:
+    return int(_lib.load().drgb_mlp_param_count())
+
+
+def mlp_init(d: int, seed: int = 0, device=None) -> torch.Tensor:
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    P = torch.empty(mlp_param_count(), dtype=torch.float32, device=dev)
+    ctx = context(dev.index)
+    _check(_lib.load().drgb_mlp_init(ctx, _ptr(P), d, seed, _stream(dev)), ctx)
+    return P
+
+
+def mlp_sample(g: Graph, n_edges: int, neg: int = 5, step: int = 0, seed: int = 0) -> torch.Tensor:
+    dev = g.row_ptr.device
+    rows = torch.empty(n_edges * (2 + neg), dtype=torch.int32, device=dev)
+    ctx = context(dev.index)
+    _check(_lib.load().drgb_mlp_sample(ctx, *_graph_args(g), g.n, g.nnz, n_edges, neg, step, seed, _ptr(rows),
+                                       _stream(dev)), ctx)
+    return rows
+
+
+def mlp_grad(params: torch.Tensor, X: torch.Tensor, rows: torch.Tensor, n_edges: int, neg: int, a: float,
+             b: float):
+    """(gradient vector, mean batch loss) for explicit rows (n_edges * (2 + neg))."""
+    X = _cuda(X, torch.float32, "X", 2)
+    rows = _cuda(rows, torch.int32, "rows")
+    grad = torch.empty_like(params)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    ctx = context(X.device.index)
+    _check(_lib.load().drgb_mlp_grad(ctx, _ptr(params), _ptr(X), X.shape[0], X.shape[1], _ptr(rows), n_edges, neg,
+                                     a, b, _ptr(grad), _ptr(loss), _stream(X.device)), ctx)
+    return grad, float(loss.item())
+
+
+def mlp_train(X: torch.Tensor, g: Graph, a: float, b: float, params: torch.Tensor, adam_m: torch.Tensor,
+              adam_v: torch.Tensor, steps: int, batch_edges: int = 4096, neg: int = 5, lr: float = 1e-3,
+              seed: int = 0, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> torch.Tensor:
+    """Run `steps` Adam steps in place; returns the per-step losses (device)."""
+    X = _cuda(X, torch.float32, "X", 2)
+    mp = _lib.MlpParams(steps, batch_edges, neg, lr, beta1, beta2, eps, seed)
+    losses = torch.zeros(max(1, steps), dtype=torch.float32, device=X.device)
+    ctx = context(X.device.index)
+    _check(_lib.load().drgb_mlp_train(ctx, _ptr(X), X.shape[0], X.shape[1], *_graph_args(g), g.nnz, a, b,
+                                      C.byref(mp), _ptr(params), _ptr(adam_m), _ptr(adam_v), _ptr(losses),
+                                      _stream(X.device)), ctx)
+    return losses[:steps]
+
+
+def mlp_embed(params: torch.Tensor, X: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    X = _cuda(X, torch.float32, "X", 2)
+    Y = torch.empty((X.shape[0], 2), dtype=torch.float32, device=X.device) if out is None else out
+    ctx = context(X.device.index)
+    _check(_lib.load().drgb_mlp_embed(ctx, _ptr(params), _ptr(X), X.shape[0], X.shape[1], _ptr(Y),
+                                      _stream(X.device)), ctx)
+    return Y
+
+
+class ParametricUMAP:
+    """Learned embedder: fit(X) builds the fuzzy graph and trains the MLP on
+    it; transform(X_new) embeds new points with one forward pass."""
+
+    def __init__(self, n_neighbors: int = 15, n_epochs: int = 200, passes: float = 50.0,
+                 batch_edges: int = 4096, neg: int = 5, lr: float = 1e-3, min_dist: float = 0.1,
+                 spread: float = 1.0, seed: int = 0):
+        self.k, self.T, self.passes, self.B = n_neighbors, n_epochs, passes, batch_edges
+        self.neg, self.lr, self.seed = neg, lr, seed
+        self.a, self.b = find_ab(spread, min_dist)
+        self.params = None
+
+    def fit(self, X: torch.Tensor):
+        X = _cuda(X, torch.float32, "X", 2)
+        idx, dist = knn_graph(X, self.k)
+        g = fuzzy_weights(idx, dist, self.T)
+        self.params = mlp_init(X.shape[1], self.seed, X.device.index)
+        m, v = torch.zeros_like(self.params), torch.zeros_like(self.params)
+        steps = max(1, int(round(self.passes * g.nnz / self.B)))
+        self.losses = mlp_train(X, g, self.a, self.b, self.params, m, v, steps, self.B, self.neg, self.lr,
+                                self.seed + 1)
+        return self
+
+    def transform(self, X: torch.Tensor) -> torch.Tensor:
+        return mlp_embed(self.params, X)
 
 
 # ---------------------------------------------------------------- metrics

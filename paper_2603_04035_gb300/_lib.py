@@ -36,6 +36,11 @@ class Params(C.Structure):
                 ("knn_mode", C.c_int32), ("flags", C.c_int32)]
 
 
+class MlpParams(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("batch_edges", C.c_int32), ("neg", C.c_int32), ("lr", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_uint64)]
+
+
 EPOCH_CB = C.CFUNCTYPE(C.c_int, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p)
 
 vp, i32, i64, u64, f32 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_float
@@ -62,6 +67,13 @@ SIGNATURES = {
                                     u64, vp]),
     "drgb_fit_transform": (C.c_int, [vp, vp, i64, i32, C.POINTER(Params), vp, EPOCH_CB, vp, vp]),
     "drgb_default_params": (C.c_int, [C.POINTER(Params)]),
+    "drgb_mlp_param_count": (C.c_int64, []),
+    "drgb_mlp_init": (C.c_int, [vp, vp, i32, u64, vp]),
+    "drgb_mlp_sample": (C.c_int, [vp, vp, vp, vp, i64, i64, i32, i32, C.c_uint32, u64, vp, vp]),
+    "drgb_mlp_grad": (C.c_int, [vp, vp, vp, i64, i32, vp, i32, i32, f32, f32, vp, vp, vp]),
+    "drgb_mlp_train": (C.c_int, [vp, vp, i64, i32, vp, vp, vp, i64, f32, f32, C.POINTER(MlpParams), vp, vp, vp,
+                                 vp, vp]),
+    "drgb_mlp_embed": (C.c_int, [vp, vp, vp, i64, i32, vp, vp]),
     "drgb_fit_transform_batched": (C.c_int, [vp, vp, C.POINTER(C.c_int64), i32, i32, C.POINTER(Params),
                                              C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), vp, vp]),
     "drgb_autotune_epoch": (C.c_int, [vp, vp, vp, vp, vp, i64, f32, f32, i32, i32, u64, i32,

@@ -33,7 +33,7 @@ static int eval_common(Ctx* c, const float* X, const float* Y, int64_t n, int d,
                        int64_t n_query, bool want_recall, double* out, cudaStream_t st) {
     if (!c) return DRGB_ERR_INVALID;
     if (!X || !Y || !out) return set_error(c, DRGB_ERR_INVALID, "eval: NULL pointer");
-    if (!aligned(X, 16) || !aligned(Y, 8)) return set_error(c, DRGB_ERR_INVALID, "eval: misaligned");
+    if (!aligned(X, 4) || !aligned(Y, 8)) return set_error(c, DRGB_ERR_INVALID, "eval: misaligned");
     if (k < 1 || k > DRGB_MAX_K || n < int64_t(k) + 1 || n > INT32_MAX || d < 1)
         return set_error(c, DRGB_ERR_INVALID, "eval: bad sizes");
     if (!want_recall && 2.0 * n - 3.0 * k - 1.0 <= 0)

@@ -312,7 +312,7 @@ int check_knn_args(Ctx* c, const float* X, int64_t n, int d, int k, const void* 
                    const void* dist_out) {
     if (!c) return DRGB_ERR_INVALID;
     if (!X || !idx_out || !dist_out) return set_error(c, DRGB_ERR_INVALID, "knn_graph: NULL pointer");
-    if (!aligned(X, 16)) return set_error(c, DRGB_ERR_INVALID, "knn_graph: X must be 16-byte aligned");
+    if (!aligned(X, 4)) return set_error(c, DRGB_ERR_INVALID, "knn_graph: X must be 4-byte aligned");
     if (k < 1 || k > DRGB_MAX_K || d < 1 || n < int64_t(k) + 1 || n > INT32_MAX)
         return set_error(c, DRGB_ERR_INVALID, "knn_graph: bad sizes n=%lld d=%d k=%d", (long long)n, d, k);
     return DRGB_OK;

@@ -121,6 +121,10 @@ def test_rejects_bad_sizes(drgb):
     assert e.value.code == -1
     with pytest.raises(drgb.DrgbError):
         drgb.knn_graph(torch.zeros((100, 4), device="cuda"), 33)
-    flat = torch.zeros(100 * 4 + 1, device="cuda")
-    with pytest.raises(drgb.DrgbError):
-        drgb.knn_graph(flat[1:].view(100, 4), 5)   # 4-byte offset: misaligned
+    raw = torch.zeros(100 * 4 * 4 + 4, dtype=torch.uint8, device="cuda")
+    rc = drgb._lib.load().drgb_knn_graph(drgb.context(), drgb._ptr(raw[2:]), 100, 4, 5, 1,
+                                         drgb._ptr(raw), drgb._ptr(raw), None)
+    assert rc == -1   # 2-byte offset: not even float-aligned, refused on the host
+    flat = torch.zeros(100 * 4 + 1, device="cuda")  # a 4-byte offset (a row slice) is fine
+    idx, _ = drgb.knn_graph(flat[1:].view(100, 4), 5)
+    assert idx.shape == (100, 5)
