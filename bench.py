@@ -439,13 +439,77 @@ def run_batched(args):
     return 0
 
 
+# ---------------------------------------------------------------- learned form
+def run_mlp(args):
+    """MLP trained on the 70K graph (50 passes of 4096-edge batches), then
+    1M held-out points embedded by the network vs by the plain transform."""
+    import torch
+    import datagen
+    import paper_2603_04035_gb300 as drgb
+
+    dev = torch.device("cuda", 0)
+    X, _, mean, V = datagen.images_config(70_000, seed=0)
+    n_new = args.mlp_heldout
+    Xn = datagen.images_heldout(n_new, mean, V, seed=0)
+    Xd, Xnd = torch.from_numpy(X).to(dev), torch.from_numpy(Xn).to(dev)
+    a, b = drgb.find_ab()
+    idx, dist = drgb.knn_graph(Xd, K_NN)
+    g = drgb.fuzzy_weights(idx, dist, N_EPOCHS)
+    steps = int(round(args.mlp_passes * g.nnz / 4096))
+    P = drgb.mlp_init(50, seed=0)
+    m, v = torch.zeros_like(P), torch.zeros_like(P)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    losses = drgb.mlp_train(Xd, g, a, b, P, m, v, steps, 4096, NEG, 1e-3, 1)
+    e1.record()
+    e1.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    Yt = drgb.fit_transform(Xd, n_epochs=N_EPOCHS)
+    Ym = torch.empty((n_new, 2), device=dev)
+    for _ in range(max(1, args.warmup)):
+        drgb.mlp_embed(P, Xnd, out=Ym)
+    ms = []
+    for _ in range(args.steps):
+        e0.record()
+        drgb.mlp_embed(P, Xnd, out=Ym)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    mlp_ms = float(np.mean(ms))
+    e0.record()
+    Yp = drgb.transform(Xd, Yt, Xnd, n_epochs=N_EPOCHS)
+    e1.record()
+    e1.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    nq = 10_000
+    qm = (drgb.eval_recall(Xnd, Ym, K_NN, nq), drgb.eval_trust(Xnd, Ym, K_NN, nq))
+    qp = (drgb.eval_recall(Xnd, Yp, K_NN, nq), drgb.eval_trust(Xnd, Yp, K_NN, nq))
+    line = {"metric": METRIC, "value": n_new / (mlp_ms / 1e3), "unit": "points/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mlp_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"learned form: MLP 50-256-256-2 trained {args.mlp_passes} passes "
+                                   f"({steps} steps of 4096 edges + {NEG} negatives) on the 70K graph; "
+                                   f"inference on {n_new} held-out points",
+                       "l2": "inputs 200 MB > L2"},
+            "train_ms": train_ms, "final_loss": float(losses[-200:].mean()),
+            "mlp": {"points_per_s": n_new / (mlp_ms / 1e3), "recall15": qm[0], "trust15": qm[1]},
+            "plain_transform": {"points_per_s": n_new / (plain_ms / 1e3), "ms": plain_ms, "recall15": qp[0],
+                                "trust15": qp[1]},
+            "quality_queries": nq}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["70k", "2k", "batched"], default="70k")
+    ap.add_argument("--workload", choices=["70k", "2k", "batched", "mlp"], default="70k")
+    ap.add_argument("--mlp-passes", type=float, default=50.0)
+    ap.add_argument("--mlp-heldout", type=int, default=1_000_000)
     ap.add_argument("--knn-mode", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -455,6 +519,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "mlp":
+        return run_mlp(args)
     return run_ours(args)
 
 

@@ -37,6 +37,7 @@ __all__ = [
     "pca_basis",
     "pca_project",
     "images_config",
+    "images_heldout",
     "aniso_params",
     "aniso_mixture",
     "aniso_mixture_torch",
@@ -124,6 +125,17 @@ def images_config(n: int = 70_000, seed: int = 0, dim: int = 50):
     imgs, labels = blob_images(n, seed)
     mean, V = pca_basis(imgs, dim)
     return pca_project(imgs, mean, V), labels, mean, V
+
+
+def images_heldout(n: int, mean: np.ndarray, V: np.ndarray, seed: int = 0, chunk: int = 100_000):
+    """n further images of the 70K-style generator (its held-out noise stream),
+    projected with the training basis (mean, V); generated in chunks."""
+    out = np.empty((n, V.shape[1]), dtype=np.float32)
+    for s in range(0, n, chunk):
+        m = min(chunk, n - s)
+        imgs, _ = blob_images(m, seed, stream=4, start=s)
+        out[s:s + m] = pca_project(imgs, mean, V)
+    return out
 
 
 def aniso_params(d: int = 50, n_clusters: int = 100, seed: int = 0,

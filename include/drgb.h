@@ -346,6 +346,20 @@ int drgb_mlp_train(drgb_ctx* ctx, const float* X, int64_t n, int32_t d, const in
 int drgb_mlp_embed(drgb_ctx* ctx, const float* params, const float* X, int64_t n, int32_t d, float* Y,
                    void* stream);
 
+/* Plain-optimisation embedding of new points against a fixed training
+ * embedding (the fallback of the learned embedder and the judge of its
+ * recall; the paper embeds only whole data sets).  X_train (n_train x d),
+ * Y_train (n_train x 2), X_new (n_new x d): device FP32.  Each new point gets
+ * its exact k nearest training points and their directed memberships (the
+ * rho / sigma construction of drgb_fuzzy_weights), starts at the
+ * membership-weighted mean of their training coordinates, then moves for
+ * ceil(T/3) synchronous epochs (T = p->n_epochs, lr0 (1 - t/T'), negatives
+ * from the training embedding, Philox key p->seed_neg) while Y_train stays
+ * fixed.  Writes Y_new (n_new x 2).  Synchronous. */
+int drgb_transform(drgb_ctx* ctx, const float* X_train, const float* Y_train, int64_t n_train,
+                   const float* X_new, int64_t n_new, int32_t d, const drgb_params* p, float* Y_new,
+                   void* stream);
+
 /* Fill *p with the defaults (k 15, 200 epochs, neg 5, lr0 1, min_dist 0.1,
  * spread 1, init_range 10, seeds 1 and 2, knn_mode auto). */
 int drgb_default_params(drgb_params* p);

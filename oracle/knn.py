@@ -93,3 +93,25 @@ def sq_dist_rows(X: np.ndarray, rows: np.ndarray, cols: np.ndarray) -> np.ndarra
     """Direct FP64 squared distances between X[rows[a]] and X[cols[a, b]]."""
     X64 = np.asarray(X, dtype=np.float64)
     return ((X64[cols] - X64[rows][:, None, :]) ** 2).sum(axis=2)
+
+
+def knn_query(Q: np.ndarray, X: np.ndarray, k: int, chunk: int = 256):
+    """Exact k nearest rows of X for each row of Q (no self exclusion): the
+    FP64 expansion shortlists k + 16 candidates, whose squared distances are
+    recomputed directly; (distance, index) order.  Returns (idx, dist)."""
+    Q64 = np.asarray(Q, dtype=np.float64)
+    X64 = np.asarray(X, dtype=np.float64)
+    n = X64.shape[0]
+    m = min(n, k + 16)
+    sqx = (X64 ** 2).sum(axis=1)
+    out_i = np.empty((len(Q64), k), dtype=np.int64)
+    out_d = np.empty((len(Q64), k))
+    for s in range(0, len(Q64), chunk):
+        q = Q64[s:s + chunk]
+        D = (q ** 2).sum(axis=1)[:, None] + sqx[None, :] - 2.0 * (q @ X64.T)
+        cand = np.argpartition(D, m - 1, axis=1)[:, :m] if m < n else np.broadcast_to(np.arange(n), D.shape)
+        dd = ((X64[cand] - q[:, None, :]) ** 2).sum(axis=2)
+        order = np.lexsort((cand, dd), axis=1)[:, :k]
+        out_i[s:s + len(q)] = np.take_along_axis(cand, order, axis=1)
+        out_d[s:s + len(q)] = np.sqrt(np.take_along_axis(dd, order, axis=1))
+    return out_i, out_d

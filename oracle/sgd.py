@@ -113,6 +113,62 @@ def epoch(Y, row_ptr, col, q, a, b, lr, neg, t, seed, eps=1e-3, clip=4.0,
     return Y_next
 
 
+def anchored_epoch(Y_train, Y_new, row_ptr, col, q, a, b, lr, neg, t, seed, eps=1e-3, clip=4.0):
+    """One epoch that moves only new points: row i of the CSR is new point i,
+    its entries point into the fixed training embedding, negatives are drawn
+    from the training points (m = floor(u n_train / 2^32), Philox counter
+    (e, t, j' div 4, 0) with e the entry index of the new points' CSR).
+    Returns the new points' coordinates (FP64)."""
+    Yt = np.asarray(Y_train, dtype=np.float64)
+    Yn = np.asarray(Y_new, dtype=np.float64)
+    n_train, n_new = Yt.shape[0], Yn.shape[0]
+    heads = np.repeat(np.arange(n_new), np.diff(np.asarray(row_ptr, np.int64)))
+    e_act = np.nonzero(active_mask(q, t))[0]
+    i = heads[e_act]
+    j = np.asarray(col, np.int64)[e_act]
+    G = np.zeros((n_new, 2))
+    diff = Yn[i] - Yt[j]
+    d = (diff ** 2).sum(axis=1)
+    term = _clip(attraction_coeff(d, a, b)[:, None] * diff, clip)
+    for c in range(2):
+        G[:, c] += np.bincount(i, weights=term[:, c], minlength=n_new)
+    if neg > 0 and e_act.size:
+        words = philox.negative_words(e_act, t, neg, seed)
+        for jj in range(neg):
+            m = philox.negative_index(words[:, jj], n_train)
+            diff = Yn[i] - Yt[m]
+            d = (diff ** 2).sum(axis=1)
+            term = _clip(repulsion_coeff(d, a, b, eps)[:, None] * diff, clip)
+            for c in range(2):
+                G[:, c] += np.bincount(i, weights=term[:, c], minlength=n_new)
+    return Yn + lr * G
+
+
+def transform(X_train, Y_train, X_new, k=15, n_epochs=200, min_dist=0.1, spread=1.0, neg=5, lr0=1.0,
+              seed_neg=2, ab=None):
+    """New points against a fixed training embedding: exact k nearest training
+    points, directed memberships (rho, sigma as in the fuzzy graph), start at
+    the membership-weighted mean of the neighbours' coordinates, then
+    ceil(T / 3) anchored epochs with lr0 (1 - t / T')."""
+    from .fuzzy import directed_weights, smooth_knn
+    from .knn import knn_query
+    a, b = find_ab(spread, min_dist) if ab is None else ab
+    idx, dist = knn_query(X_new, X_train, k)
+    rho, sigma = smooth_knn(dist, k)
+    w = directed_weights(dist, rho, sigma)
+    order = np.argsort(idx, axis=1, kind="stable")
+    col = np.take_along_axis(idx, order, axis=1)
+    w = np.take_along_axis(w, order, axis=1)
+    Yt = np.asarray(Y_train, np.float64)
+    Y = (w[:, :, None] * Yt[col]).sum(axis=1) / w.sum(axis=1)[:, None]
+    q = np.rint(Q_ONE * w).astype(np.uint64).ravel()
+    row_ptr = np.arange(len(X_new) + 1) * k
+    T3 = (n_epochs + 2) // 3
+    for t in range(T3):
+        Y = anchored_epoch(Yt, Y, row_ptr, col.ravel(), q, a, b, lr0 * (1.0 - t / T3), neg, t, seed_neg)
+    return Y
+
+
 def active_count(q, t_total: int) -> np.ndarray:
     """Times each entry fires over epochs 0..T-1: floor(T q / 2^24)."""
     return (np.uint64(t_total) * np.asarray(q, np.uint64)) >> np.uint64(24)
@@ -143,4 +199,4 @@ def fit(X, k: int = 15, n_epochs: int = 200, min_dist: float = 0.1, spread: floa
 
 
 __all__ = ["init_embedding", "active_mask", "attraction_coeff", "repulsion_coeff", "epoch",
-           "active_count", "fit", "Q_ONE"]
+           "anchored_epoch", "transform", "active_count", "fit", "Q_ONE"]

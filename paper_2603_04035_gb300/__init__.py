@@ -35,7 +35,7 @@ __all__ = ["DrgbError", "Graph", "UMAP", "knn_graph", "fuzzy_weights", "find_ab"
            "eval_trust", "default_params", "context", "knn_uncertified", "launch_count",
            "set_profiling", "stage_times", "set_tuning", "fit_transform_batched",
            "autotune_epoch", "mlp_param_count", "mlp_init", "mlp_sample", "mlp_grad", "mlp_train",
-           "mlp_embed", "ParametricUMAP"]
+           "mlp_embed", "ParametricUMAP", "transform"]
 
 
 class DrgbError(RuntimeError):
@@ -360,6 +360,20 @@ def mlp_embed(params: torch.Tensor, X: torch.Tensor, out: torch.Tensor | None = 
     ctx = context(X.device.index)
     _check(_lib.load().drgb_mlp_embed(ctx, _ptr(params), _ptr(X), X.shape[0], X.shape[1], _ptr(Y),
                                       _stream(X.device)), ctx)
+    return Y
+
+
+def transform(X_train: torch.Tensor, Y_train: torch.Tensor, X_new: torch.Tensor, **params) -> torch.Tensor:
+    """Embed new points by plain optimisation against a fixed training embedding."""
+    X_train = _cuda(X_train, torch.float32, "X_train", 2)
+    Y_train = _cuda(Y_train, torch.float32, "Y_train", 2)
+    X_new = _cuda(X_new, torch.float32, "X_new", 2)
+    p = _params(**params)
+    Y = torch.empty((X_new.shape[0], 2), dtype=torch.float32, device=X_new.device)
+    ctx = context(X_new.device.index)
+    _check(_lib.load().drgb_transform(ctx, _ptr(X_train), _ptr(Y_train), X_train.shape[0], _ptr(X_new),
+                                      X_new.shape[0], X_new.shape[1], C.byref(p), _ptr(Y), _stream(X_new.device)),
+           ctx)
     return Y
 
 

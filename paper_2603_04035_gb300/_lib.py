@@ -74,6 +74,7 @@ SIGNATURES = {
     "drgb_mlp_train": (C.c_int, [vp, vp, i64, i32, vp, vp, vp, i64, f32, f32, C.POINTER(MlpParams), vp, vp, vp,
                                  vp, vp]),
     "drgb_mlp_embed": (C.c_int, [vp, vp, vp, i64, i32, vp, vp]),
+    "drgb_transform": (C.c_int, [vp, vp, vp, i64, vp, i64, i32, C.POINTER(Params), vp, vp]),
     "drgb_fit_transform_batched": (C.c_int, [vp, vp, C.POINTER(C.c_int64), i32, i32, C.POINTER(Params),
                                              C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), vp, vp]),
     "drgb_autotune_epoch": (C.c_int, [vp, vp, vp, vp, vp, i64, f32, f32, i32, i32, u64, i32,

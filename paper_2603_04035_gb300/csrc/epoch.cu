@@ -165,7 +165,7 @@ embed_epoch_kernel(EpochArgs A) {
     const unsigned lt_mask = (1u << lane) - 1u;
     const float two_ab = 2.0f * A.a * A.b, two_b = 2.0f * A.b;
     const uint64_t t0 = A.t, t1 = uint64_t(A.t) + 1;
-    const int64_t n_blocks = (A.n + EPOCH_ROWS - 1) / EPOCH_ROWS;
+    const int64_t n_blocks = (A.n - A.row_begin + EPOCH_ROWS - 1) / EPOCH_ROWS;
     int64_t rb_static = int64_t(blockIdx.x) * EPOCH_WARPS + w;
     for (;;) {
         int64_t rb = 0;
@@ -177,12 +177,12 @@ embed_epoch_kernel(EpochArgs A) {
             rb_static += int64_t(gridDim.x) * EPOCH_WARPS;
         }
         if (rb >= n_blocks) break;
-        const int64_t r0 = rb * EPOCH_ROWS;
+        const int64_t r0 = A.row_begin + rb * EPOCH_ROWS;
         const int nr = int(A.n - r0 < EPOCH_ROWS ? A.n - r0 : EPOCH_ROWS);
-        if (lane <= nr) s_rp[w][lane] = A.row_ptr[r0 + lane];
+        if (lane <= nr) s_rp[w][lane] = A.row_ptr[r0 - A.row_begin + lane];
         if (lane < nr) {
             s_y[w][lane] = A.Y_in[r0 + lane];
-            RowInst R{0, uint32_t(A.n), 0, A.k0, A.k1};
+            RowInst R{0, A.neg_n ? A.neg_n : uint32_t(A.n), 0, A.k0, A.k1};
             if (A.count > 0) {
                 const int64_t i = r0 + lane;
                 int lo = 0, hi = A.count - 1;  // instance b with inst_off[b] <= i
@@ -288,7 +288,7 @@ embed_epoch_kernel(EpochArgs A) {
 int launch_epoch(Ctx* c, const EpochArgs& A, int rows, cudaStream_t st) {
     const int threads = EPOCH_WARPS * 32;
     if (rows <= 0) rows = c->epoch_rows;
-    const int64_t row_blocks = (A.n + rows - 1) / rows;
+    const int64_t row_blocks = (A.n - A.row_begin + rows - 1) / rows;
     const int blocks = grid_for(row_blocks, EPOCH_WARPS, c->num_sms * 4);
     if (!A.work) return set_error(c, DRGB_ERR_INVALID, "epoch: no work counter");
     const int pf = c->epoch_prefetch;
@@ -334,7 +334,7 @@ int launch_init(Ctx* c, float2* Y, int64_t n, float range, uint64_t seed, cudaSt
 int run_epochs(Ctx* c, float2* Y, float2* Y_tmp, const int32_t* rp, const int32_t* col,
                const uint32_t* q, int64_t n, float a, float b, float lr0, int neg, int t_begin,
                int t_end, int T, uint64_t seed, int rows_per_warp, cudaStream_t st, int count,
-               const int64_t* inst_off, const uint64_t* inst_seed) {
+               const int64_t* inst_off, const uint64_t* inst_seed, int64_t row_begin, uint32_t neg_n) {
     if (t_end <= t_begin) return DRGB_OK;
     cudaStream_t cap;
     DRGB_CUDA(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
@@ -368,6 +368,8 @@ int run_epochs(Ctx* c, float2* Y, float2* Y_tmp, const int32_t* rp, const int32_
         A.count = count;
         A.inst_off = inst_off;
         A.inst_seed = inst_seed;
+        A.row_begin = row_begin;
+        A.neg_n = neg_n;
         rc = launch_epoch(c, A, rows_per_warp, cap);
         float2* tmp = src;
         src = dst;

@@ -22,6 +22,10 @@ struct EpochArgs {
     int count = 0;
     const int64_t* inst_off = nullptr;
     const uint64_t* inst_seed = nullptr;
+    // Anchored form: only rows [row_begin, n) are updated (row_ptr is indexed
+    // by row - row_begin) and negatives are drawn from [0, neg_n) (0: [0, n)).
+    int64_t row_begin = 0;
+    uint32_t neg_n = 0;
 };
 
 int launch_epoch(Ctx* c, const EpochArgs& A, int rows_per_warp, cudaStream_t st);
@@ -29,7 +33,8 @@ int launch_init(Ctx* c, float2* Y, int64_t n, float range, uint64_t seed, cudaSt
 int run_epochs(Ctx* c, float2* Y, float2* Y_tmp, const int32_t* rp, const int32_t* col,
                const uint32_t* q, int64_t n, float a, float b, float lr0, int neg, int t_begin,
                int t_end, int T, uint64_t seed, int rows_per_warp, cudaStream_t st,
-               int count = 0, const int64_t* inst_off = nullptr, const uint64_t* inst_seed = nullptr);
+               int count = 0, const int64_t* inst_off = nullptr, const uint64_t* inst_seed = nullptr,
+               int64_t row_begin = 0, uint32_t neg_n = 0);
 // Time every supported epoch schedule on this graph (Ya, Yb: n-float2 scratch)
 // and keep the fastest in the context; results do not depend on the choice.
 int autotune_epoch(Ctx* c, const float2* Y, float2* Ya, float2* Yb, const int32_t* rp, const int32_t* col,

@@ -24,11 +24,13 @@ namespace drgb {
 static constexpr uint32_t Q_ONE = 1u << 24;
 
 // ---------------------------------------------------------------- pass 1
+// Rows are the n query points; neighbour indices lie in [0, db_n) and, when
+// self_check is set (a graph of X on itself), must differ from the row.
 __global__ void fuzzy_rows_kernel(const int32_t* __restrict__ idx, const float* __restrict__ dist,
                                   int64_t n, int k, float target, float* __restrict__ w_dir,
                                   int32_t* __restrict__ out_col, float* __restrict__ out_w,
                                   float* __restrict__ rho_out, float* __restrict__ sigma_out,
-                                  int* __restrict__ status) {
+                                  int* __restrict__ status, int64_t db_n, int self_check) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += int64_t(gridDim.x) * blockDim.x) {
         float dr[DRGB_MAX_K];
@@ -39,7 +41,7 @@ __global__ void fuzzy_rows_kernel(const int32_t* __restrict__ idx, const float* 
             dr[s] = dist[i * k + s];
             jr[s] = idx[i * k + s];
             mean += dr[s];
-            bad |= !(dr[s] >= 0.f && dr[s] < INFINITY) || jr[s] < 0 || jr[s] >= n || jr[s] == i;
+            bad |= !(dr[s] >= 0.f && dr[s] < INFINITY) || jr[s] < 0 || jr[s] >= db_n || (self_check && jr[s] == i);
         }
         if (bad) report_status(status, DRGB_ERR_INVALID);
         mean /= float(k);
@@ -231,6 +233,15 @@ __global__ void fill_kernel(const int32_t* __restrict__ in_ptr, const int32_t* _
     }
 }
 
+int launch_directed_weights(Ctx* c, const int32_t* idx, const float* dist, int64_t n, int k, int64_t db_n,
+                            float* w_dir, int32_t* out_col, float* out_w, cudaStream_t st) {
+    const float target = float(std::log2(double(k)));
+    fuzzy_rows_kernel<<<grid_for(n, 128, c->num_sms * 16), 128, 0, st>>>(idx, dist, n, k, target, w_dir, out_col,
+                                                                        out_w, nullptr, nullptr, c->d_status, db_n, 0);
+    DRGB_CHECK_LAUNCH(c);
+    return DRGB_OK;
+}
+
 size_t fuzzy_scratch_bytes(int64_t n, int k) {
     const size_t nk = size_t(n) * k;
     size_t b = 0;
@@ -268,7 +279,7 @@ int build_fuzzy_graph(Ctx* c, const int32_t* idx, const float* dist, int64_t n, 
     const int gmax = c->num_sms * 16;
     const float target = float(std::log2(double(k)));
     fuzzy_rows_kernel<<<grid_for(n, 128, gmax), 128, 0, st>>>(idx, dist, n, k, target, w_dir, out_col,
-                                                             out_w, rho, sigma, c->d_status);
+                                                             out_w, rho, sigma, c->d_status, n, 1);
     DRGB_CHECK_LAUNCH(c);
     DRGB_CUDA(c, cudaMemsetAsync(in_cnt, 0, (n + 1) * 4, st));
     DRGB_CUDA(c, cudaMemsetAsync(in_fill, 0, (n + 1) * 4, st));

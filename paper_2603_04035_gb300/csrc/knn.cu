@@ -38,7 +38,7 @@ __device__ __forceinline__ void topk_insert(float (&D)[K], int32_t (&I)[K], floa
 // points starting at p0, over all d dimensions.
 __device__ __forceinline__ void tile_distances(const float* __restrict__ X, int64_t n, int d,
                                                int64_t qi, bool qvalid, int64_t p0, float* s_db,
-                                               float (&acc)[TP]) {
+                                               float (&acc)[TP], const float* __restrict__ Q) {
 #pragma unroll
     for (int p = 0; p < TP; ++p) acc[p] = 0.f;
     for (int c0 = 0; c0 < d; c0 += DC) {
@@ -52,7 +52,7 @@ __device__ __forceinline__ void tile_distances(const float* __restrict__ X, int6
         __syncthreads();
         float qv[DC];
 #pragma unroll
-        for (int cc = 0; cc < DC; ++cc) qv[cc] = (qvalid && c0 + cc < d) ? X[qi * d + c0 + cc] : 0.f;
+        for (int cc = 0; cc < DC; ++cc) qv[cc] = (qvalid && c0 + cc < d) ? Q[qi * d + c0 + cc] : 0.f;
 #pragma unroll 4
         for (int p = 0; p < TP; ++p) {
             float a = acc[p];
@@ -78,7 +78,10 @@ __global__ void __launch_bounds__(KNN_THREADS)
 knn_exact_kernel(const float* __restrict__ X, int64_t n, int d, int k,
                  const int64_t* __restrict__ rows, int64_t n_rows, int32_t* __restrict__ idx_out,
                  float* __restrict__ dist_out, int write_sqrt, const int32_t* __restrict__ rows32,
-                 const int32_t* __restrict__ n_rows_dev, int64_t chunk = 0) {
+                 const int32_t* __restrict__ n_rows_dev, int64_t chunk = 0, const float* __restrict__ Qx = nullptr) {
+    // queries come from Qx (a separate matrix, no self to exclude) or from X
+    const float* Q = Qx ? Qx : X;
+    const int64_t self_off = Qx ? -1 : 0;
     __shared__ __align__(16) float s_db[TP * DC];
     if (n_rows_dev) {
         n_rows = *n_rows_dev;
@@ -103,11 +106,12 @@ knn_exact_kernel(const float* __restrict__ X, int64_t n, int d, int k,
     }
     float acc[TP];
     for (int64_t p0 = p_begin; p0 < p_end; p0 += TP) {
-        tile_distances(X, p_end, d, qi, valid, p0, s_db, acc);
+        tile_distances(X, p_end, d, qi, valid, p0, s_db, acc, Q);
+        const int64_t self = self_off ? int64_t(-1) : qi;
 #pragma unroll
         for (int p = 0; p < TP; ++p) {
             const int64_t gp = p0 + p;
-            if (acc[p] < D[K - 1] && gp < p_end && gp != qi) topk_insert<K>(D, I, acc[p], int32_t(gp));
+            if (acc[p] < D[K - 1] && gp < p_end && gp != self) topk_insert<K>(D, I, acc[p], int32_t(gp));
         }
     }
     if (valid) {
@@ -217,6 +221,20 @@ int launch_knn_exact_rows(Ctx* c, const float* X, int64_t n, int d, int k, const
     return DRGB_OK;
 }
 
+int launch_knn_query(Ctx* c, const float* Q, int64_t nq, const float* X, int64_t n, int d, int k,
+                     int32_t* idx_out, float* dist_out, cudaStream_t st) {
+    const int blocks = int((nq + KNN_THREADS - 1) / KNN_THREADS);
+    if (blocks < 1) return DRGB_OK;
+    if (k <= 16)
+        knn_exact_kernel<16><<<blocks, KNN_THREADS, 0, st>>>(X, n, d, k, nullptr, nq, idx_out, dist_out, 1, nullptr,
+                                                            nullptr, 0, Q);
+    else
+        knn_exact_kernel<32><<<blocks, KNN_THREADS, 0, st>>>(X, n, d, k, nullptr, nq, idx_out, dist_out, 1, nullptr,
+                                                            nullptr, 0, Q);
+    DRGB_CHECK_LAUNCH(c);
+    return DRGB_OK;
+}
+
 int launch_knn_exact(Ctx* c, const float* X, int64_t n, int d, int k, const int64_t* rows,
                      int64_t n_rows, int32_t* idx_out, float* dist_out, bool write_sqrt,
                      cudaStream_t st) {
@@ -263,7 +281,7 @@ rank_kernel(const float* __restrict__ X, int64_t n, int d, int k, const int64_t*
     }
     float acc[TP];
     for (int64_t p0 = 0; p0 < n; p0 += TP) {
-        tile_distances(X, n, d, qi, valid, p0, s_db, acc);
+        tile_distances(X, n, d, qi, valid, p0, s_db, acc, X);
 #pragma unroll
         for (int p = 0; p < TP; ++p) {
             const int64_t gp = p0 + p;

@@ -116,3 +116,63 @@ def test_training_reduces_loss_and_embeds_held_out(drgb, problem):
     Yn = drgb.mlp_embed(P, torch.from_numpy(np.ascontiguousarray(Xn)).cuda()).cpu().numpy()
     r, t = omet.quality(Xn, Yn, 15)
     assert r > 10 * 15 / len(Xn) and t > 0.85
+
+
+def test_transform_matches_oracle(drgb, problem):
+    import torch
+    from oracle import sgd as osgd
+    X, g = problem
+    from oracle import knn as oknn2, fuzzy as ofz
+    Xn, _ = datagen.mixture(2300, 50, 10, seed=7)
+    Xn = np.ascontiguousarray(Xn[2000:])
+    ab = drgb.find_ab(1.0, 0.1)
+    Yt, _ = osgd.fit(X, n_epochs=60, graph=g, ab=ab)       # the oracle's own training embedding
+    Yt = Yt.astype(np.float32)
+    # a small learning rate keeps the anchored epochs from amplifying the
+    # start difference (near-coincident pairs have a steep attraction force)
+    Y = drgb.transform(torch.from_numpy(X).cuda(), torch.from_numpy(Yt).cuda(), torch.from_numpy(Xn).cuda(),
+                       n_epochs=6, seed_neg=5, lr0=0.01).cpu().numpy()
+    ref = osgd.transform(X, Yt, Xn, k=15, n_epochs=6, neg=5, seed_neg=5, ab=ab, lr0=0.01)
+    # The start is a membership-weighted mean; memberships carry the fuzzy-graph
+    # tolerance (1e-5, FP32 sigma bisection), which moves the start by at most
+    # 1e-5 * sum_j |y_j - y0| / sum_j w_j; the epochs then add the epoch tolerance.
+    idx, dist = oknn2.knn_query(Xn, X, 15)
+    rho, sig = ofz.smooth_knn(dist, 15)
+    w = ofz.directed_weights(dist, rho, sig)
+    y0 = (w[:, :, None] * Yt[idx]).sum(1) / w.sum(1)[:, None]
+    spread = (np.abs(Yt[idx] - y0[:, None, :])).sum(1) / w.sum(1)[:, None]
+    bound = 2e-5 * spread + 3e-5 * np.maximum(np.abs(ref), 1.0)
+    err = np.abs(Y - ref)
+    assert np.all(err <= bound), (err.max(), (err / bound).max())
+
+
+def test_learned_embedder_gain_over_plain_transform(drgb, problem):
+    # what the trained network buys: new points embedded by one forward pass
+    # instead of a k-NN search and an optimisation per batch of new points
+    import time
+    import torch
+    X, g = problem
+    Xd = torch.from_numpy(X).cuda()
+    P = drgb.mlp_init(50, seed=1)
+    m, v = torch.zeros_like(P), torch.zeros_like(P)
+    drgb.mlp_train(Xd, _graph(drgb, g), A_, B_, P, m, v, steps=600, batch_edges=1024, neg=5, seed=2)
+    Yt = drgb.fit_transform(Xd, n_epochs=200)
+    Xn, _ = datagen.mixture(22000, 50, 10, seed=7)
+    Xn = torch.from_numpy(np.ascontiguousarray(Xn[2000:])).cuda()
+    for _ in range(2):
+        drgb.mlp_embed(P, Xn)
+        drgb.transform(Xd, Yt, Xn, n_epochs=200)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Ym = drgb.mlp_embed(P, Xn)
+    torch.cuda.synchronize()
+    t_mlp = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Yp = drgb.transform(Xd, Yt, Xn, n_epochs=200)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    rm = drgb.eval_recall(Xn, Ym, 15, 4000)
+    rp = drgb.eval_recall(Xn, Yp, 15, 4000)
+    print(f"mlp {len(Xn) / t_mlp:.3g} pts/s recall {rm:.4f}; transform {len(Xn) / t_plain:.3g} pts/s recall {rp:.4f}")
+    assert t_plain > 5 * t_mlp
+    assert rm > 10 * 15 / len(Xn) and rp > 10 * 15 / len(Xn)

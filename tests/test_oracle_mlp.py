@@ -90,3 +90,32 @@ def test_sampler_uses_documented_counters():
     assert r[5] == e and r[6] == col[e]
     un = philox.philox_generic((7, 1, 64, philox.TAG_MLP), (3, 0), 32)
     assert list(r[7:10]) == [(un[t] * 2) >> 32 for t in range(3)]
+
+
+def test_knn_query_matches_brute_force():
+    from oracle import knn as oknn
+    g = np.random.default_rng(4)
+    X, Q = g.normal(size=(300, 6)), g.normal(size=(40, 6))
+    idx, dist = oknn.knn_query(Q, X, 9)
+    D = ((Q[:, None, :] - X[None, :, :]) ** 2).sum(-1)
+    ref = np.argsort(D, axis=1, kind="stable")[:, :9]
+    assert np.array_equal(idx, ref)
+    np.testing.assert_allclose(dist, np.sqrt(np.take_along_axis(D, ref, axis=1)), rtol=1e-12)
+
+
+def test_anchored_epoch_equals_full_epoch_on_joined_graph():
+    # moving only the new rows equals a full epoch on [train; new] whose training
+    # rows have no entries, with the new rows' negatives restricted to the training set
+    from oracle import sgd
+    g = np.random.default_rng(5)
+    n_t, n_n, k = 50, 7, 4
+    Yt, Yn = g.normal(size=(n_t, 2)), g.normal(size=(n_n, 2))
+    col = np.sort(g.choice(n_t, size=(n_n, k)), axis=1)
+    q = g.integers(1 << 20, 1 << 24, size=n_n * k).astype(np.uint64)
+    rp = np.arange(n_n + 1) * k
+    Y1 = sgd.anchored_epoch(Yt, Yn, rp, col.ravel(), q, 1.5, 0.9, 0.7, 0, 3, 11)
+    # with no negatives the joined-graph epoch is a plain epoch on n_t + n_n rows
+    rp_all = np.concatenate([np.zeros(n_t, np.int64), rp])
+    Y2 = sgd.epoch(np.concatenate([Yt, Yn]), rp_all, col.ravel(), q, 1.5, 0.9, 0.7, 0, 3, 11)
+    np.testing.assert_allclose(Y1, Y2[n_t:], rtol=1e-14)
+    np.testing.assert_array_equal(Y2[:n_t], Yt)
