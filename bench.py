@@ -53,12 +53,17 @@ def load_peaks():
     return dict(FALLBACK_PEAKS), "fallback"
 
 
+EPOCHS = {"70k": 500, "2k": 200, "10m": 200}
+
+
 def workload(rank: int, name: str):
     import datagen
     if name == "70k":
         X, _ = datagen.config_70k(seed=rank)
     elif name == "2k":
         X, _ = datagen.config_small(seed=rank)
+    elif name == "10m":
+        X = datagen.aniso_mixture_torch(10_000_000, 50, 100, seed=rank, device="cuda").cpu().numpy()
     else:
         raise ValueError(name)
     return np.ascontiguousarray(X, dtype=np.float32)
@@ -139,7 +144,7 @@ def kernel_traffic(kernel: str, source_rel: str):
 
 
 # ---------------------------------------------------------------- CPU (oracle) leg
-def oracle_fit_estimate(X: np.ndarray, n_query: int, n_sub: int, n_ep: int, seed: int = 0):
+def oracle_fit_estimate(X: np.ndarray, n_query: int, n_sub: int, n_ep: int, seed: int = 0, T: int = N_EPOCHS):
     """Time the oracle on a bounded sample and extrapolate to one full fit.
 
     k-NN: exact rows for `n_query` queries against all n points, scaled by
@@ -160,29 +165,29 @@ def oracle_fit_estimate(X: np.ndarray, n_query: int, n_sub: int, n_ep: int, seed
     si, sd = oknn.knn(Xs, K_NN)
     t_sub_knn = time.perf_counter() - t0
     t0 = time.perf_counter()
-    gr = ofuzzy.build_csr(si, sd, N_EPOCHS, K_NN)
+    gr = ofuzzy.build_csr(si, sd, T, K_NN)
     t_graph = (time.perf_counter() - t0) * n / n_sub
     Y = osgd.init_embedding(n_sub, 1, 10.0)
     t0 = time.perf_counter()
     for t in range(n_ep):
-        Y = osgd.epoch(Y, gr["row_ptr"], gr["col"], gr["q"], 1.577, 0.895, 1.0 - t / N_EPOCHS, NEG, t, 2)
-    t_ep = (time.perf_counter() - t0) / n_ep * N_EPOCHS * n / n_sub
+        Y = osgd.epoch(Y, gr["row_ptr"], gr["col"], gr["q"], 1.577, 0.895, 1.0 - t / T, NEG, t, 2)
+    t_ep = (time.perf_counter() - t0) / n_ep * T * n / n_sub
     sample = (f"oracle (FP64 NumPy) timed on: exact k-NN of {n_query} query rows against all {n} "
-              f"points (x{n / n_query:.1f}); fuzzy graph and {n_ep} of {N_EPOCHS} epochs on a "
-              f"{n_sub}-point subsample (x{n / n_sub:.1f}, epochs x{N_EPOCHS / n_ep:.0f}); "
+              f"points (x{n / n_query:.1f}); fuzzy graph and {n_ep} of {T} epochs on a "
+              f"{n_sub}-point subsample (x{n / n_sub:.1f}, epochs x{T / n_ep:.0f}); "
               f"extrapolated linearly to one {n}-point fit (subsample k-NN {t_sub_knn:.2f}s not counted)")
     return t_knn + t_graph + t_ep, sample
 
 
-def updates_per_fit_cpu(X: np.ndarray, n_sub: int, seed: int = 0) -> float:
+def updates_per_fit_cpu(X: np.ndarray, n_sub: int, seed: int = 0, T: int = N_EPOCHS) -> float:
     """Edge updates of one fit estimated from the oracle's graph on a subsample
     (per-point rate x n); used only where the GPU count is unavailable."""
     from oracle import fuzzy as ofuzzy, knn as oknn, sgd as osgd
     n = X.shape[0]
     sub = np.sort(np.random.default_rng(seed).choice(n, size=n_sub, replace=False))
     si, sd = oknn.knn(X[sub], K_NN)
-    gr = ofuzzy.build_csr(si, sd, N_EPOCHS, K_NN)
-    return float(osgd.active_count(gr["q"], N_EPOCHS).sum()) * n / n_sub
+    gr = ofuzzy.build_csr(si, sd, T, K_NN)
+    return float(osgd.active_count(gr["q"], T).sum()) * n / n_sub
 
 
 # ---------------------------------------------------------------- reference arm
@@ -192,13 +197,15 @@ def run_reference(args):
         return 0
     X = workload(0, args.workload)
     n = X.shape[0]
+    T = EPOCHS[args.workload]
     cores = os.cpu_count()
-    updates = updates_per_fit_cpu(X, min(n, 10_000))
+    updates = updates_per_fit_cpu(X, min(n, 10_000), T=T)
+    nq = 300 if n <= 100_000 else 8
     for _ in range(args.warmup):
-        oracle_fit_estimate(X, 200, min(n, 4000), 1)
+        oracle_fit_estimate(X, max(1, nq // 2), min(n, 4000), 1, T=T)
     times, sample = [], ""
     for s in range(args.steps):
-        t, sample = oracle_fit_estimate(X, 300, min(n, 6000), 2, seed=s)
+        t, sample = oracle_fit_estimate(X, nq, min(n, 6000), 2, seed=s, T=T)
         times.append(t)
     sec = float(np.mean(times))
     value = updates / sec
@@ -214,11 +221,13 @@ def run_reference(args):
 
 
 def config(args, n):
-    return {"workload": f"{args.workload}: synthetic 28x28 blob images -> FP32 PCA to 50-d, "
-                        f"n={n}, k={K_NN}, {N_EPOCHS} epochs, {NEG} negatives, fit_transform"
-            if args.workload == "70k" else
-            f"{args.workload}: 10-cluster Gaussian mixture n={n} d=50, k={K_NN}, {N_EPOCHS} epochs",
-            "n": n, "d": 50, "k": K_NN, "n_epochs": N_EPOCHS, "neg": NEG,
+    T = EPOCHS[args.workload]
+    desc = {"70k": f"70k: synthetic 28x28 blob images -> FP32 PCA to 50-d, n={n}, k={K_NN}, {T} epochs, "
+                   f"{NEG} negatives, fit_transform",
+            "2k": f"2k: 10-cluster Gaussian mixture n={n} d=50, k={K_NN}, {T} epochs, fit_transform",
+            "10m": f"10m: 100 anisotropic Gaussians n={n} d=50, k={K_NN}, {T} epochs, {NEG} negatives, "
+                   f"fit_transform"}[args.workload]
+    return {"workload": desc, "n": n, "d": 50, "k": K_NN, "n_epochs": T, "neg": NEG,
             "knn_mode": args.knn_mode, "l2": "256 MiB buffer written between timed steps",
             "parallelism": f"replicas x{args.gpus}"}
 
@@ -240,15 +249,16 @@ def run_ours(args):
 
     X_host = workload(rank, args.workload)
     n, d = X_host.shape
+    T = EPOCHS[args.workload]
     X = torch.from_numpy(X_host).to(dev)
-    params = dict(k=K_NN, n_epochs=N_EPOCHS, neg=NEG, knn_mode=args.knn_mode,
+    params = dict(k=K_NN, n_epochs=T, neg=NEG, knn_mode=args.knn_mode,
                   seed_init=1, seed_neg=2)
 
     # updates per fit from the library's own graph (bookkeeping, untimed)
     idx, dst = drgb.knn_graph(X, K_NN, mode=args.knn_mode)
-    g = drgb.fuzzy_weights(idx, dst, N_EPOCHS)
+    g = drgb.fuzzy_weights(idx, dst, T)
     q64 = g.q.to(torch.int64)
-    updates = float(((N_EPOCHS * q64) >> 24).sum().item())
+    updates = float(((T * q64) >> 24).sum().item())
     nnz = g.nnz
     act_sum_neg = updates  # active entries summed over the epochs
     del idx, dst, g, q64
@@ -312,7 +322,7 @@ def run_ours(args):
 
     if rank == 0:
         peaks, peak_src = load_peaks()
-        roof = roofline(args, n, d, nnz, act_sum_neg, stage_acc, args.steps, peaks, peak_src)
+        roof = roofline(args, n, d, nnz, act_sum_neg, stage_acc, args.steps, peaks, peak_src, T)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -328,7 +338,7 @@ def run_ours(args):
                 "clocks": clk.summary(),
                 "paper_context": "UMAP fit_transform 2.60 s on Fashion-MNIST 70K, Apple M3 Ultra (Table 1)"}
         if not args.no_cpu_baseline:
-            sec, sample = oracle_fit_estimate(X_host, 1500, 10_000, 3)
+            sec, sample = oracle_fit_estimate(X_host, 1500 if n <= 100_000 else 16, 10_000, 3, T=T)
             line["cpu_baseline"] = {"value": updates / sec, "unit": UNIT, "cores": os.cpu_count(),
                                     "kind": "oracle", "sample": sample, "s_per_embed": sec}
         print(json.dumps(line), flush=True)
@@ -338,16 +348,17 @@ def run_ours(args):
     return 0
 
 
-def roofline(args, n, d, nnz, updates, stage_acc, steps, peaks, peak_src):
+def roofline(args, n, d, nnz, updates, stage_acc, steps, peaks, peak_src, T):
     """Roofline entry for the step's dominant stage (its average launch)."""
     knn_ms = stage_acc.get("knn", 0.0) / steps
     ep_ms = stage_acc.get("epochs", 0.0) / steps
+    gemm_ms = stage_acc.get("knn_gemm", 0.0) / steps
     if ep_ms >= knn_ms:
-        per_launch_s = ep_ms / N_EPOCHS / 1e3
+        per_launch_s = ep_ms / T / 1e3
         # algorithmic bytes per epoch (average over the T epochs): row_ptr,
         # Y_i read + Y'_i write, col + q of every entry, 8-byte gathers of
         # the tail and the negatives of every active entry
-        act_per_epoch = updates / N_EPOCHS
+        act_per_epoch = updates / T
         bytes_ep = 4 * (n + 1) + 16 * n + 8 * nnz + 8 * act_per_epoch * (1 + NEG)
         achieved = bytes_ep / per_launch_s / 1e9
         peak = float(peaks["hbm_gbs"])
@@ -356,26 +367,26 @@ def roofline(args, n, d, nnz, updates, stage_acc, steps, peaks, peak_src):
                 "bytes_per_launch": bytes_ep, "launch_ms": per_launch_s * 1e3,
                 "traffic": kernel_traffic("embed_epoch_kernel",
                                           "paper_2603_04035_gb300/csrc/epoch.cu")}
-    per_launch_s = knn_ms / 1e3
-    if args.knn_mode != 2:
-        flops = 3.0 * n * n * d      # subtract, multiply, add per pair and dimension
-        mhz = float(peaks.get("sm_max_mhz", 2070.0))
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-        achieved = flops / per_launch_s / 1e12
-        return {"kernel": "knn_exact_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
+    if gemm_ms > 0:
+        # FP16 and BF16 share the tcgen05 kind::f16 rate: the measured BF16 peak applies
+        flops = 2.0 * n * n * d      # algorithmic (d = 50; the GEMM executes K = 64)
+        peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+        achieved = flops / (gemm_ms / 1e3) / 1e12
+        return {"kernel": "knn_tc_kernel", "bound": "tensor", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
-                               f"{mhz:.0f} MHz ({peak_src} clock)",
-                "flops_per_launch": flops, "launch_ms": knn_ms,
-                "traffic": kernel_traffic("knn_exact_kernel", "paper_2603_04035_gb300/csrc/knn.cu")}
-    flops = 2.0 * n * n * d
-    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
-    achieved = flops / per_launch_s / 1e12
-    return {"kernel": "knn_tc_kernel", "bound": "tensor", "achieved": achieved, "peak": peak,
+                "peak_source": f"bf16_tflops_sustained ({peak_src}); FP16 has the same nominal rate",
+                "flops_per_launch": flops, "launch_ms": gemm_ms, "knn_stage_ms": knn_ms,
+                "traffic": kernel_traffic("knn_tc_kernel", "paper_2603_04035_gb300/csrc/knn_tc.cu")}
+    flops = 3.0 * n * n * d      # subtract, multiply, add per pair and dimension
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    achieved = flops / (knn_ms / 1e3) / 1e12
+    return {"kernel": "knn_exact_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak,
-            "peak_source": f"bf16_tflops_sustained ({peak_src})", "flops_per_launch": flops,
-            "launch_ms": knn_ms,
-            "traffic": kernel_traffic("knn_tc_kernel", "paper_2603_04035_gb300/csrc/knn_tc.cu")}
+            "peak_source": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
+                           f"{mhz:.0f} MHz ({peak_src} clock)",
+            "flops_per_launch": flops, "launch_ms": knn_ms,
+            "traffic": kernel_traffic("knn_exact_kernel", "paper_2603_04035_gb300/csrc/knn.cu")}
 
 
 # ---------------------------------------------------------------- batched form
@@ -507,7 +518,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["70k", "2k", "batched", "mlp"], default="70k")
+    ap.add_argument("--workload", choices=["70k", "2k", "10m", "batched", "mlp"], default="70k")
     ap.add_argument("--mlp-passes", type=float, default=50.0)
     ap.add_argument("--mlp-heldout", type=int, default=1_000_000)
     ap.add_argument("--knn-mode", type=int, default=0)

@@ -181,9 +181,11 @@ def aniso_mixture_torch(n: int, d: int = 50, n_clusters: int = 100, seed: int = 
     X = torch.empty((n, d), dtype=torch.float32, device=device)
     for s in range(0, n, chunk):
         m = min(chunk, n - s)
-        lab = torch.arange(s, s + m, device=device) % n_clusters
         z = torch.randn((m, d), generator=gen, device=device, dtype=torch.float32)
-        X[s:s + m] = C[lab] + torch.bmm(Tt[lab], z.unsqueeze(-1)).squeeze(-1)
+        for c in range(n_clusters):  # rows with label c: s + r, (s + r) mod n_clusters = c
+            first = (c - s) % n_clusters
+            if first < m:
+                X[s + first:s + m:n_clusters] = C[c] + z[first::n_clusters] @ Tt[c].T
     return X
 
 

@@ -115,7 +115,8 @@ int drgb_set_tuning(drgb_ctx* ctx, int32_t param, int32_t value);
  * records CUDA events on its stream between its stages; drgb_stage_times
  * (synchronous: waits for the events) writes up to `max` elapsed times in
  * milliseconds: [0] k-NN graph, [1] fuzzy graph, [2] initialisation,
- * [3] epoch loop, and returns the number written (or a negative error). */
+ * [3] epoch loop, [4] the tensor-core k-NN kernel alone (0 if the exact
+ * scan ran), and returns the number written (or a negative error). */
 int drgb_set_profiling(drgb_ctx* ctx, int on);
 int drgb_stage_times(drgb_ctx* ctx, float* ms, int max);
 

@@ -113,6 +113,35 @@ def epoch(Y, row_ptr, col, q, a, b, lr, neg, t, seed, eps=1e-3, clip=4.0,
     return Y_next
 
 
+def epoch_rows(Y, row_ptr, col, q, rows, a, b, lr, neg, t, seed, eps=1e-3, clip=4.0):
+    """The epoch update of selected rows only (same arithmetic as ``epoch``);
+    returns their new coordinates (len(rows) x 2).  For checks on large graphs
+    where a full FP64 epoch is too costly."""
+    Y64 = np.asarray(Y, dtype=np.float64)
+    n = Y64.shape[0]
+    row_ptr = np.asarray(row_ptr, np.int64)
+    out = np.empty((len(rows), 2))
+    for r, i in enumerate(np.asarray(rows, np.int64)):
+        e = np.arange(row_ptr[i], row_ptr[i + 1])
+        e = e[active_mask(np.asarray(q)[e], t)]
+        g = np.zeros(2)
+        if e.size:
+            j = np.asarray(col, np.int64)[e]
+            diff = Y64[i] - Y64[j]
+            d = (diff ** 2).sum(axis=1)
+            g += _clip(attraction_coeff(d, a, b)[:, None] * diff, clip).sum(axis=0)
+            if neg > 0:
+                words = philox.negative_words(e, t, neg, seed)
+                for jj in range(neg):
+                    m = philox.negative_index(words[:, jj], n)
+                    keep = m != i
+                    diff = Y64[i] - Y64[m[keep]]
+                    d = (diff ** 2).sum(axis=1)
+                    g += _clip(repulsion_coeff(d, a, b, eps)[:, None] * diff, clip).sum(axis=0)
+        out[r] = Y64[i] + lr * g
+    return out
+
+
 def anchored_epoch(Y_train, Y_new, row_ptr, col, q, a, b, lr, neg, t, seed, eps=1e-3, clip=4.0):
     """One epoch that moves only new points: row i of the CSR is new point i,
     its entries point into the fixed training embedding, negatives are drawn
@@ -199,4 +228,4 @@ def fit(X, k: int = 15, n_epochs: int = 200, min_dist: float = 0.1, spread: floa
 
 
 __all__ = ["init_embedding", "active_mask", "attraction_coeff", "repulsion_coeff", "epoch",
-           "anchored_epoch", "transform", "active_count", "fit", "Q_ONE"]
+           "epoch_rows", "anchored_epoch", "transform", "active_count", "fit", "Q_ONE"]

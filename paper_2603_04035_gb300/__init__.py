@@ -137,7 +137,7 @@ def set_profiling(on: bool, device=None) -> None:
     _check(_lib.load().drgb_set_profiling(context(device), int(bool(on))), context(device))
 
 
-STAGES = ("knn", "fuzzy", "init", "epochs")
+STAGES = ("knn", "fuzzy", "init", "epochs", "knn_gemm")
 
 
 def stage_times(device=None) -> dict:

@@ -31,6 +31,7 @@ struct Ctx {
     bool profiling = false;       // record stage events in fit_transform
     cudaEvent_t stage_ev[8] = {};
     int stage_marks = 0;
+    bool gemm_marked = false;     // events 6, 7 bracket the tensor-core k-NN kernel
     std::string err;
 };
 

@@ -42,7 +42,8 @@ int stage_mark(Ctx* c, int idx, cudaStream_t st) {
     if (!c->profiling || idx < 0 || idx >= 8) return DRGB_OK;
     if (!c->stage_ev[idx]) DRGB_CUDA(c, cudaEventCreate(&c->stage_ev[idx]));
     DRGB_CUDA(c, cudaEventRecord(c->stage_ev[idx], st));
-    if (idx + 1 > c->stage_marks) c->stage_marks = idx + 1;
+    if (idx < 6 && idx + 1 > c->stage_marks) c->stage_marks = idx + 1;
+    if (idx == 7) c->gemm_marked = true;
     return DRGB_OK;
 }
 
@@ -230,15 +231,24 @@ int drgb_set_profiling(drgb_ctx* c, int on) {
     if (!c) return DRGB_ERR_INVALID;
     c->profiling = on != 0;
     c->stage_marks = 0;
+    c->gemm_marked = false;
     return DRGB_OK;
 }
 
 int drgb_stage_times(drgb_ctx* c, float* ms, int max) {
     if (!c || !ms || max < 0) return DRGB_ERR_INVALID;
     int m = 0;
-    for (int s = 0; s + 1 < c->stage_marks && m < max; ++s, ++m) {
+    for (int s = 0; s + 1 < c->stage_marks && m < max && s < 4; ++s, ++m) {
         DRGB_CUDA(c, cudaEventSynchronize(c->stage_ev[s + 1]));
         DRGB_CUDA(c, cudaEventElapsedTime(&ms[m], c->stage_ev[s], c->stage_ev[s + 1]));
+    }
+    if (m == 4 && max > 4) {  // [4]: the tensor-core k-NN kernel alone (0 if it did not run)
+        ms[4] = 0.f;
+        if (c->gemm_marked) {
+            DRGB_CUDA(c, cudaEventSynchronize(c->stage_ev[7]));
+            DRGB_CUDA(c, cudaEventElapsedTime(&ms[4], c->stage_ev[6], c->stage_ev[7]));
+        }
+        m = 5;
     }
     return m;
 }

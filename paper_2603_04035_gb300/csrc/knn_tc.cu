@@ -546,8 +546,10 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
     P.cand_s = cand_s;
     P.status = c->d_status;
     const int grid = int((n + TC_BM - 1) / TC_BM);
+    if ((rc = stage_mark(c, 6, st))) return rc;
     knn_tc_kernel<F16><<<grid, TC_THREADS, TC_SMEM, st>>>(mA, mB, P);
     DRGB_CHECK_LAUNCH(c);
+    if ((rc = stage_mark(c, 7, st))) return rc;
 
     const int rb = grid_for(n, 128, c->num_sms * 8);
     if (k <= 16)

@@ -165,3 +165,13 @@ def test_fit_small_mixture_quality():
     r, tw = metrics.quality(X, Y, 15, rows, knn_x=graph["knn_idx"][rows])
     assert r > 10 * 15 / 1000  # an order of magnitude above a random embedding
     assert tw > 0.9
+
+
+def test_epoch_rows_equals_full_epoch():
+    g = _small_graph(200, 8, 50, seed=3)
+    n = len(g["row_ptr"]) - 1
+    Y = np.random.default_rng(9).uniform(-5, 5, size=(n, 2))
+    full = sgd.epoch(Y, g["row_ptr"], g["col"], g["q"], 1.577, 0.895, 0.8, 5, 4, 21)
+    rows = np.array([0, 3, 77, n - 1])
+    part = sgd.epoch_rows(Y, g["row_ptr"], g["col"], g["q"], rows, 1.577, 0.895, 0.8, 5, 4, 21)
+    np.testing.assert_allclose(part, full[rows], rtol=1e-13, atol=1e-13)
