@@ -100,16 +100,13 @@ int64_t drgb_ctx_scratch_bytes(const drgb_ctx* ctx);
 int64_t drgb_launch_count(const drgb_ctx* ctx);
 
 /* Tuning knobs (performance only; results do not depend on them):
- *   DRGB_TUNE_EPOCH_ROWS      rows per warp block of the epoch kernel: 4, 8, 16, 31
- *   DRGB_TUNE_EPOCH_PREFETCH  q chunks (32 entries each) loaded per scan step: 4, 8, 16
- *   DRGB_TUNE_EPOCH_DYNAMIC   1: row blocks handed out by an atomic counter; 0: static
- * Supported (rows, prefetch) pairs: (4,4) (4,8) (8,4) (8,8) (8,16) (16,4)
- * (16,8) (16,16) (31,16).  Returns DRGB_ERR_INVALID for an unknown parameter
- * or value; an unsupported pair is reported by the next epoch launch. */
-#define DRGB_TUNE_EPOCH_ROWS 1
-#define DRGB_TUNE_EPOCH_PREFETCH 2
-#define DRGB_TUNE_EPOCH_DYNAMIC 3
+ *   DRGB_TUNE_EPOCH_WARPS     warps per CTA of the epoch's force kernel: 4 or 8
+ * Returns DRGB_ERR_INVALID for an unknown parameter or value. */
+#define DRGB_TUNE_EPOCH_WARPS 1
 int drgb_set_tuning(drgb_ctx* ctx, int32_t param, int32_t value);
+/* Current value of a tuning knob in *value.  DRGB_ERR_INVALID for an unknown
+ * parameter or a NULL pointer. */
+int drgb_get_tuning(const drgb_ctx* ctx, int32_t param, int32_t* value);
 
 /* Stage timing of drgb_fit_transform.  When enabled (on != 0), each fit
  * records CUDA events on its stream between its stages; drgb_stage_times
@@ -224,11 +221,16 @@ int drgb_init_embedding(drgb_ctx* ctx, int64_t n, float init_range, uint64_t see
  *   skipped if m = i, d = |Y_i - Y_m|^2,
  *   g_i += clip4(2b / ((0.001 + d)(1 + a d^b)) (Y_i - Y_m)).
  * Y_out[i] = Y_in[i] + lr g_i.  All reads are from Y_in (Y^(t)); Y_out must
- * not alias Y_in.  Only row i is written per row: no atomics.
+ * not alias Y_in.  No atomics.  The terms of a row are added in an order
+ * fixed by the CSR alone (entry order within groups of 32 active entries of
+ * 512-entry windows; see the epoch source), so the result does not depend on
+ * the launch configuration.
  *   Y_in, Y_out  n x 2 FP32 (8-byte aligned);  row_ptr n+1, col, q as from
- *   drgb_fuzzy_weights.
+ *   drgb_fuzzy_weights (4-byte aligned).
+ * Reads row_ptr[n] back to the host (one small synchronising copy on
+ * `stream`) to size the context scratch; the epoch itself is asynchronous.
  * Errors: DRGB_ERR_INVALID (NULL/aliasing/misaligned pointers, n < 1,
- * neg < 0). */
+ * neg < 0; a malformed CSR is reported by the next synchronising call). */
 int drgb_embed_epoch(drgb_ctx* ctx, const float* Y_in, float* Y_out, const int32_t* row_ptr,
                      const int32_t* col, const uint32_t* q, int64_t n, float a, float b, float lr,
                      int32_t neg, int32_t epoch, uint64_t seed, void* stream);
@@ -238,6 +240,7 @@ int drgb_embed_epoch(drgb_ctx* ctx, const float* Y_in, float* Y_out, const int32
  * on entry and Y^(t_end) on return; Y_tmp (n x 2) is ping-pong scratch.
  * Because the schedule and the negatives are pure functions of (t, seed),
  * running [0, t1) then [t1, T) gives bit-identical results to [0, T).
+ * Like drgb_embed_epoch it reads row_ptr[n] back first.
  * Errors: as drgb_embed_epoch, plus DRGB_ERR_INVALID if
  * 0 <= t_begin <= t_end <= n_epochs does not hold. */
 int drgb_embed_epochs(drgb_ctx* ctx, float* Y, float* Y_tmp, const int32_t* row_ptr,
@@ -265,8 +268,8 @@ int drgb_fit_transform(drgb_ctx* ctx, const float* X, int64_t n, int32_t d,
  * optional HOST arrays of per-instance Philox keys (NULL: every instance uses
  * p->seed_init / p->seed_neg).  Each instance's k-NN graph is computed on its
  * own rows, the fuzzy graph of all instances is built in one pass, and each
- * of the p->n_epochs epochs is one launch over all rows (the loop is one
- * captured CUDA graph).  Instance b's result is bit-identical to
+ * of the p->n_epochs epochs is one force and one update launch over all rows
+ * (the loop is one captured CUDA graph).  Instance b's result is bit-identical to
  * drgb_fit_transform of its rows alone with the same parameters and seeds.
  * Synchronous.  Errors: DRGB_ERR_INVALID (an instance with fewer than k + 1
  * rows, bad offsets or parameters), plus those of drgb_fit_transform. */
@@ -275,12 +278,12 @@ int drgb_fit_transform_batched(drgb_ctx* ctx, const float* X_cat, const int64_t*
                                const uint64_t* seeds_init, const uint64_t* seeds_neg, float* Y_cat,
                                void* stream);
 
-/* Epoch-schedule autotuner: times every supported (rows per block, q
- * prefetch, scheduling) choice for `trials` epochs of the given graph on a
- * scratch copy of Y (n x 2, device; not modified), keeps the fastest in the
- * context (see drgb_set_tuning) and returns it in choice[0..2] (rows,
- * prefetch, dynamic) with its time per epoch.  Every choice gives
- * bit-identical results.  Synchronous. */
+/* Epoch autotuner: times every supported force-kernel width (warps per CTA)
+ * for `trials` epochs of the given graph on a scratch copy of Y (n x 2,
+ * device; not modified), keeps the fastest in the context (see
+ * drgb_set_tuning) and returns it in choice[0] (choice[1], choice[2] are set
+ * to 0) with its time per epoch.  Every choice gives bit-identical results.
+ * Synchronous. */
 int drgb_autotune_epoch(drgb_ctx* ctx, const float* Y, const int32_t* row_ptr, const int32_t* col,
                         const uint32_t* q, int64_t n, float a, float b, int32_t neg, int32_t n_epochs,
                         uint64_t seed, int32_t trials, int32_t* choice, float* us_per_epoch,

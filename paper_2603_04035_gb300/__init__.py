@@ -33,7 +33,7 @@ from ._lib import MAX_K, Params  # noqa: F401
 __all__ = ["DrgbError", "Graph", "UMAP", "knn_graph", "fuzzy_weights", "find_ab",
            "init_embedding", "embed_epoch", "embed_epochs", "fit_transform", "eval_recall",
            "eval_trust", "default_params", "context", "knn_uncertified", "launch_count",
-           "set_profiling", "stage_times", "set_tuning", "fit_transform_batched",
+           "set_profiling", "stage_times", "set_tuning", "get_tuning", "fit_transform_batched",
            "autotune_epoch", "mlp_param_count", "mlp_init", "mlp_sample", "mlp_grad", "mlp_train",
            "mlp_embed", "ParametricUMAP", "transform"]
 
@@ -131,6 +131,14 @@ def set_tuning(param: int, value: int, device=None) -> None:
     """Set a performance knob of the device's context (see include/drgb.h)."""
     ctx = context(device)
     _check(_lib.load().drgb_set_tuning(ctx, param, value), ctx)
+
+
+def get_tuning(param: int, device=None) -> int:
+    """Current value of a performance knob of the device's context."""
+    ctx = context(device)
+    v = C.c_int32(0)
+    _check(_lib.load().drgb_get_tuning(ctx, param, C.byref(v)), ctx)
+    return int(v.value)
 
 
 def set_profiling(on: bool, device=None) -> None:
@@ -294,15 +302,15 @@ def fit_transform_batched(X_cat: torch.Tensor, offsets, seeds_init=None, seeds_n
 
 def autotune_epoch(Y: torch.Tensor, g: Graph, a: float, b: float, neg: int = 5, n_epochs: int = 200,
                    seed: int = 2, trials: int = 3):
-    """Time the epoch schedules on this graph; keeps and returns the fastest
-    ((rows, prefetch, dynamic), microseconds per epoch)."""
+    """Time the epoch force-kernel widths on this graph; keeps and returns the
+    fastest (warps per CTA, microseconds per epoch)."""
     Y = _cuda(Y, torch.float32, "Y", 2)
     choice = (C.c_int32 * 3)()
     us = C.c_float()
     ctx = context(Y.device.index)
     _check(_lib.load().drgb_autotune_epoch(ctx, _ptr(Y), *_graph_args(g), Y.shape[0], a, b, neg, n_epochs, seed,
                                            trials, choice, C.byref(us), _stream(Y.device)), ctx)
-    return (choice[0], choice[1], choice[2]), us.value
+    return int(choice[0]), us.value
 
 
 # ---------------------------------------------------------------- learned embedder

@@ -19,9 +19,7 @@ ERR_NONFINITE = -5
 ERR_DEVICE = -6
 MAX_K = 32
 STATIC_SCRATCH_BYTES = 16 << 20
-TUNE_EPOCH_ROWS = 1
-TUNE_EPOCH_PREFETCH = 2
-TUNE_EPOCH_DYNAMIC = 3
+TUNE_EPOCH_WARPS = 1
 FLAG_AUTOTUNE = 1
 
 ERROR_NAMES = {ERR_INVALID: "invalid argument", ERR_WORKSPACE: "workspace too small",
@@ -54,6 +52,7 @@ SIGNATURES = {
     "drgb_ctx_scratch_bytes": (C.c_int64, [vp]),
     "drgb_launch_count": (C.c_int64, [vp]),
     "drgb_set_tuning": (C.c_int, [vp, i32, i32]),
+    "drgb_get_tuning": (C.c_int, [vp, i32, C.POINTER(i32)]),
     "drgb_set_profiling": (C.c_int, [vp, C.c_int]),
     "drgb_stage_times": (C.c_int, [vp, C.POINTER(C.c_float), C.c_int]),
     "drgb_knn_graph": (C.c_int, [vp, vp, i64, i32, i32, i32, vp, vp, vp]),

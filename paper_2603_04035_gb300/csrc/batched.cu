@@ -35,76 +35,6 @@ __global__ void globalize_idx_kernel(int32_t* __restrict__ idx, int64_t n_total,
     }
 }
 
-struct Choice {
-    int rows, pf, dyn;
-};
-static const Choice kChoices[] = {{4, 4, 1},  {4, 8, 1},  {8, 4, 1},  {8, 8, 1},  {8, 16, 1},
-                                  {16, 4, 1}, {16, 8, 1}, {16, 16, 1}, {4, 8, 0}, {8, 8, 0},
-                                  {16, 8, 0}, {16, 16, 0}, {31, 16, 0}};
-
-// Time `trials` epochs per choice (starting at epoch t0 of a T-epoch schedule)
-// on a scratch copy of Y; keep the fastest choice in the context.
-int autotune_epoch(Ctx* c, const float2* Y, float2* Ya, float2* Yb, const int32_t* rp, const int32_t* col,
-                   const uint32_t* q, int64_t n, float a, float b, int neg, int T, uint64_t seed, int trials,
-                   cudaStream_t st, int count, const int64_t* inst_off, const uint64_t* inst_seed,
-                   float* best_us) {
-    cudaEvent_t e0, e1;
-    DRGB_CUDA(c, cudaEventCreate(&e0));
-    DRGB_CUDA(c, cudaEventCreate(&e1));
-    float best = 1e30f;
-    Choice keep{c->epoch_rows, c->epoch_prefetch, c->epoch_dynamic};
-    int rc = DRGB_OK;
-    for (const Choice& ch : kChoices) {
-        c->epoch_rows = ch.rows;
-        c->epoch_prefetch = ch.pf;
-        c->epoch_dynamic = ch.dyn;
-        EpochArgs A;
-        A.row_ptr = rp;
-        A.col = col;
-        A.q = q;
-        A.n = n;
-        A.a = a;
-        A.b = b;
-        A.neg = neg;
-        A.k0 = uint32_t(seed);
-        A.k1 = uint32_t(seed >> 32);
-        A.status = c->d_status;
-        A.work = c->d_work;
-        A.count = count;
-        A.inst_off = inst_off;
-        A.inst_seed = inst_seed;
-        if (cudaMemcpyAsync(Ya, Y, size_t(n) * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
-            rc = set_error(c, DRGB_ERR_CUDA, "autotune: copy failed");
-            break;
-        }
-        for (int r = 0; r <= trials && rc == DRGB_OK; ++r) {  // first launch warms up
-            if (r == 1) cudaEventRecord(e0, st);
-            A.Y_in = (r & 1) ? Yb : Ya;
-            A.Y_out = (r & 1) ? Ya : Yb;
-            A.t = uint32_t(r % T);
-            A.lr = 1.0f;
-            rc = launch_epoch(c, A, 0, st);
-        }
-        if (rc) break;
-        cudaEventRecord(e1, st);
-        DRGB_CUDA(c, cudaEventSynchronize(e1));
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        const float us = ms * 1000.f / float(trials);
-        if (us < best) {
-            best = us;
-            keep = ch;
-        }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    c->epoch_rows = keep.rows;
-    c->epoch_prefetch = keep.pf;
-    c->epoch_dynamic = keep.dyn;
-    if (best_us) *best_us = best;
-    return rc;
-}
-
 }  // namespace drgb
 
 using namespace drgb;
@@ -145,7 +75,8 @@ int drgb_fit_transform_batched(drgb_ctx* c, const float* X_cat, const int64_t* o
     const size_t Nk = size_t(N) * k;
     const size_t main_bytes = Carve::round(Nk * 4) * 2 + Carve::round((N + 1) * 4) + Carve::round(2 * Nk * 4) * 3 +
                               Carve::round(N * 8) * 2 + Carve::round((count + 1) * 8) + 2 * Carve::round(count * 8) +
-                              Carve::round(fuzzy_scratch_bytes(N, k)) + 8192;
+                              Carve::round(fuzzy_scratch_bytes(N, k)) +
+                              Carve::round(epoch_scratch_bytes(N, int64_t(2 * Nk), count)) + 8192;
     int rc = ensure_scratch(c, Carve::round(main_bytes) + knn_bytes, st);
     if (rc) return rc;
     Carve cv(c->scratch);
@@ -161,6 +92,7 @@ int drgb_fit_transform_batched(drgb_ctx* c, const float* X_cat, const int64_t* o
     uint64_t* d_seed_init = cv.take<uint64_t>(count);
     uint64_t* d_seed_neg = cv.take<uint64_t>(count);
     void* fz = cv.take<char>(fuzzy_scratch_bytes(N, k));
+    void* ep = cv.take<char>(epoch_scratch_bytes(N, int64_t(2 * Nk), count));
     void* knn_scratch = static_cast<char*>(c->scratch) + Carve::round(main_bytes);
 
     std::vector<uint64_t> si(count), sn(count);
@@ -192,13 +124,15 @@ int drgb_fit_transform_batched(drgb_ctx* c, const float* X_cat, const int64_t* o
     if ((rc = launch_init_batched(c, Y, N, p->init_range, count, d_off, d_seed_init, st))) return rc;
     if (p->flags & DRGB_FLAG_AUTOTUNE) {
         float us = 0.f;
-        rc = autotune_epoch(c, Y, Y_tune, Y_tmp, row_ptr, col, q, N, a, bb, p->neg, p->n_epochs, 0, 3, st, count,
+        EpochScratch es;
+        if ((rc = epoch_prepare(c, row_ptr, N, 0, int64_t(2 * Nk), count, d_off, ep, &es, st))) return rc;
+        rc = autotune_epoch(c, Y, Y_tune, Y_tmp, row_ptr, col, q, N, a, bb, p->neg, p->n_epochs, 0, 3, st, es, count,
                             d_off, d_seed_neg, &us);
         if (rc) return rc;
     }
     if ((rc = stage_mark(c, 3, st))) return rc;
-    rc = run_epochs(c, Y, Y_tmp, row_ptr, col, q, N, a, bb, p->lr0, p->neg, 0, p->n_epochs, p->n_epochs, 0, 0, st,
-                    count, d_off, d_seed_neg);
+    rc = run_epochs(c, Y, Y_tmp, row_ptr, col, q, N, a, bb, p->lr0, p->neg, 0, p->n_epochs, p->n_epochs, 0, st,
+                    int64_t(2 * Nk), ep, count, d_off, d_seed_neg);
     if (rc) return rc;
     if ((rc = stage_mark(c, 4, st))) return rc;
     return drgb_sync(c, stream);
@@ -209,21 +143,29 @@ int drgb_autotune_epoch(drgb_ctx* c, const float* Y, const int32_t* row_ptr, con
                         uint64_t seed, int32_t trials, int32_t* choice, float* us_per_epoch, void* stream) {
     if (!c) return DRGB_ERR_INVALID;
     if (!Y || !row_ptr || !col || !q || n < 1 || n > INT32_MAX || neg < 0 || neg > 64 || n_epochs < 1 ||
-        trials < 1 || !aligned(Y, 8))
+        trials < 1 || !aligned(Y, 8) || !aligned(row_ptr, 4) || !aligned(col, 4) || !aligned(q, 4))
         return set_error(c, DRGB_ERR_INVALID, "autotune_epoch: bad arguments");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int rc = ensure_scratch(c, 2 * Carve::round(size_t(n) * 8), st);
+    int32_t nnz = 0;
+    DRGB_CUDA(c, cudaMemcpyAsync(&nnz, row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    DRGB_CUDA(c, cudaStreamSynchronize(st));
+    if (nnz < 0) return set_error(c, DRGB_ERR_INVALID, "autotune_epoch: row_ptr[n] < 0");
+    const size_t yb = Carve::round(size_t(n) * 8);
+    int rc = ensure_scratch(c, 2 * yb + epoch_scratch_bytes(n, nnz, 0), st);
     if (rc) return rc;
     Carve cv(c->scratch);
     float2* Ya = cv.take<float2>(n);
     float2* Yb = cv.take<float2>(n);
+    void* ep = cv.take<char>(epoch_scratch_bytes(n, nnz, 0));
+    EpochScratch es;
+    if ((rc = epoch_prepare(c, row_ptr, n, 0, nnz, 0, nullptr, ep, &es, st))) return rc;
     rc = autotune_epoch(c, reinterpret_cast<const float2*>(Y), Ya, Yb, row_ptr, col, q, n, a, b, neg, n_epochs, seed,
-                        trials, st, 0, nullptr, nullptr, us_per_epoch);
+                        trials, st, es, 0, nullptr, nullptr, us_per_epoch);
     if (rc) return rc;
     if (choice) {
-        choice[0] = c->epoch_rows;
-        choice[1] = c->epoch_prefetch;
-        choice[2] = c->epoch_dynamic;
+        choice[0] = c->epoch_warps;
+        choice[1] = 0;
+        choice[2] = 0;
     }
     return drgb_sync(c, stream);
 }

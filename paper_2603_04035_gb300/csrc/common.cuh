@@ -22,11 +22,8 @@ struct Ctx {
     size_t scratch_bytes = 0;
     int* d_status = nullptr;      // device status word (0 = ok, else DRGB_ERR_*)
     unsigned long long* d_counter = nullptr;  // diagnostic counter (uncertified rows)
-    unsigned int* d_work = nullptr;           // epoch work counters (self-resetting)
     int64_t launches = 0;         // kernels launched (host-side count)
-    int epoch_rows = 4;           // rows per warp block of the epoch kernel (tuning)
-    int epoch_prefetch = 8;       // q chunks loaded per scan step (tuning)
-    int epoch_dynamic = 1;        // dynamic (1) or static (0) row-block assignment (tuning)
+    int epoch_warps = 8;          // warps per CTA of the epoch force kernel (tuning)
     int knn_tile_n = 256;         // database tile width of the tensor-core k-NN (tuning)
     bool profiling = false;       // record stage events in fit_transform
     cudaEvent_t stage_ev[8] = {};
@@ -110,6 +107,27 @@ __host__ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t
         c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
     }
     return c;
+}
+
+// The same generator with its ten round keys given: rk[2r], rk[2r + 1] are the
+// key words of round r (k0 + r W0, k1 + r W1).  A kernel whose key is the same
+// for every thread takes them from its parameters, which saves the key bumps.
+__device__ __forceinline__ U4 philox4x32_10_rk(U4 c, const uint32_t* rk) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = uint64_t(M0) * c.x, p1 = uint64_t(M1) * c.z;
+        c = U4{uint32_t(p1 >> 32) ^ c.y ^ rk[2 * r], uint32_t(p1), uint32_t(p0 >> 32) ^ c.w ^ rk[2 * r + 1],
+               uint32_t(p0)};
+    }
+    return c;
+}
+
+inline void philox_round_keys(uint32_t k0, uint32_t k1, uint32_t* rk) {
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = k0 + uint32_t(r) * 0x9E3779B9u;
+        rk[2 * r + 1] = k1 + uint32_t(r) * 0xBB67AE85u;
+    }
 }
 
 enum : uint32_t { TAG_NEGATIVE = 0u, TAG_INIT = 1u, TAG_MLP = 2u };

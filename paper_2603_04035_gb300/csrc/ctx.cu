@@ -178,7 +178,6 @@ int drgb_ctx_create(int device, drgb_ctx** out) {
     }
     cudaMemset(c->d_status, 0, 256);
     c->d_counter = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(c->d_status) + 128);
-    c->d_work = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(c->d_status) + 192);
     cudaDeviceSynchronize();
     cudaSetDevice(prev);
     *out = c;
@@ -209,21 +208,21 @@ int64_t drgb_launch_count(const drgb_ctx* c) { return c ? c->launches : 0; }
 int drgb_set_tuning(drgb_ctx* c, int32_t param, int32_t value) {
     if (!c) return DRGB_ERR_INVALID;
     switch (param) {
-        case DRGB_TUNE_EPOCH_ROWS:
-            if (value != 4 && value != 8 && value != 16 && value != 31)
-                return set_error(c, DRGB_ERR_INVALID, "epoch rows must be 4, 8, 16 or 31");
-            c->epoch_rows = value;
-            return DRGB_OK;
-        case DRGB_TUNE_EPOCH_PREFETCH:
-            if (value != 4 && value != 8 && value != 16)
-                return set_error(c, DRGB_ERR_INVALID, "epoch prefetch must be 4, 8 or 16");
-            c->epoch_prefetch = value;
-            return DRGB_OK;
-        case DRGB_TUNE_EPOCH_DYNAMIC:
-            c->epoch_dynamic = value != 0;
+        case DRGB_TUNE_EPOCH_WARPS:
+            if (value != 4 && value != 8)
+                return set_error(c, DRGB_ERR_INVALID, "epoch force-kernel width must be 4 or 8 warps");
+            c->epoch_warps = value;
             return DRGB_OK;
         default:
             return set_error(c, DRGB_ERR_INVALID, "unknown tuning parameter %d", param);
+    }
+}
+
+int drgb_get_tuning(const drgb_ctx* c, int32_t param, int32_t* value) {
+    if (!c || !value) return DRGB_ERR_INVALID;
+    switch (param) {
+        case DRGB_TUNE_EPOCH_WARPS: *value = c->epoch_warps; return DRGB_OK;
+        default: return DRGB_ERR_INVALID;
     }
 }
 

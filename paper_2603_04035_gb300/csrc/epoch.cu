@@ -4,8 +4,26 @@
 //
 // Layout: Y is n x 2 FP32 read as float2 (one 8-byte gather per point); the
 // CSR is head-sorted (row_ptr int32, col int32, q uint32 schedule words).
-// No atomics: every row is written by exactly one lane, and all reads come
-// from Y^(t).
+// All reads come from Y^(t); there are no atomics.
+//
+// An epoch is two kernels.  The force kernel gives each warp windows of
+// EPOCH_WIN consecutive CSR entries (counted from its instance's first entry):
+// the warp compacts the window's active entries into shared memory, computes
+// their forces 32 at a time (one entry per lane) and adds each head's terms.
+// The update kernel then gives each row its partial sums, in window order,
+// and writes Y' = Y + lr * sum.
+//
+// Summation order of a row's force (a fixed function of the row's instance
+// CSR, so results do not depend on the launch shape, the tuning or on other
+// instances of a batch):
+//   term(e)       = (((0 + attraction) + repulsion_0) + ...) + repulsion_{neg-1}
+//   group sum     = a window's active entries, in entry order, form groups of
+//                   32; the terms of one head in one group are added by the
+//                   5-step segmented inclusive scan over the group's lanes
+//                   (step d adds the partial d lanes to the left)
+//   window sum    = (((group sum_0) + group sum_1) + ...) over the groups that
+//                   hold the head, in order
+//   force         = (((0 + window sum_0) + window sum_1) + ...) over windows
 #include "common.cuh"
 #include "epoch.cuh"
 
@@ -55,22 +73,11 @@ __device__ __forceinline__ float hw_lg2(float x) {
 // d^b for d > 0 via the hardware base-2 logarithm and exponential.
 __device__ __forceinline__ float pow_pos(float d, float b) { return hw_ex2(b * hw_lg2(d)); }
 
-// Warps per CTA of the epoch kernel; rows per warp block is a template
-// parameter (a tuning knob: fewer rows give more warps, more rows fill the
-// per-warp queue of active entries better).
-static constexpr int EPOCH_WARPS = 8;
-static constexpr int QPF_MAX = 16;                 // most 32-entry chunks whose q words load together
-static constexpr int QCAP = 32 + 32 * QPF_MAX;     // queue slots per warp
 static constexpr unsigned FULL = 0xffffffffu;
 
-// Force on head i from one active entry e = (i, j) and its negatives, summed in
-// the fixed order: attraction, then negatives j' = 0 .. neg-1.  The first
-// eight negatives are drawn before any gather, so their loads, the col[e]
-// load and the Y_j load overlap; further negatives (neg > 8) follow in groups
-// of four.
 // Instance-local view of a row: rows [off, off + n) with entries from eoff on,
 // negatives drawn under Philox key (k0, k1).  A single instance has off = 0,
-// n = A.n, eoff = 0 and the call's key.
+// n = A.n (or the anchored negative range), eoff = 0 and the call's key.
 struct RowInst {
     int64_t off;
     uint32_t n;
@@ -78,21 +85,43 @@ struct RowInst {
     uint32_t k0, k1;
 };
 
-__device__ __forceinline__ float2 entry_force(const EpochArgs& A, int32_t e, int64_t i, float2 yi,
+// Negative words of entry e32 at epoch t, group g (negatives 4g .. 4g+3):
+// Philox4x32-10 at counter (e, t, g, 0) under the row's key.  A single
+// instance takes the precomputed round keys from the kernel parameters.
+template <bool BATCHED>
+__device__ __forceinline__ U4 negative_words(const EpochArgs& A, const RowInst& R, uint32_t e32, uint32_t g) {
+    if (BATCHED) return philox4x32_10(U4{e32, A.t, g, TAG_NEGATIVE}, R.k0, R.k1);
+    return philox4x32_10_rk(U4{e32, A.t, g, TAG_NEGATIVE}, A.rk);
+}
+
+// Force on head i from one active entry e = (i, j) and its negatives, summed in
+// the fixed order: attraction, then negatives j' = 0 .. neg-1.  NEG is the
+// negative count when fixed at compile time (5, the method's default), or -1
+// for any count up to 64 (A.neg).  The first eight negatives are drawn before
+// any gather, so their loads and the Y_j load overlap; further negatives
+// follow in groups of four.
+//
+// A skipped negative (m = i) is evaluated with Y_m = Y_i: its difference vector
+// is zero, so it adds exactly +0 and needs no branch (a sum that starts at +0
+// never becomes -0).  A zero distance takes d^b = 0, so coincident points
+// repel with zero force as well.
+template <int NEG, bool BATCHED>
+__device__ __forceinline__ float2 entry_force(const EpochArgs& A, int32_t e, int32_t j, int64_t i, float2 yi,
                                               float two_ab, float two_b, const RowInst& R) {
-    const int32_t j = A.col[e];
+    constexpr int NP = NEG >= 0 ? (NEG < 8 ? NEG : 8) : 8;  // negatives drawn before the gathers
+    const int neg = NEG >= 0 ? NEG : A.neg;
     const uint32_t n32 = R.n, i32 = uint32_t(i - R.off), e32 = uint32_t(e - R.eoff);
     const float2* Yb = A.Y_in + R.off;
-    const U4 r0 = philox4x32_10(U4{e32, A.t, 0u, TAG_NEGATIVE}, R.k0, R.k1);
-    const U4 r1 = A.neg > 4 ? philox4x32_10(U4{e32, A.t, 1u, TAG_NEGATIVE}, R.k0, R.k1) : r0;
+    U4 r0{0u, 0u, 0u, 0u}, r1{0u, 0u, 0u, 0u};
+    if (NP > 0 && neg > 0) r0 = negative_words<BATCHED>(A, R, e32, 0u);
+    if (NP > 4 && neg > 4) r1 = negative_words<BATCHED>(A, R, e32, 1u);
     const uint32_t u[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-    bool ok[8];
-    float2 ym[8];
+    float2 ym[NP > 0 ? NP : 1];
 #pragma unroll
-    for (int w = 0; w < 8; ++w) {
+    for (int w = 0; w < NP; ++w) {
         const uint32_t m = __umulhi(u[w], n32);  // floor(u n / 2^32)
-        ok[w] = (w < A.neg) && (m != i32);
-        ym[w] = ok[w] ? Yb[m] : yi;
+        const bool ok = (NEG >= 0 || w < neg) && (m != i32);
+        ym[w] = ok ? Yb[m] : yi;
     }
     const bool j_ok = uint64_t(uint32_t(j)) < uint64_t(A.n);
     if (!j_ok) {  // malformed CSR: report and skip the entry
@@ -104,12 +133,10 @@ __device__ __forceinline__ float2 entry_force(const EpochArgs& A, int32_t e, int
     {
         const float dx = yi.x - yj.x, dy = yi.y - yj.y;
         const float d = fmaf(dx, dx, dy * dy);
-        if (d > 0.f) {
-            const float pb = pow_pos(d, A.b);
-            const float c = __fdividef(-two_ab * pb, d * fmaf(A.a, pb, 1.0f));
-            gx += clip4(c * dx);
-            gy += clip4(c * dy);
-        }
+        const float pb = d > 0.f ? pow_pos(d, A.b) : 0.f;
+        const float c = d > 0.f ? __fdividef(-two_ab * pb, d * fmaf(A.a, pb, 1.0f)) : 0.f;
+        gx += clip4(c * dx);
+        gy += clip4(c * dy);
     }
     auto repel = [&](float2 y) {
         const float rx = yi.x - y.x, ry = yi.y - y.y;
@@ -120,197 +147,298 @@ __device__ __forceinline__ float2 entry_force(const EpochArgs& A, int32_t e, int
         gy += clip4(c * ry);
     };
 #pragma unroll
-    for (int w = 0; w < 8; ++w)
-        if (ok[w]) repel(ym[w]);
-    for (int g = 2; g * 4 < A.neg; ++g) {
-        const U4 r = philox4x32_10(U4{e32, A.t, uint32_t(g), TAG_NEGATIVE}, R.k0, R.k1);
-        const uint32_t v[4] = {r.x, r.y, r.z, r.w};
-        bool okg[4];
-        float2 yg[4];
+    for (int w = 0; w < NP; ++w) repel(ym[w]);
+    if (NEG < 0 || NEG > 8) {
+        for (int g = 2; g * 4 < neg; ++g) {
+            const U4 r = negative_words<BATCHED>(A, R, e32, uint32_t(g));
+            const uint32_t v[4] = {r.x, r.y, r.z, r.w};
+            float2 yg[4];
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            const uint32_t m = __umulhi(v[w], n32);
-            okg[w] = (g * 4 + w < A.neg) && (m != i32);
-            yg[w] = okg[w] ? Yb[m] : yi;
+            for (int w = 0; w < 4; ++w) {
+                const uint32_t m = __umulhi(v[w], n32);
+                const bool ok = (g * 4 + w < neg) && (m != i32);
+                yg[w] = ok ? Yb[m] : yi;
+            }
+#pragma unroll
+            for (int w = 0; w < 4; ++w) repel(yg[w]);
         }
-#pragma unroll
-        for (int w = 0; w < 4; ++w)
-            if (okg[w]) repel(yg[w]);
     }
     return make_float2(gx, gy);
 }
 
-// Row blocks are handed out dynamically (one atomic per block from a counter
-// that the last CTA to finish resets), so no SM idles while others still hold
-// several blocks; which warp takes a block does not change any result.
-//
-// One warp owns a block of EPOCH_ROWS consecutive head rows.  Its lanes scan
-// the block's CSR entries 32 at a time (coalesced q loads), test the schedule,
-// and append the active entries to a per-warp queue in shared memory; each
-// time 32 are queued, every lane computes the force of one queued entry, so
-// all lanes work although only about a quarter of the entries fire in an
-// epoch.  The lane that owns a row then adds that row's forces in entry order,
-// which makes each row's sum independent of how entries fell into batches.
-template <int EPOCH_ROWS, int Q_PREFETCH, bool DYNAMIC>
-__global__ void __launch_bounds__(EPOCH_WARPS * 32, 4)
-embed_epoch_kernel(EpochArgs A) {
-    __shared__ int32_t s_rp[EPOCH_WARPS][EPOCH_ROWS + 1];
-    __shared__ float2 s_y[EPOCH_WARPS][EPOCH_ROWS];
-    __shared__ int32_t s_qe[EPOCH_WARPS][QCAP];
-    __shared__ int32_t s_qh[EPOCH_WARPS][QCAP];
-    __shared__ float2 s_term[EPOCH_WARPS][32];
-    __shared__ int32_t s_seg[EPOCH_WARPS][32];   // per owner row: first queue slot | count << 8
-    __shared__ RowInst s_inst[EPOCH_WARPS][EPOCH_ROWS];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    const float two_ab = 2.0f * A.a * A.b, two_b = 2.0f * A.b;
-    const uint64_t t0 = A.t, t1 = uint64_t(A.t) + 1;
-    const int64_t n_blocks = (A.n - A.row_begin + EPOCH_ROWS - 1) / EPOCH_ROWS;
-    int64_t rb_static = int64_t(blockIdx.x) * EPOCH_WARPS + w;
-    for (;;) {
-        int64_t rb = 0;
-        if (DYNAMIC) {
-            if (lane == 0) rb = atomicAdd(A.work, 1u);
-            rb = __shfl_sync(FULL, rb, 0);
-        } else {
-            rb = rb_static;
-            rb_static += int64_t(gridDim.x) * EPOCH_WARPS;
-        }
-        if (rb >= n_blocks) break;
-        const int64_t r0 = A.row_begin + rb * EPOCH_ROWS;
-        const int nr = int(A.n - r0 < EPOCH_ROWS ? A.n - r0 : EPOCH_ROWS);
-        if (lane <= nr) s_rp[w][lane] = A.row_ptr[r0 - A.row_begin + lane];
-        if (lane < nr) {
-            s_y[w][lane] = A.Y_in[r0 + lane];
-            RowInst R{0, A.neg_n ? A.neg_n : uint32_t(A.n), 0, A.k0, A.k1};
-            if (A.count > 0) {
-                const int64_t i = r0 + lane;
-                int lo = 0, hi = A.count - 1;  // instance b with inst_off[b] <= i
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (A.inst_off[mid] <= i) lo = mid; else hi = mid - 1;
-                }
-                R.off = A.inst_off[lo];
-                R.n = uint32_t(A.inst_off[lo + 1] - R.off);
-                R.eoff = A.row_ptr[R.off];
-                R.k0 = uint32_t(A.inst_seed[lo]);
-                R.k1 = uint32_t(A.inst_seed[lo] >> 32);
-            }
-            s_inst[w][lane] = R;
-        }
-        __syncwarp();
-        const int32_t e_begin = s_rp[w][0], e_end = s_rp[w][nr];
-        float ax = 0.f, ay = 0.f;
-        int qn = 0;
 
-        auto process = [&](int cnt) {
-            float2 f = make_float2(0.f, 0.f);
-            const int h = lane < cnt ? s_qh[w][lane] : -1 - lane;
-            if (lane < cnt) f = entry_force(A, s_qe[w][lane], r0 + h, s_y[w][h], two_ab, two_b, s_inst[w][h]);
-            s_term[w][lane] = f;
-            s_seg[w][lane] = 0;
-            __syncwarp();
-            // queue slots are sorted by head: each head's slots are contiguous
-            const unsigned same = __match_any_sync(FULL, h);
-            if (lane < cnt && lane == __ffs(same) - 1) s_seg[w][h] = lane | (__popc(same) << 8);
-            __syncwarp();
-            const int seg = s_seg[w][lane];
-            for (int t = seg & 0xff, t_end = (seg & 0xff) + (seg >> 8); t < t_end; ++t) {
-                ax += s_term[w][t].x;
-                ay += s_term[w][t].y;
-            }
-            __syncwarp();
-        };
-
-        // fill the queue (scanning Q_PREFETCH chunks per step) until 32
-        // entries wait or the block is scanned, then process 32 (or the rest)
-        int32_t e_cur = e_begin;
-        for (;;) {
-            while (qn < 32 && e_cur < e_end) {
-                uint32_t qv[Q_PREFETCH];
-#pragma unroll
-                for (int c = 0; c < Q_PREFETCH; ++c) {
-                    const int32_t e = e_cur + 32 * c + lane;
-                    qv[c] = e < e_end ? A.q[e] : 0u;  // q = 0 never fires
-                }
-#pragma unroll
-                for (int c = 0; c < Q_PREFETCH; ++c) {
-                    const int32_t e = e_cur + 32 * c + lane;
-                    const uint32_t qe = qv[c];
-                    const bool act = ((t1 * qe) >> 24) != ((t0 * qe) >> 24);
-                    const unsigned mask = __ballot_sync(FULL, act);
-                    if (act) {
-                        int lo = 0, hi = nr - 1;  // last row h with s_rp[h] <= e
-                        while (lo < hi) {
-                            const int mid = (lo + hi + 1) >> 1;
-                            if (s_rp[w][mid] <= e) lo = mid; else hi = mid - 1;
-                        }
-                        const int pos = qn + __popc(mask & lt_mask);
-                        s_qe[w][pos] = e;
-                        s_qh[w][pos] = lo;
-                    }
-                    qn += __popc(mask);
-                }
-                e_cur += 32 * Q_PREFETCH;
-                __syncwarp();
-            }
-            if (qn == 0) break;
-            const int cnt = qn < 32 ? qn : 32;
-            process(cnt);
-            for (int t = lane; t < qn - cnt; t += 32) {
-                const int32_t qe = s_qe[w][t + cnt], qh = s_qh[w][t + cnt];
-                __syncwarp(__activemask());
-                s_qe[w][t] = qe;
-                s_qh[w][t] = qh;
-            }
-            qn -= cnt;
-            __syncwarp();
+// ------------------------------------------------------------------ per-call preparation
+// Head row of every CSR entry of rows [row_begin, n).  Entries not covered by
+// any row keep -1; a row whose bounds leave [0, nnz_cap] is reported.
+__global__ void epoch_heads_kernel(const int32_t* __restrict__ rp, int64_t n_rows, int64_t row_begin,
+                                   int64_t nnz_cap, int32_t* __restrict__ row_of, int* status) {
+    for (int64_t lr = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; lr < n_rows;
+         lr += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t beg = rp[lr], end = rp[lr + 1];
+        if (beg < 0 || end < beg || end > nnz_cap) {
+            report_status(status, DRGB_ERR_INVALID);
+            continue;
         }
-        if (lane < nr) {
-            const float2 yi = s_y[w][lane];
-            A.Y_out[r0 + lane] = make_float2(fmaf(A.lr, ax, yi.x), fmaf(A.lr, ay, yi.y));
-        }
-        __syncwarp();
+        const int32_t r = int32_t(row_begin + lr);
+        for (int32_t e = beg; e < end; ++e) row_of[e] = r;
     }
-    // the last CTA to finish resets the work counter for the next launch
-    if (!DYNAMIC) return;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(A.work + 1, 1u) == gridDim.x - 1) {
-            A.work[0] = 0;
-            A.work[1] = 0;
-            __threadfence();
+}
+
+// Entry offsets of the instances and their window counts.
+__global__ void epoch_instances_kernel(const int32_t* __restrict__ rp, const int64_t* __restrict__ inst_off,
+                                       int count, int32_t* __restrict__ inst_eoff, int32_t* __restrict__ win_cnt) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b <= count; b += gridDim.x * blockDim.x) {
+        inst_eoff[b] = rp[inst_off[b]];
+        if (b < count) {
+            const int32_t ne = rp[inst_off[b + 1]] - rp[inst_off[b]];
+            win_cnt[b] = ne > 0 ? (ne + EPOCH_WIN - 1) / EPOCH_WIN : 0;
         }
     }
 }
 
-int launch_epoch(Ctx* c, const EpochArgs& A, int rows, cudaStream_t st) {
-    const int threads = EPOCH_WARPS * 32;
-    if (rows <= 0) rows = c->epoch_rows;
-    const int64_t row_blocks = (A.n - A.row_begin + rows - 1) / rows;
-    const int blocks = grid_for(row_blocks, EPOCH_WARPS, c->num_sms * 4);
-    if (!A.work) return set_error(c, DRGB_ERR_INVALID, "epoch: no work counter");
-    const int pf = c->epoch_prefetch;
-    const bool dyn = c->epoch_dynamic != 0;
-#define DRGB_EPOCH_CASE(R, P)                                                           \
-    if (rows == R && pf == P) {                                                        \
-        if (dyn) embed_epoch_kernel<R, P, true><<<blocks, threads, 0, st>>>(A);        \
-        else embed_epoch_kernel<R, P, false><<<blocks, threads, 0, st>>>(A);           \
-        DRGB_CHECK_LAUNCH(c);                                                          \
-        return DRGB_OK;                                                                \
+size_t epoch_scratch_bytes(int64_t n, int64_t nnz_cap, int count) {
+    const int64_t win_cap = (nnz_cap + EPOCH_WIN - 1) / EPOCH_WIN + count;
+    size_t b = Carve::round(size_t(nnz_cap > 0 ? nnz_cap : 1) * 4) + Carve::round(size_t(n + win_cap + 1) * 16);
+    if (count > 0)
+        b += 3 * Carve::round(size_t(count + 1) * 4) + Carve::round(scan_scratch_elems(count) * 4);
+    return b + 1024;
+}
+
+int epoch_prepare(Ctx* c, const int32_t* rp, int64_t n, int64_t row_begin, int64_t nnz_cap, int count,
+                  const int64_t* inst_off, void* scratch, EpochScratch* es, cudaStream_t st) {
+    Carve cv(scratch);
+    es->nnz_cap = nnz_cap;
+    es->win_cap = (nnz_cap + EPOCH_WIN - 1) / EPOCH_WIN + count;
+    es->row_of = cv.take<int32_t>(size_t(nnz_cap > 0 ? nnz_cap : 1));
+    es->pieces = cv.take<float4>(size_t(n + es->win_cap + 1));
+    DRGB_CUDA(c, cudaMemsetAsync(es->row_of, 0xFF, size_t(nnz_cap > 0 ? nnz_cap : 1) * 4, st));
+    DRGB_CUDA(c, cudaMemsetAsync(es->pieces, 0, size_t(n + es->win_cap + 1) * 16, st));
+    const int64_t n_rows = n - row_begin;
+    if (n_rows > 0) {
+        epoch_heads_kernel<<<grid_for(n_rows, 256, c->num_sms * 8), 256, 0, st>>>(rp, n_rows, row_begin, nnz_cap,
+                                                                                 es->row_of, c->d_status);
+        DRGB_CHECK_LAUNCH(c);
     }
-    DRGB_EPOCH_CASE(4, 4)
-    DRGB_EPOCH_CASE(4, 8)
-    DRGB_EPOCH_CASE(8, 4)
-    DRGB_EPOCH_CASE(8, 8)
-    DRGB_EPOCH_CASE(8, 16)
-    DRGB_EPOCH_CASE(16, 4)
-    DRGB_EPOCH_CASE(16, 8)
-    DRGB_EPOCH_CASE(16, 16)
-    DRGB_EPOCH_CASE(31, 16)
-#undef DRGB_EPOCH_CASE
-    return set_error(c, DRGB_ERR_INVALID, "epoch: unsupported rows/prefetch combination %d/%d", rows, pf);
+    if (count > 0) {
+        es->inst_eoff = cv.take<int32_t>(count + 1);
+        int32_t* win_cnt = cv.take<int32_t>(count + 1);
+        es->win_base = cv.take<int32_t>(count + 1);
+        int32_t* tmp = cv.take<int32_t>(scan_scratch_elems(count));
+        epoch_instances_kernel<<<grid_for(count + 1, 256, c->num_sms), 256, 0, st>>>(rp, inst_off, count,
+                                                                                    es->inst_eoff, win_cnt);
+        DRGB_CHECK_LAUNCH(c);
+        int rc = exclusive_scan(c, win_cnt, es->win_base, count, tmp, st);
+        if (rc) return rc;
+    }
+    return DRGB_OK;
+}
+
+// ------------------------------------------------------------------ force kernel
+// One warp per window of EPOCH_WIN entries (grid-stride over windows).  Each
+// (row, window) pair that holds active entries gets one record,
+// pieces[row + window]: rows and windows both grow along the CSR, so the index
+// is unique, and it stays below n + windows.
+template <bool BATCHED, int NEG>
+__global__ void __launch_bounds__(256, 4) epoch_force_kernel(const __grid_constant__ EpochArgs A) {
+    // [warps][EPOCH_WIN] (entry, tail) and [warps][EPOCH_WIN] head of the window's active entries
+    extern __shared__ int2 s_active[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    int2* act_w = s_active + w * EPOCH_WIN;
+    int32_t* head_w = reinterpret_cast<int32_t*>(s_active + nw * EPOCH_WIN) + w * EPOCH_WIN;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const float two_ab = 2.0f * A.a * A.b, two_b = 2.0f * A.b;
+    int32_t nnz = 0, n_win = 0;
+    if (BATCHED) {
+        nnz = A.inst_eoff[A.count];
+        n_win = A.win_base[A.count];
+    } else {
+        nnz = A.row_ptr[A.n - A.row_begin];
+        n_win = (nnz + EPOCH_WIN - 1) / EPOCH_WIN;
+    }
+    if (nnz < 0 || nnz > A.nnz_cap || n_win > A.win_cap) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) report_status(A.status, DRGB_ERR_INVALID);
+        return;
+    }
+    const RowInst R1{0, A.neg_n ? A.neg_n : uint32_t(A.n), 0, A.k0, A.k1};
+    for (int32_t W = int32_t(blockIdx.x) * nw + w; W < n_win; W += int32_t(gridDim.x) * nw) {
+        RowInst R = R1;
+        int64_t h_lo = A.row_begin, h_hi = A.n;  // rows a head may take
+        int32_t ws, we;
+        if (BATCHED) {
+            int lo = 0, hi = A.count - 1;  // the instance whose windows hold W
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (A.win_base[mid] <= W) lo = mid; else hi = mid - 1;
+            }
+            const int32_t eoff = A.inst_eoff[lo];
+            ws = eoff + (W - A.win_base[lo]) * EPOCH_WIN;
+            we = min(ws + EPOCH_WIN, A.inst_eoff[lo + 1]);
+            R.off = A.inst_off[lo];
+            R.n = uint32_t(A.inst_off[lo + 1] - R.off);
+            R.eoff = eoff;
+            R.k0 = uint32_t(A.inst_seed[lo]);
+            R.k1 = uint32_t(A.inst_seed[lo] >> 32);
+            h_lo = R.off;
+            h_hi = R.off + R.n;
+        } else {
+            ws = W * EPOCH_WIN;
+            we = min(ws + EPOCH_WIN, nnz);
+        }
+        // compaction, in entry order: the window's q, col and heads are loaded
+        // LD chunks of 32 at a time (coalesced; the whole window in one round
+        // trip for a single instance), then tested and appended
+        constexpr int LD = BATCHED ? 8 : 16;
+        int qn = 0;
+#pragma unroll
+        for (int s0 = 0; s0 < EPOCH_WIN / 32; s0 += LD) {
+            uint32_t qv[LD];
+            int32_t jv[LD], hv[LD];
+#pragma unroll
+            for (int s = 0; s < LD; ++s) {
+                const int32_t e = ws + 32 * (s0 + s) + lane;
+                const bool in = e < we;
+                qv[s] = in ? A.q[e] : 0u;  // q = 0 never fires
+                jv[s] = in ? A.col[e] : 0;
+                hv[s] = in ? A.row_of[e] : -1;
+            }
+#pragma unroll
+            for (int s = 0; s < LD; ++s) {
+                // floor((t+1) q / 2^24) > floor(t q / 2^24)  <=>  (t q mod 2^24) + q >= 2^24
+                const bool act = qv[s] >= 0x1000000u - ((A.t * qv[s]) & 0xFFFFFFu);
+                const unsigned m = __ballot_sync(FULL, act);
+                if (act) {
+                    const int pos = qn + __popc(m & lt_mask);
+                    act_w[pos] = make_int2(ws + 32 * (s0 + s) + lane, jv[s]);
+                    head_w[pos] = hv[s];
+                }
+                qn += __popc(m);
+            }
+        }
+        __syncwarp();
+        // groups of 32 active entries; (cx, cy) carries the running window sum
+        // of the previous group's last head
+        float cx = 0.f, cy = 0.f;
+        int32_t chead = -1;
+        for (int g0 = 0; g0 < qn; g0 += 32) {
+            const int cnt = qn - g0 < 32 ? qn - g0 : 32;
+            int32_t e = 0, j = 0, i = -1;
+            if (lane < cnt) {
+                const int2 ej = act_w[g0 + lane];
+                e = ej.x;
+                j = ej.y;
+                i = head_w[g0 + lane];
+            }
+            const bool ok = lane < cnt && i >= h_lo && i < h_hi;
+            if (lane < cnt && !ok) report_status(A.status, DRGB_ERR_INVALID);
+            float fx = 0.f, fy = 0.f;
+            if (ok) {
+                const float2 f = entry_force<NEG, BATCHED>(A, e, j, i, A.Y_in[i], two_ab, two_b, R);
+                fx = f.x;
+                fy = f.y;
+            } else {
+                i = -1 - lane;  // a head of its own, never written
+            }
+            // the carried head ends unless this group starts with it
+            if (chead >= 0 && lane == 0 && i != chead)
+                A.pieces[int64_t(chead) + W] = make_float4(cx, cy, 1.0f, 0.f);
+            // segmented inclusive scan over runs of equal heads
+            const int32_t i_prev = __shfl_up_sync(FULL, i, 1);
+            const unsigned starts = __ballot_sync(FULL, lane == 0 || i_prev != i);
+            const int seg0 = 31 - __clz(starts & (FULL >> (31 - lane)));
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const float ox = __shfl_up_sync(FULL, fx, d), oy = __shfl_up_sync(FULL, fy, d);
+                if (lane - d >= seg0) {
+                    fx = ox + fx;
+                    fy = oy + fy;
+                }
+            }
+            if (seg0 == 0 && i == chead) {
+                fx = cx + fx;
+                fy = cy + fy;
+            }
+            const int32_t i_next = __shfl_down_sync(FULL, i, 1);
+            const bool last = lane == cnt - 1;
+            const bool more = g0 + 32 < qn;
+            if (ok && (last ? !more : i_next != i)) A.pieces[int64_t(i) + W] = make_float4(fx, fy, 1.0f, 0.f);
+            cx = __shfl_sync(FULL, fx, cnt - 1);
+            cy = __shfl_sync(FULL, fy, cnt - 1);
+            chead = __shfl_sync(FULL, i, cnt - 1);
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ update kernel
+// Row r adds its window records in window order and writes Y'_r; each record
+// read is marked consumed (z = 0) for the next epoch.
+template <bool BATCHED>
+__global__ void epoch_update_kernel(const __grid_constant__ EpochArgs A) {
+    for (int64_t r = A.row_begin + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < A.n;
+         r += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t lr = r - A.row_begin;
+        const int32_t beg = A.row_ptr[lr], end = A.row_ptr[lr + 1];
+        float ax = 0.f, ay = 0.f;
+        if (beg >= 0 && end > beg) {
+            int64_t w0, w1;
+            if (BATCHED) {
+                int lo = 0, hi = A.count - 1;  // instance of row r
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (A.inst_off[mid] <= r) lo = mid; else hi = mid - 1;
+                }
+                const int32_t eoff = A.inst_eoff[lo];
+                w0 = A.win_base[lo] + (beg - eoff) / EPOCH_WIN;
+                w1 = A.win_base[lo] + (end - 1 - eoff) / EPOCH_WIN;
+            } else {
+                w0 = beg / EPOCH_WIN;
+                w1 = (end - 1) / EPOCH_WIN;
+            }
+            if (w0 < 0 || w1 >= A.win_cap) {
+                report_status(A.status, DRGB_ERR_INVALID);
+                w1 = w0 - 1;
+            }
+            for (int64_t W = w0; W <= w1; ++W) {
+                float4* p = A.pieces + r + W;
+                const float4 v = *p;
+                if (v.z != 0.f) {
+                    ax += v.x;
+                    ay += v.y;
+                    p->z = 0.f;
+                }
+            }
+        }
+        const float2 y = A.Y_in[r];
+        A.Y_out[r] = make_float2(fmaf(A.lr, ax, y.x), fmaf(A.lr, ay, y.y));
+    }
+}
+
+bool epoch_warps_supported(int warps) { return warps == 4 || warps == 8; }
+
+int launch_epoch(Ctx* c, const EpochArgs& A_in, int warps, cudaStream_t st) {
+    if (warps <= 0) warps = c->epoch_warps;
+    if (!epoch_warps_supported(warps))
+        return set_error(c, DRGB_ERR_INVALID, "epoch: unsupported force-kernel width %d", warps);
+    if (!A_in.row_of || !A_in.pieces) return set_error(c, DRGB_ERR_INVALID, "epoch: state not prepared");
+    EpochArgs A = A_in;
+    philox_round_keys(A.k0, A.k1, A.rk);
+    const int threads = warps * 32;
+    const size_t smem = size_t(warps) * EPOCH_WIN * (sizeof(int2) + sizeof(int32_t));
+    const int fgrid = grid_for(A.win_cap, warps, c->num_sms * (32 / warps));
+    const bool bat = A.count > 0, n5 = A.neg == 5;
+    if (bat) {
+        if (n5) epoch_force_kernel<true, 5><<<fgrid, threads, smem, st>>>(A);
+        else epoch_force_kernel<true, -1><<<fgrid, threads, smem, st>>>(A);
+    } else {
+        if (n5) epoch_force_kernel<false, 5><<<fgrid, threads, smem, st>>>(A);
+        else epoch_force_kernel<false, -1><<<fgrid, threads, smem, st>>>(A);
+    }
+    DRGB_CHECK_LAUNCH(c);
+    const int ugrid = grid_for(A.n - A.row_begin, 256, c->num_sms * 8);
+    if (bat) epoch_update_kernel<true><<<ugrid, 256, 0, st>>>(A);
+    else epoch_update_kernel<false><<<ugrid, 256, 0, st>>>(A);
+    DRGB_CHECK_LAUNCH(c);
+    return DRGB_OK;
 }
 
 int launch_init_batched(Ctx* c, float2* Y, int64_t n_total, float range, int count,
@@ -328,19 +456,47 @@ int launch_init(Ctx* c, float2* Y, int64_t n, float range, uint64_t seed, cudaSt
     return DRGB_OK;
 }
 
+static void fill_args(EpochArgs& A, const int32_t* rp, const int32_t* col, const uint32_t* q, int64_t n, float a,
+                      float b, int neg, uint64_t seed, int* status, const EpochScratch& es, int count,
+                      const int64_t* inst_off, const uint64_t* inst_seed, int64_t row_begin, uint32_t neg_n) {
+    A.row_ptr = rp;
+    A.col = col;
+    A.q = q;
+    A.n = n;
+    A.a = a;
+    A.b = b;
+    A.neg = neg;
+    A.k0 = uint32_t(seed);
+    A.k1 = uint32_t(seed >> 32);
+    A.status = status;
+    A.row_of = es.row_of;
+    A.pieces = es.pieces;
+    A.nnz_cap = es.nnz_cap;
+    A.win_cap = es.win_cap;
+    A.count = count;
+    A.inst_off = inst_off;
+    A.inst_seed = inst_seed;
+    A.inst_eoff = es.inst_eoff;
+    A.win_base = es.win_base;
+    A.row_begin = row_begin;
+    A.neg_n = neg_n;
+}
+
 // Epochs [t_begin, t_end) of a T-epoch schedule, ping-ponging between Y and
 // Y_tmp; the result is left in Y.  The launches are captured once into a CUDA
 // graph (on a private stream) and the graph is launched on `st`.
-int run_epochs(Ctx* c, float2* Y, float2* Y_tmp, const int32_t* rp, const int32_t* col,
-               const uint32_t* q, int64_t n, float a, float b, float lr0, int neg, int t_begin,
-               int t_end, int T, uint64_t seed, int rows_per_warp, cudaStream_t st, int count,
-               const int64_t* inst_off, const uint64_t* inst_seed, int64_t row_begin, uint32_t neg_n) {
+int run_epochs(Ctx* c, float2* Y, float2* Y_tmp, const int32_t* rp, const int32_t* col, const uint32_t* q,
+               int64_t n, float a, float b, float lr0, int neg, int t_begin, int t_end, int T, uint64_t seed,
+               cudaStream_t st, int64_t nnz_cap, void* scratch, int count, const int64_t* inst_off,
+               const uint64_t* inst_seed, int64_t row_begin, uint32_t neg_n) {
     if (t_end <= t_begin) return DRGB_OK;
+    EpochScratch es;
+    int rc = epoch_prepare(c, rp, n, row_begin, nnz_cap, count, inst_off, scratch, &es, st);
+    if (rc) return rc;
     cudaStream_t cap;
     DRGB_CUDA(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    int rc = DRGB_OK;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
         cudaStreamDestroy(cap);
@@ -350,27 +506,12 @@ int run_epochs(Ctx* c, float2* Y, float2* Y_tmp, const int32_t* rp, const int32_
     float2* dst = Y_tmp;
     for (int t = t_begin; t < t_end && rc == DRGB_OK; ++t) {
         EpochArgs A;
+        fill_args(A, rp, col, q, n, a, b, neg, seed, c->d_status, es, count, inst_off, inst_seed, row_begin, neg_n);
         A.Y_in = src;
         A.Y_out = dst;
-        A.row_ptr = rp;
-        A.col = col;
-        A.q = q;
-        A.n = n;
-        A.a = a;
-        A.b = b;
         A.lr = float(double(lr0) * (1.0 - double(t) / double(T)));
-        A.neg = neg;
         A.t = uint32_t(t);
-        A.k0 = uint32_t(seed);
-        A.k1 = uint32_t(seed >> 32);
-        A.status = c->d_status;
-        A.work = c->d_work;
-        A.count = count;
-        A.inst_off = inst_off;
-        A.inst_seed = inst_seed;
-        A.row_begin = row_begin;
-        A.neg_n = neg_n;
-        rc = launch_epoch(c, A, rows_per_warp, cap);
+        rc = launch_epoch(c, A, 0, cap);
         float2* tmp = src;
         src = dst;
         dst = tmp;
@@ -396,6 +537,55 @@ int run_epochs(Ctx* c, float2* Y, float2* Y_tmp, const int32_t* rp, const int32_
     return rc;
 }
 
+// Force-kernel widths tried by the tuner.
+static const int kWarpChoices[] = {4, 8};
+
+int autotune_epoch(Ctx* c, const float2* Y, float2* Ya, float2* Yb, const int32_t* rp, const int32_t* col,
+                   const uint32_t* q, int64_t n, float a, float b, int neg, int T, uint64_t seed, int trials,
+                   cudaStream_t st, const EpochScratch& es, int count, const int64_t* inst_off,
+                   const uint64_t* inst_seed, float* best_us) {
+    cudaEvent_t e0, e1;
+    DRGB_CUDA(c, cudaEventCreate(&e0));
+    DRGB_CUDA(c, cudaEventCreate(&e1));
+    int best_w = c->epoch_warps, rc = DRGB_OK;
+    float best = 1e30f;
+    const int t0 = T / 4 < T - trials ? T / 4 : (T - trials > 0 ? T - trials : 0);
+    for (int warps : kWarpChoices) {
+        EpochArgs A;
+        fill_args(A, rp, col, q, n, a, b, neg, seed, c->d_status, es, count, inst_off, inst_seed, 0, 0);
+        if (cudaMemcpyAsync(Ya, Y, size_t(n) * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+            rc = set_error(c, DRGB_ERR_CUDA, "autotune: copy failed");
+            break;
+        }
+        float ms = 0.f;
+        for (int pass = 0; pass < 2 && rc == DRGB_OK; ++pass) {  // pass 0 warms up
+            cudaEventRecord(e0, st);
+            for (int k = 0; k < trials && rc == DRGB_OK; ++k) {
+                A.Y_in = (k & 1) ? Yb : Ya;
+                A.Y_out = (k & 1) ? Ya : Yb;
+                A.t = uint32_t(t0 + k);
+                A.lr = 1.0f - float(t0 + k) / float(T);
+                rc = launch_epoch(c, A, warps, st);
+            }
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = set_error(c, DRGB_ERR_CUDA, "autotune: sync failed");
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (rc) break;
+        const float us = ms * 1000.f / trials;
+        if (us < best) {
+            best = us;
+            best_w = warps;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    c->epoch_warps = best_w;
+    if (best_us) *best_us = best;
+    return DRGB_OK;
+}
+
 }  // namespace drgb
 
 using namespace drgb;
@@ -418,9 +608,22 @@ static int check_epoch_args(drgb_ctx* c, const float* Y_in, const float* Y_out, 
     if (Y_in == Y_out) return set_error(c, DRGB_ERR_INVALID, "embed_epoch: Y_out aliases Y_in");
     if (!aligned(Y_in, 8) || !aligned(Y_out, 8))
         return set_error(c, DRGB_ERR_INVALID, "embed_epoch: Y must be 8-byte aligned");
+    if (!aligned(rp, 4) || !aligned(col, 4) || !aligned(q, 4))
+        return set_error(c, DRGB_ERR_INVALID, "embed_epoch: CSR arrays must be 4-byte aligned");
     if (n < 1 || n > INT32_MAX) return set_error(c, DRGB_ERR_INVALID, "embed_epoch: bad n");
     if (neg < 0 || neg > 64) return set_error(c, DRGB_ERR_INVALID, "embed_epoch: neg out of range");
     return DRGB_OK;
+}
+
+// Entry count row_ptr[n] (read back to size the per-call state) and that state.
+static int epoch_state_for(drgb_ctx* c, const int32_t* rp, int64_t n, cudaStream_t st, EpochScratch* es) {
+    int32_t nnz = 0;
+    DRGB_CUDA(c, cudaMemcpyAsync(&nnz, rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    DRGB_CUDA(c, cudaStreamSynchronize(st));
+    if (nnz < 0) return set_error(c, DRGB_ERR_INVALID, "embed_epoch: row_ptr[n] < 0");
+    int rc = ensure_scratch(c, epoch_scratch_bytes(n, nnz, 0), st);
+    if (rc) return rc;
+    return epoch_prepare(c, rp, n, 0, nnz, 0, nullptr, c->scratch, es, st);
 }
 
 int drgb_embed_epoch(drgb_ctx* c, const float* Y_in, float* Y_out, const int32_t* row_ptr,
@@ -429,23 +632,16 @@ int drgb_embed_epoch(drgb_ctx* c, const float* Y_in, float* Y_out, const int32_t
     int rc = check_epoch_args(c, Y_in, Y_out, row_ptr, col, q, n, neg);
     if (rc) return rc;
     if (epoch < 0) return set_error(c, DRGB_ERR_INVALID, "embed_epoch: epoch < 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    EpochScratch es;
+    if ((rc = epoch_state_for(c, row_ptr, n, st, &es))) return rc;
     EpochArgs A;
+    fill_args(A, row_ptr, col, q, n, a, b, neg, seed, c->d_status, es, 0, nullptr, nullptr, 0, 0);
     A.Y_in = reinterpret_cast<const float2*>(Y_in);
     A.Y_out = reinterpret_cast<float2*>(Y_out);
-    A.row_ptr = row_ptr;
-    A.col = col;
-    A.q = q;
-    A.n = n;
-    A.a = a;
-    A.b = b;
     A.lr = lr;
-    A.neg = neg;
     A.t = uint32_t(epoch);
-    A.k0 = uint32_t(seed);
-    A.k1 = uint32_t(seed >> 32);
-    A.status = c->d_status;
-    A.work = c->d_work;
-    return launch_epoch(c, A, 0, static_cast<cudaStream_t>(stream));
+    return launch_epoch(c, A, 0, st);
 }
 
 int drgb_embed_epochs(drgb_ctx* c, float* Y, float* Y_tmp, const int32_t* row_ptr,
@@ -456,9 +652,14 @@ int drgb_embed_epochs(drgb_ctx* c, float* Y, float* Y_tmp, const int32_t* row_pt
     if (rc) return rc;
     if (!(0 <= t_begin && t_begin <= t_end && t_end <= n_epochs) || n_epochs < 1)
         return set_error(c, DRGB_ERR_INVALID, "embed_epochs: bad epoch range");
-    return run_epochs(c, reinterpret_cast<float2*>(Y), reinterpret_cast<float2*>(Y_tmp), row_ptr,
-                      col, q, n, a, b, lr0, neg, t_begin, t_end, n_epochs, seed, 0,
-                      static_cast<cudaStream_t>(stream));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int32_t nnz = 0;
+    DRGB_CUDA(c, cudaMemcpyAsync(&nnz, row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    DRGB_CUDA(c, cudaStreamSynchronize(st));
+    if (nnz < 0) return set_error(c, DRGB_ERR_INVALID, "embed_epochs: row_ptr[n] < 0");
+    if ((rc = ensure_scratch(c, epoch_scratch_bytes(n, nnz, 0), st))) return rc;
+    return run_epochs(c, reinterpret_cast<float2*>(Y), reinterpret_cast<float2*>(Y_tmp), row_ptr, col, q, n, a,
+                      b, lr0, neg, t_begin, t_end, n_epochs, seed, st, nnz, c->scratch);
 }
 
 }  // extern "C"

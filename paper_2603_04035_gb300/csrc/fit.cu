@@ -19,12 +19,14 @@ struct FitBuffers {
     float2* Y_tmp;
     float2* Y_tune;
     void* fuzzy_scratch;
+    void* epoch_scratch;
 };
 
 static size_t fit_bytes(int64_t n, int k) {
     const size_t nk = size_t(n) * k;
     return Carve::round(nk * 4) * 2 + Carve::round((n + 1) * 4) + Carve::round(2 * nk * 4) * 3 +
-           Carve::round(n * 8) * 2 + Carve::round(fuzzy_scratch_bytes(n, k)) + 4096;
+           Carve::round(n * 8) * 2 + Carve::round(fuzzy_scratch_bytes(n, k)) +
+           Carve::round(epoch_scratch_bytes(n, int64_t(2 * nk), 0)) + 4096;
 }
 
 // Fit buffers first, then the k-NN scratch region (disjoint from them).
@@ -41,6 +43,7 @@ static FitBuffers carve_fit(void* base, int64_t n, int k) {
     b.Y_tmp = cv.take<float2>(n);
     b.Y_tune = cv.take<float2>(n);
     b.fuzzy_scratch = cv.take<char>(fuzzy_scratch_bytes(n, k));
+    b.epoch_scratch = cv.take<char>(epoch_scratch_bytes(n, int64_t(2 * nk), 0));
     return b;
 }
 
@@ -86,21 +89,24 @@ extern "C" int drgb_fit_transform(drgb_ctx* c, const float* X, int64_t n, int32_
     float2* Y = reinterpret_cast<float2*>(Y_out);
     rc = launch_init(c, Y, n, p->init_range, p->seed_init, st);
     if (rc) return rc;
+    const int64_t nnz_cap = int64_t(2) * n * k;
     if (p->flags & DRGB_FLAG_AUTOTUNE) {
         float us = 0.f;
+        EpochScratch es;
+        if ((rc = epoch_prepare(c, b.row_ptr, n, 0, nnz_cap, 0, nullptr, b.epoch_scratch, &es, st))) return rc;
         rc = autotune_epoch(c, Y, b.Y_tune, b.Y_tmp, b.row_ptr, b.col, b.q, n, a, bb, p->neg, p->n_epochs,
-                            p->seed_neg, 3, st, 0, nullptr, nullptr, &us);
+                            p->seed_neg, 3, st, es, 0, nullptr, nullptr, &us);
         if (rc) return rc;
     }
     if ((rc = stage_mark(c, 3, st))) return rc;
     if (!cb) {
         rc = run_epochs(c, Y, b.Y_tmp, b.row_ptr, b.col, b.q, n, a, bb, p->lr0, p->neg, 0, p->n_epochs,
-                        p->n_epochs, p->seed_neg, 0, st);
+                        p->n_epochs, p->seed_neg, st, nnz_cap, b.epoch_scratch);
         if (rc) return rc;
     } else {
         for (int t = 0; t < p->n_epochs; ++t) {
             rc = run_epochs(c, Y, b.Y_tmp, b.row_ptr, b.col, b.q, n, a, bb, p->lr0, p->neg, t, t + 1,
-                            p->n_epochs, p->seed_neg, 0, st);
+                            p->n_epochs, p->seed_neg, st, nnz_cap, b.epoch_scratch);
             if (rc) return rc;
             rc = drgb_sync(c, stream);
             if (rc) return rc;

@@ -60,7 +60,7 @@ extern "C" int drgb_transform(drgb_ctx* c, const float* X_train, const float* Y_
     const int64_t N = n_train + n_new;
     const size_t nk = size_t(n_new) * k;
     const size_t bytes = 4 * Carve::round(nk * 4) + Carve::round(nk * 4) + Carve::round((n_new + 1) * 4) +
-                         2 * Carve::round(size_t(N) * 8) + 4096;
+                         2 * Carve::round(size_t(N) * 8) + Carve::round(epoch_scratch_bytes(N, int64_t(nk), 0)) + 4096;
     int rc = ensure_scratch(c, bytes, st);
     if (rc) return rc;
     Carve cv(c->scratch);
@@ -73,6 +73,7 @@ extern "C" int drgb_transform(drgb_ctx* c, const float* X_train, const float* Y_
     int32_t* rp = cv.take<int32_t>(n_new + 1);
     float2* Ya = cv.take<float2>(N);
     float2* Yb = cv.take<float2>(N);
+    void* ep = cv.take<char>(epoch_scratch_bytes(N, int64_t(nk), 0));
 
     float a = 0.f, b = 0.f;
     if ((rc = drgb_find_ab(p->spread, p->min_dist, &a, &b))) return set_error(c, rc, "bad spread/min_dist");
@@ -86,8 +87,8 @@ extern "C" int drgb_transform(drgb_ctx* c, const float* X_train, const float* Y_
     arange_kernel<<<grid_for(n_new + 1, 256, c->num_sms * 8), 256, 0, st>>>(rp, n_new, k);
     DRGB_CHECK_LAUNCH(c);
     const int T3 = (p->n_epochs + 2) / 3;
-    rc = run_epochs(c, Ya, Yb, rp, out_col, q, N, a, b, p->lr0, p->neg, 0, T3, T3, p->seed_neg, 0, st, 0, nullptr,
-                    nullptr, n_train, uint32_t(n_train));
+    rc = run_epochs(c, Ya, Yb, rp, out_col, q, N, a, b, p->lr0, p->neg, 0, T3, T3, p->seed_neg, st, int64_t(nk), ep,
+                    0, nullptr, nullptr, n_train, uint32_t(n_train));
     if (rc) return rc;
     DRGB_CUDA(c, cudaMemcpyAsync(Y_new, Ya + n_train, size_t(n_new) * 8, cudaMemcpyDeviceToDevice, st));
     return drgb_sync(c, stream);

@@ -68,7 +68,7 @@ def test_autotune_returns_a_supported_choice(drgb):
     Y = drgb.init_embedding(5000, 10.0, 1)
     Y0 = Y.clone()
     choice, us = drgb.autotune_epoch(Y, g, 1.577, 0.895, trials=2)
-    assert choice[0] in (4, 8, 16, 31) and choice[1] in (4, 8, 16) and choice[2] in (0, 1)
+    assert choice in (4, 8)
     assert us > 0 and torch.equal(Y, Y0)   # the caller's embedding is untouched
 
 

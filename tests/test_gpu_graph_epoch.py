@@ -210,3 +210,55 @@ def test_epoch_rejects_bad_arguments(drgb):
         drgb.embed_epoch(Y, g, 1.0, 1.0, 1.0, -1, 0, 0)              # negative neg
     with pytest.raises(drgb.DrgbError):
         drgb.embed_epochs(Y, g, 1.0, 1.0, 1.0, 5, 10, 5, 50, 0)      # bad range
+
+
+def _star_graph(n_hub=3000, n_empty=100, seed=1):
+    """Row 0 has n_hub entries, rows 1..n_hub one entry each, then n_empty empty rows."""
+    n = n_hub + 1 + n_empty
+    heads = np.concatenate([np.zeros(n_hub, np.int64), np.arange(1, n_hub + 1)])
+    cols = np.concatenate([np.arange(1, n_hub + 1), np.zeros(n_hub, np.int64)])
+    order = np.lexsort((cols, heads))
+    heads, cols = heads[order], cols[order]
+    rp = np.zeros(n + 1, np.int64)
+    np.add.at(rp, heads + 1, 1)
+    q = np.random.default_rng(seed).integers(Q_ONE // 200, Q_ONE + 1, size=len(cols)).astype(np.uint64)
+    return n, np.cumsum(rp), cols, q
+
+
+@pytest.mark.parametrize("graph", ["mixture", "star"])
+def test_epoch_every_tuning_choice_is_bit_identical(drgb, graph):
+    """The force-kernel width changes the speed only: every choice must give
+    the same bits, and those bits must stay within the oracle tolerance."""
+    import torch
+    from paper_2603_04035_gb300 import _lib
+    if graph == "mixture":
+        X, o = _oracle_graph(2000, 15, 200, 0)
+        n, rp, col, q = 2000, o["row_ptr"], o["col"], o["q"]
+    else:
+        n, rp, col, q = _star_graph()
+    g = _graph_tensors(drgb, rp, col, q)
+    Y = np.random.default_rng(5).uniform(-10, 10, size=(n, 2)).astype(np.float32)
+    Yd = _t(Y)
+    saved = drgb.get_tuning(_lib.TUNE_EPOCH_WARPS)
+    outs = {}
+    try:
+        for warps in (4, 8):
+            drgb.set_tuning(_lib.TUNE_EPOCH_WARPS, warps)
+            for neg in (5, 6):   # the fixed-count and the generic force paths
+                outs[(warps, neg)] = drgb.embed_epoch(Yd, g, 1.577, 0.895, 0.7, neg, 13, 4).clone()
+        torch.cuda.synchronize()
+    finally:
+        drgb.set_tuning(_lib.TUNE_EPOCH_WARPS, saved)
+    for neg in (5, 6):
+        assert torch.equal(outs[(4, neg)], outs[(8, neg)]), neg
+        ref = osgd.epoch(Y, rp, col, q.astype(np.uint64), 1.577, 0.895, 0.7, neg, 13, 4)
+        assert np.all(np.abs(_np(outs[(4, neg)]) - ref) <= epoch_tolerance(ref))
+
+
+def test_set_tuning_rejects_unsupported_values(drgb):
+    from paper_2603_04035_gb300 import _lib
+    for bad in (0, 2, 16, 32):
+        with pytest.raises(drgb.DrgbError):
+            drgb.set_tuning(_lib.TUNE_EPOCH_WARPS, bad)
+    with pytest.raises(drgb.DrgbError):
+        drgb.set_tuning(99, 4)
