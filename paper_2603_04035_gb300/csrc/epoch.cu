@@ -97,41 +97,64 @@ __device__ __forceinline__ U4 negative_words(const EpochArgs& A, const RowInst& 
 // Force on head i from one active entry e = (i, j) and its negatives, summed in
 // the fixed order: attraction, then negatives j' = 0 .. neg-1.  NEG is the
 // negative count when fixed at compile time (5, the method's default), or -1
-// for any count up to 64 (A.neg).  The first eight negatives are drawn before
-// any gather, so their loads and the Y_j load overlap; further negatives
-// follow in groups of four.
+// for any count up to 64 (A.neg).
+//
+// It is split in two so that a warp can gather one group's points while it
+// computes the previous group's forces: fetch_entry draws the first (up to
+// eight) negatives and issues the loads of Y_i, Y_j and Y_m; entry_math does
+// the arithmetic (and, for more than eight negatives, draws and gathers the
+// rest itself).
 //
 // A skipped negative (m = i) is evaluated with Y_m = Y_i: its difference vector
 // is zero, so it adds exactly +0 and needs no branch (a sum that starts at +0
 // never becomes -0).  A zero distance takes d^b = 0, so coincident points
 // repel with zero force as well.
+template <int NEG>
+struct EntryInputs {
+    static constexpr int NP = NEG >= 0 ? (NEG < 8 ? NEG : 8) : 8;  // negatives drawn with the fetch
+    float2 yi, yj;
+    float2 ym[NP > 0 ? NP : 1];
+    int32_t e;
+    int32_t i;   // head row; -1 - lane for a lane without a valid entry
+    bool ok;
+};
+
 template <int NEG, bool BATCHED>
-__device__ __forceinline__ float2 entry_force(const EpochArgs& A, int32_t e, int32_t j, int64_t i, float2 yi,
-                                              float two_ab, float two_b, const RowInst& R) {
-    constexpr int NP = NEG >= 0 ? (NEG < 8 ? NEG : 8) : 8;  // negatives drawn before the gathers
+__device__ __forceinline__ void fetch_entry(const EpochArgs& A, const RowInst& R, bool valid, int32_t e, int32_t j,
+                                            int32_t i, int64_t h_lo, int64_t h_hi, int lane,
+                                            EntryInputs<NEG>& in) {
+    constexpr int NP = EntryInputs<NEG>::NP;
     const int neg = NEG >= 0 ? NEG : A.neg;
-    const uint32_t n32 = R.n, i32 = uint32_t(i - R.off), e32 = uint32_t(e - R.eoff);
+    bool ok = valid && i >= h_lo && i < h_hi && uint64_t(uint32_t(j)) < uint64_t(A.n);
+    if (valid && !ok) report_status(A.status, DRGB_ERR_INVALID);  // malformed CSR: skip the entry
+    in.ok = ok;
+    in.e = e;
+    in.i = ok ? i : -1 - lane;
+    const int32_t ii = ok ? i : int32_t(h_lo);
+    in.yi = A.Y_in[ii];
+    in.yj = A.Y_in[ok ? j : ii];
+    const uint32_t n32 = R.n, i32 = uint32_t(ii - R.off), e32 = uint32_t(e - R.eoff);
     const float2* Yb = A.Y_in + R.off;
     U4 r0{0u, 0u, 0u, 0u}, r1{0u, 0u, 0u, 0u};
     if (NP > 0 && neg > 0) r0 = negative_words<BATCHED>(A, R, e32, 0u);
     if (NP > 4 && neg > 4) r1 = negative_words<BATCHED>(A, R, e32, 1u);
     const uint32_t u[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-    float2 ym[NP > 0 ? NP : 1];
 #pragma unroll
     for (int w = 0; w < NP; ++w) {
         const uint32_t m = __umulhi(u[w], n32);  // floor(u n / 2^32)
-        const bool ok = (NEG >= 0 || w < neg) && (m != i32);
-        ym[w] = ok ? Yb[m] : yi;
+        const bool take = ok && (NEG >= 0 || w < neg) && (m != i32);
+        in.ym[w] = Yb[take ? m : i32];           // a skipped negative reads Y_i
     }
-    const bool j_ok = uint64_t(uint32_t(j)) < uint64_t(A.n);
-    if (!j_ok) {  // malformed CSR: report and skip the entry
-        report_status(A.status, DRGB_ERR_INVALID);
-        return make_float2(0.f, 0.f);
-    }
-    const float2 yj = A.Y_in[j];
+}
+
+template <int NEG, bool BATCHED>
+__device__ __forceinline__ float2 entry_math(const EpochArgs& A, const RowInst& R, const EntryInputs<NEG>& in,
+                                             float two_ab, float two_b) {
+    constexpr int NP = EntryInputs<NEG>::NP;
+    const float2 yi = in.yi;
     float gx = 0.f, gy = 0.f;
     {
-        const float dx = yi.x - yj.x, dy = yi.y - yj.y;
+        const float dx = yi.x - in.yj.x, dy = yi.y - in.yj.y;
         const float d = fmaf(dx, dx, dy * dy);
         const float pb = d > 0.f ? pow_pos(d, A.b) : 0.f;
         const float c = d > 0.f ? __fdividef(-two_ab * pb, d * fmaf(A.a, pb, 1.0f)) : 0.f;
@@ -147,8 +170,11 @@ __device__ __forceinline__ float2 entry_force(const EpochArgs& A, int32_t e, int
         gy += clip4(c * ry);
     };
 #pragma unroll
-    for (int w = 0; w < NP; ++w) repel(ym[w]);
+    for (int w = 0; w < NP; ++w) repel(in.ym[w]);
     if (NEG < 0 || NEG > 8) {
+        const int neg = NEG >= 0 ? NEG : A.neg;
+        const uint32_t n32 = R.n, i32 = uint32_t(in.i - R.off), e32 = uint32_t(in.e - R.eoff);
+        const float2* Yb = A.Y_in + R.off;
         for (int g = 2; g * 4 < neg; ++g) {
             const U4 r = negative_words<BATCHED>(A, R, e32, uint32_t(g));
             const uint32_t v[4] = {r.x, r.y, r.z, r.w};
@@ -165,7 +191,6 @@ __device__ __forceinline__ float2 entry_force(const EpochArgs& A, int32_t e, int
     }
     return make_float2(gx, gy);
 }
-
 
 // ------------------------------------------------------------------ per-call preparation
 // Head row of every CSR entry of rows [row_begin, n).  Entries not covered by
@@ -239,7 +264,7 @@ int epoch_prepare(Ctx* c, const int32_t* rp, int64_t n, int64_t row_begin, int64
 // pieces[row + window]: rows and windows both grow along the CSR, so the index
 // is unique, and it stays below n + windows.
 template <bool BATCHED, int NEG>
-__global__ void __launch_bounds__(256, 4) epoch_force_kernel(const __grid_constant__ EpochArgs A) {
+__global__ void __launch_bounds__(256, 3) epoch_force_kernel(const __grid_constant__ EpochArgs A) {
     // [warps][EPOCH_WIN] (entry, tail) and [warps][EPOCH_WIN] head of the window's active entries
     extern __shared__ int2 s_active[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -315,29 +340,34 @@ __global__ void __launch_bounds__(256, 4) epoch_force_kernel(const __grid_consta
             }
         }
         __syncwarp();
-        // groups of 32 active entries; (cx, cy) carries the running window sum
-        // of the previous group's last head
+        // groups of 32 active entries, software-pipelined: the next group's
+        // negatives are drawn and its points gathered before this group's
+        // forces are computed.  (cx, cy) carries the running window sum of the
+        // previous group's last head.
         float cx = 0.f, cy = 0.f;
         int32_t chead = -1;
+        EntryInputs<NEG> cur, nxt;
+        {
+            const bool v = lane < qn;
+            const int2 ej = v ? act_w[lane] : make_int2(ws, 0);
+            fetch_entry<NEG, BATCHED>(A, R, v, ej.x, ej.y, v ? head_w[lane] : -1, h_lo, h_hi, lane, cur);
+        }
         for (int g0 = 0; g0 < qn; g0 += 32) {
             const int cnt = qn - g0 < 32 ? qn - g0 : 32;
-            int32_t e = 0, j = 0, i = -1;
-            if (lane < cnt) {
-                const int2 ej = act_w[g0 + lane];
-                e = ej.x;
-                j = ej.y;
-                i = head_w[g0 + lane];
+            if (g0 + 32 < qn) {
+                const bool v = g0 + 32 + lane < qn;
+                const int2 ej = v ? act_w[g0 + 32 + lane] : make_int2(ws, 0);
+                fetch_entry<NEG, BATCHED>(A, R, v, ej.x, ej.y, v ? head_w[g0 + 32 + lane] : -1, h_lo, h_hi, lane,
+                                          nxt);
             }
-            const bool ok = lane < cnt && i >= h_lo && i < h_hi;
-            if (lane < cnt && !ok) report_status(A.status, DRGB_ERR_INVALID);
             float fx = 0.f, fy = 0.f;
-            if (ok) {
-                const float2 f = entry_force<NEG, BATCHED>(A, e, j, i, A.Y_in[i], two_ab, two_b, R);
+            if (cur.ok) {
+                const float2 f = entry_math<NEG, BATCHED>(A, R, cur, two_ab, two_b);
                 fx = f.x;
                 fy = f.y;
-            } else {
-                i = -1 - lane;  // a head of its own, never written
             }
+            const int32_t i = cur.i;
+            const bool ok = cur.ok;
             // the carried head ends unless this group starts with it
             if (chead >= 0 && lane == 0 && i != chead)
                 A.pieces[int64_t(chead) + W] = make_float4(cx, cy, 1.0f, 0.f);
@@ -364,6 +394,7 @@ __global__ void __launch_bounds__(256, 4) epoch_force_kernel(const __grid_consta
             cx = __shfl_sync(FULL, fx, cnt - 1);
             cy = __shfl_sync(FULL, fy, cnt - 1);
             chead = __shfl_sync(FULL, i, cnt - 1);
+            cur = nxt;
         }
         __syncwarp();
     }
@@ -424,7 +455,7 @@ int launch_epoch(Ctx* c, const EpochArgs& A_in, int warps, cudaStream_t st) {
     philox_round_keys(A.k0, A.k1, A.rk);
     const int threads = warps * 32;
     const size_t smem = size_t(warps) * EPOCH_WIN * (sizeof(int2) + sizeof(int32_t));
-    const int fgrid = grid_for(A.win_cap, warps, c->num_sms * (32 / warps));
+    const int fgrid = grid_for(A.win_cap, warps, c->num_sms * (24 / warps));
     const bool bat = A.count > 0, n5 = A.neg == 5;
     if (bat) {
         if (n5) epoch_force_kernel<true, 5><<<fgrid, threads, smem, st>>>(A);

@@ -53,12 +53,21 @@ __device__ __forceinline__ void tile_distances(const float* __restrict__ X, int6
         float qv[DC];
 #pragma unroll
         for (int cc = 0; cc < DC; ++cc) qv[cc] = (qvalid && c0 + cc < d) ? Q[qi * d + c0 + cc] : 0.f;
-#pragma unroll 4
+        // fully unrolled so that acc stays in registers; dimensions are added
+        // in order (beyond d both sides are 0 and the fma leaves a unchanged)
+#pragma unroll
         for (int p = 0; p < TP; ++p) {
             float a = acc[p];
 #pragma unroll
-            for (int cc = 0; cc < DC; ++cc) {
-                const float df = qv[cc] - s_db[p * DC + cc];
+            for (int cc = 0; cc < DC; cc += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(&s_db[p * DC + cc]);
+                float df = qv[cc] - v.x;
+                a = fmaf(df, df, a);
+                df = qv[cc + 1] - v.y;
+                a = fmaf(df, df, a);
+                df = qv[cc + 2] - v.z;
+                a = fmaf(df, df, a);
+                df = qv[cc + 3] - v.w;
                 a = fmaf(df, df, a);
             }
             acc[p] = a;
@@ -126,12 +135,22 @@ knn_exact_kernel(const float* __restrict__ X, int64_t n, int d, int k,
 }
 
 // Merge the C partial k-lists (squared distances, ascending) of each listed
-// row into its final k nearest, ordered by (distance, index).
+// row into its final k nearest, ordered by (distance, index).  One warp per
+// row: lane l keeps the best K of the lists l, l + 32, ...; then k rounds each
+// take the warp-wide smallest head by (distance, index).  The chunks cover
+// disjoint index ranges, so no index appears twice.
+template <int K>
+__device__ __forceinline__ bool lex_less(float a, int32_t i, float b, int32_t j) {
+    return a < b || (a == b && i < j);
+}
+
 template <int K>
 __global__ void merge_partials_kernel(const int32_t* __restrict__ pidx, const float* __restrict__ pd2,
                                       int64_t cnt, int C, int k, const int32_t* __restrict__ rows32,
                                       int32_t* __restrict__ idx_out, float* __restrict__ dist_out) {
-    for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < cnt; r += int64_t(gridDim.x) * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t r = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); r < cnt; r += warps) {
         float D[K];
         int32_t I[K];
 #pragma unroll
@@ -139,30 +158,50 @@ __global__ void merge_partials_kernel(const int32_t* __restrict__ pidx, const fl
             D[s] = INFINITY;
             I[s] = INT32_MAX;
         }
-        for (int c = 0; c < C; ++c) {
+        for (int c = lane; c < C; c += 32) {
+            const int64_t base = (int64_t(c) * cnt + r) * k;
             for (int s = 0; s < k; ++s) {
-                const float a = pd2[(int64_t(c) * cnt + r) * k + s];
-                const int32_t j = pidx[(int64_t(c) * cnt + r) * k + s];
-                if (j < 0 || !(a < D[K - 1] || (a == D[K - 1] && j < I[K - 1]))) continue;
+                const float a = pd2[base + s];
+                const int32_t j = pidx[base + s];
+                if (j < 0 || !lex_less<K>(a, j, D[K - 1], I[K - 1])) break;  // each list is ascending
 #pragma unroll
                 for (int t = K - 1; t > 0; --t) {
-                    const bool shift = a < D[t - 1] || (a == D[t - 1] && j < I[t - 1]);
-                    const bool place = !shift && (a < D[t] || (a == D[t] && j < I[t]));
+                    const bool shift = lex_less<K>(a, j, D[t - 1], I[t - 1]);
+                    const bool place = !shift && lex_less<K>(a, j, D[t], I[t]);
                     D[t] = shift ? D[t - 1] : (place ? a : D[t]);
                     I[t] = shift ? I[t - 1] : (place ? j : I[t]);
                 }
-                if (a < D[0] || (a == D[0] && j < I[0])) {
+                if (lex_less<K>(a, j, D[0], I[0])) {
                     D[0] = a;
                     I[0] = j;
                 }
             }
         }
         const int64_t row = rows32[r];
+        for (int s = 0; s < k; ++s) {
+            float bd = D[0];
+            int32_t bi = I[0];
 #pragma unroll
-        for (int s = 0; s < K; ++s) {
-            if (s < k) {
-                idx_out[row * k + s] = I[s];
-                dist_out[row * k + s] = sqrtf(D[s]);
+            for (int o = 16; o > 0; o >>= 1) {
+                const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+                const int32_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (lex_less<K>(od, oi, bd, bi)) {
+                    bd = od;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                idx_out[row * k + s] = bi;
+                dist_out[row * k + s] = sqrtf(bd);
+            }
+            if (I[0] == bi && D[0] == bd) {  // the owner pops its head
+#pragma unroll
+                for (int t = 0; t < K - 1; ++t) {
+                    D[t] = D[t + 1];
+                    I[t] = I[t + 1];
+                }
+                D[K - 1] = INFINITY;
+                I[K - 1] = INT32_MAX;
             }
         }
     }
@@ -184,12 +223,13 @@ int launch_knn_exact_rows(Ctx* c, const float* X, int64_t n, int d, int k, const
     const int64_t cnt = cnt32 < max_rows ? cnt32 : max_rows;
     if (cnt <= 0) return DRGB_OK;
     const int row_blocks = int((cnt + KNN_THREADS - 1) / KNN_THREADS);
-    int C = (4 * c->num_sms + row_blocks - 1) / row_blocks;
-    const int64_t max_c = (n + 255) / 256;               // at least 256 points per chunk
-    if (C > max_c) C = int(max_c);
-    if (C > 64) C = 64;
-    const size_t need = 2 * Carve::round(size_t(cnt) * C * k * 4);
-    if (C <= 1 || part_scratch == nullptr || need > part_bytes) {
+    int64_t C = (8 * int64_t(c->num_sms) + row_blocks - 1) / row_blocks;
+    const int64_t max_c = (n + 127) / 128;               // at least 128 points per chunk
+    if (C > max_c) C = max_c;
+    if (C > 1024) C = 1024;
+    const int64_t fit_c = part_scratch ? int64_t(part_bytes / 2 / (size_t(cnt) * k * 4 + 256)) : 0;
+    if (C > fit_c) C = fit_c;                            // partial lists must fit the scratch
+    if (C <= 1) {
         const int blocks = row_blocks;
         if (k <= 16)
             knn_exact_kernel<16><<<blocks, KNN_THREADS, 0, st>>>(X, n, d, k, nullptr, cnt, idx_out, dist_out, 1,
@@ -204,7 +244,7 @@ int launch_knn_exact_rows(Ctx* c, const float* X, int64_t n, int d, int k, const
     int32_t* pidx = cv.take<int32_t>(size_t(cnt) * C * k);
     float* pd2 = cv.take<float>(size_t(cnt) * C * k);
     const int64_t chunk = (n + C - 1) / C;
-    dim3 grid(row_blocks, C);
+    dim3 grid(row_blocks, unsigned(C));
     if (k <= 16)
         knn_exact_kernel<16><<<grid, KNN_THREADS, 0, st>>>(X, n, d, k, nullptr, cnt, pidx, pd2, 0, rows32,
                                                           nullptr, chunk);
@@ -212,11 +252,11 @@ int launch_knn_exact_rows(Ctx* c, const float* X, int64_t n, int d, int k, const
         knn_exact_kernel<32><<<grid, KNN_THREADS, 0, st>>>(X, n, d, k, nullptr, cnt, pidx, pd2, 0, rows32,
                                                           nullptr, chunk);
     DRGB_CHECK_LAUNCH(c);
-    const int mb = grid_for(cnt, 128, c->num_sms * 4);
+    const int mb = grid_for(cnt, 4, c->num_sms * 8);   // one warp per row, 4 warps per CTA
     if (k <= 16)
-        merge_partials_kernel<16><<<mb, 128, 0, st>>>(pidx, pd2, cnt, C, k, rows32, idx_out, dist_out);
+        merge_partials_kernel<16><<<mb, 128, 0, st>>>(pidx, pd2, cnt, int(C), k, rows32, idx_out, dist_out);
     else
-        merge_partials_kernel<32><<<mb, 128, 0, st>>>(pidx, pd2, cnt, C, k, rows32, idx_out, dist_out);
+        merge_partials_kernel<32><<<mb, 128, 0, st>>>(pidx, pd2, cnt, int(C), k, rows32, idx_out, dist_out);
     DRGB_CHECK_LAUNCH(c);
     return DRGB_OK;
 }
