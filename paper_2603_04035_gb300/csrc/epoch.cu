@@ -6,24 +6,24 @@
 // CSR is head-sorted (row_ptr int32, col int32, q uint32 schedule words).
 // All reads come from Y^(t); there are no atomics.
 //
-// An epoch is two kernels.  The force kernel gives each warp windows of
-// EPOCH_WIN consecutive CSR entries (counted from its instance's first entry):
-// the warp compacts the window's active entries into shared memory, computes
-// their forces 32 at a time (one entry per lane) and adds each head's terms.
-// The update kernel then gives each row its partial sums, in window order,
-// and writes Y' = Y + lr * sum.
+// An epoch is one kernel.  The rows of an instance are cut into windows by
+// their first entry: window w holds the rows whose first entry lies in
+// [w EPOCH_WIN, (w + 1) EPOCH_WIN) (counted from the instance's first entry).
+// One warp takes a window: it compacts the active entries of the window's
+// rows into shared memory, computes their forces 32 at a time (one entry per
+// lane), adds each head's terms and writes Y' = Y + lr * sum for every row of
+// the window.  No row crosses a window, so no row needs a second writer.
 //
 // Summation order of a row's force (a fixed function of the row's instance
 // CSR, so results do not depend on the launch shape, the tuning or on other
 // instances of a batch):
-//   term(e)       = (((0 + attraction) + repulsion_0) + ...) + repulsion_{neg-1}
-//   group sum     = a window's active entries, in entry order, form groups of
-//                   32; the terms of one head in one group are added by the
-//                   5-step segmented inclusive scan over the group's lanes
-//                   (step d adds the partial d lanes to the left)
-//   window sum    = (((group sum_0) + group sum_1) + ...) over the groups that
-//                   hold the head, in order
-//   force         = (((0 + window sum_0) + window sum_1) + ...) over windows
+//   term(e)    = (((0 + attraction) + repulsion_0) + ...) + repulsion_{neg-1}
+//   group sum  = the window's active entries, in entry order, form groups of
+//                32; the terms of one head in one group are added by the
+//                5-step segmented inclusive scan over the group's lanes (step d
+//                adds the partial d lanes to the left)
+//   force      = 0 + (((group sum_0) + group sum_1) + ...) over the groups that
+//                hold the head, in order
 #include "common.cuh"
 #include "epoch.cuh"
 
@@ -221,11 +221,52 @@ __global__ void epoch_instances_kernel(const int32_t* __restrict__ rp, const int
     }
 }
 
+// First row of every window: window w of an instance holds the rows whose
+// first entry lies in [eoff + w EPOCH_WIN, eoff + (w + 1) EPOCH_WIN) (relative
+// to the instance's first entry), plus, in the instance's last window, its
+// trailing empty rows.  win_row[w + 1] ends window w.
+__global__ void epoch_windows_kernel(const int32_t* __restrict__ rp, int64_t n, int64_t row_begin, int count,
+                                     const int64_t* __restrict__ inst_off, const int32_t* __restrict__ inst_eoff,
+                                     const int32_t* __restrict__ win_base, int64_t win_cap,
+                                     int32_t* __restrict__ win_row) {
+    const int64_t n_rows = n - row_begin;
+    const int32_t n_win = count > 0 ? win_base[count] : (rp[n_rows] + EPOCH_WIN - 1) / EPOCH_WIN;
+    for (int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; w <= win_cap;
+         w += int64_t(gridDim.x) * blockDim.x) {
+        if (w >= n_win) {
+            win_row[w] = int32_t(n);
+            continue;
+        }
+        int64_t lo, hi;     // rows searched (relative to row_begin), the target entry
+        int32_t target;
+        if (count > 0) {
+            int a = 0, z = count - 1;  // instance whose windows hold w
+            while (a < z) {
+                const int mid = (a + z + 1) >> 1;
+                if (win_base[mid] <= w) a = mid; else z = mid - 1;
+            }
+            lo = inst_off[a];
+            hi = inst_off[a + 1];
+            target = inst_eoff[a] + int32_t(w - win_base[a]) * EPOCH_WIN;
+        } else {
+            lo = 0;
+            hi = n_rows;
+            target = int32_t(w) * EPOCH_WIN;
+        }
+        while (lo < hi) {  // first row whose first entry is >= target
+            const int64_t mid = (lo + hi) >> 1;
+            if (rp[mid] < target) lo = mid + 1; else hi = mid;
+        }
+        win_row[w] = int32_t(row_begin + lo);
+    }
+}
+
 size_t epoch_scratch_bytes(int64_t n, int64_t nnz_cap, int count) {
     const int64_t win_cap = (nnz_cap + EPOCH_WIN - 1) / EPOCH_WIN + count;
-    size_t b = Carve::round(size_t(nnz_cap > 0 ? nnz_cap : 1) * 4) + Carve::round(size_t(n + win_cap + 1) * 16);
+    size_t b = Carve::round(size_t(nnz_cap > 0 ? nnz_cap : 1) * 4) + Carve::round(size_t(win_cap + 2) * 4);
     if (count > 0)
         b += 3 * Carve::round(size_t(count + 1) * 4) + Carve::round(scan_scratch_elems(count) * 4);
+    (void)n;
     return b + 1024;
 }
 
@@ -235,9 +276,8 @@ int epoch_prepare(Ctx* c, const int32_t* rp, int64_t n, int64_t row_begin, int64
     es->nnz_cap = nnz_cap;
     es->win_cap = (nnz_cap + EPOCH_WIN - 1) / EPOCH_WIN + count;
     es->row_of = cv.take<int32_t>(size_t(nnz_cap > 0 ? nnz_cap : 1));
-    es->pieces = cv.take<float4>(size_t(n + es->win_cap + 1));
+    es->win_row = cv.take<int32_t>(size_t(es->win_cap + 2));
     DRGB_CUDA(c, cudaMemsetAsync(es->row_of, 0xFF, size_t(nnz_cap > 0 ? nnz_cap : 1) * 4, st));
-    DRGB_CUDA(c, cudaMemsetAsync(es->pieces, 0, size_t(n + es->win_cap + 1) * 16, st));
     const int64_t n_rows = n - row_begin;
     if (n_rows > 0) {
         epoch_heads_kernel<<<grid_for(n_rows, 256, c->num_sms * 8), 256, 0, st>>>(rp, n_rows, row_begin, nnz_cap,
@@ -255,23 +295,41 @@ int epoch_prepare(Ctx* c, const int32_t* rp, int64_t n, int64_t row_begin, int64
         int rc = exclusive_scan(c, win_cnt, es->win_base, count, tmp, st);
         if (rc) return rc;
     }
+    epoch_windows_kernel<<<grid_for(es->win_cap + 1, 256, c->num_sms * 4), 256, 0, st>>>(
+        rp, n, row_begin, count, inst_off, es->inst_eoff, es->win_base, es->win_cap, es->win_row);
+    DRGB_CHECK_LAUNCH(c);
     return DRGB_OK;
 }
 
-// ------------------------------------------------------------------ force kernel
-// One warp per window of EPOCH_WIN entries (grid-stride over windows).  Each
-// (row, window) pair that holds active entries gets one record,
-// pieces[row + window]: rows and windows both grow along the CSR, so the index
-// is unique, and it stays below n + windows.
+// ------------------------------------------------------------------ epoch kernel
+// Programmatic dependent launch: an epoch launched right after another one
+// may start while that one finishes.  Everything before grid_dep_wait() reads
+// only the CSR and the prepared tables (which no epoch writes); Y is read and
+// written only after it, when the previous epoch's grid has completed and its
+// writes are visible.  Without a programmatic dependency both are no-ops.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Active entries of one compaction piece waiting in shared memory: at most 31
+// left over from the previous piece plus one piece of EPOCH_WIN entries.
+static constexpr int EPOCH_QCAP = EPOCH_WIN + 32;
+
+// One warp per window (grid-stride over windows).  No row crosses a window, so
+// the warp writes the final Y' of every row of its window.
 template <bool BATCHED, int NEG>
 __global__ void __launch_bounds__(256, 3) epoch_force_kernel(const __grid_constant__ EpochArgs A) {
-    // [warps][EPOCH_WIN] (entry, tail) and [warps][EPOCH_WIN] head of the window's active entries
+    // [warps][EPOCH_QCAP] (entry, tail) and [warps][EPOCH_QCAP] head of the waiting active entries
     extern __shared__ int2 s_active[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    int2* act_w = s_active + w * EPOCH_WIN;
-    int32_t* head_w = reinterpret_cast<int32_t*>(s_active + nw * EPOCH_WIN) + w * EPOCH_WIN;
+    int2* act_w = s_active + w * EPOCH_QCAP;
+    int32_t* head_w = reinterpret_cast<int32_t*>(s_active + nw * EPOCH_QCAP) + w * EPOCH_QCAP;
+    // carry of each warp: running sum of the previous group's last head and
+    // that head's position; the head itself (-1 when none)
+    __shared__ float4 s_carry[8];
+    __shared__ int32_t s_chead[8];
     const unsigned lt_mask = (1u << lane) - 1u;
     const float two_ab = 2.0f * A.a * A.b, two_b = 2.0f * A.b;
+    grid_dep_launch();
     int32_t nnz = 0, n_win = 0;
     if (BATCHED) {
         nnz = A.inst_eoff[A.count];
@@ -284,190 +342,206 @@ __global__ void __launch_bounds__(256, 3) epoch_force_kernel(const __grid_consta
         if (threadIdx.x == 0 && blockIdx.x == 0) report_status(A.status, DRGB_ERR_INVALID);
         return;
     }
+    if (n_win == 0) {  // no entries at all: every row keeps its position
+        grid_dep_wait();
+        for (int64_t r = A.row_begin + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < A.n;
+             r += int64_t(gridDim.x) * blockDim.x) {
+            const float2 y = A.Y_in[r];
+            A.Y_out[r] = make_float2(fmaf(A.lr, 0.f, y.x), fmaf(A.lr, 0.f, y.y));
+        }
+        return;
+    }
     const RowInst R1{0, A.neg_n ? A.neg_n : uint32_t(A.n), 0, A.k0, A.k1};
     for (int32_t W = int32_t(blockIdx.x) * nw + w; W < n_win; W += int32_t(gridDim.x) * nw) {
+        const int32_t rA = A.win_row[W], rB = A.win_row[W + 1];
+        if (rA >= rB) continue;  // a long row started in an earlier window covers this one
         RowInst R = R1;
-        int64_t h_lo = A.row_begin, h_hi = A.n;  // rows a head may take
-        int32_t ws, we;
+        int64_t h_lo = A.row_begin, h_hi = A.n;  // rows a head may take (the instance's rows)
         if (BATCHED) {
             int lo = 0, hi = A.count - 1;  // the instance whose windows hold W
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
                 if (A.win_base[mid] <= W) lo = mid; else hi = mid - 1;
             }
-            const int32_t eoff = A.inst_eoff[lo];
-            ws = eoff + (W - A.win_base[lo]) * EPOCH_WIN;
-            we = min(ws + EPOCH_WIN, A.inst_eoff[lo + 1]);
             R.off = A.inst_off[lo];
             R.n = uint32_t(A.inst_off[lo + 1] - R.off);
-            R.eoff = eoff;
+            R.eoff = A.inst_eoff[lo];
             R.k0 = uint32_t(A.inst_seed[lo]);
             R.k1 = uint32_t(A.inst_seed[lo] >> 32);
             h_lo = R.off;
             h_hi = R.off + R.n;
-        } else {
-            ws = W * EPOCH_WIN;
-            we = min(ws + EPOCH_WIN, nnz);
         }
-        // compaction, in entry order: the window's q, col and heads are loaded
-        // LD chunks of 32 at a time (coalesced; the whole window in one round
-        // trip for a single instance), then tested and appended
-        constexpr int LD = BATCHED ? 8 : 16;
-        int qn = 0;
-#pragma unroll
-        for (int s0 = 0; s0 < EPOCH_WIN / 32; s0 += LD) {
-            uint32_t qv[LD];
-            int32_t jv[LD], hv[LD];
-#pragma unroll
-            for (int s = 0; s < LD; ++s) {
-                const int32_t e = ws + 32 * (s0 + s) + lane;
-                const bool in = e < we;
-                qv[s] = in ? A.q[e] : 0u;  // q = 0 never fires
-                jv[s] = in ? A.col[e] : 0;
-                hv[s] = in ? A.row_of[e] : -1;
+        if (rA < h_lo || rB > h_hi) {
+            if (lane == 0) report_status(A.status, DRGB_ERR_INVALID);
+            continue;
+        }
+        const int32_t es = A.row_ptr[rA - A.row_begin], ee = A.row_ptr[rB - A.row_begin];
+        // every row of the window first gets Y + lr * 0 (after the first
+        // piece is compacted); rows with active entries are rewritten with
+        // their force below
+        auto start_rows = [&]() {
+            grid_dep_wait();
+            for (int64_t r = rA + lane; r < rB; r += 32) {
+                const float2 y = A.Y_in[r];
+                A.Y_out[r] = make_float2(fmaf(A.lr, 0.f, y.x), fmaf(A.lr, 0.f, y.y));
             }
+            // s_carry / s_chead carry the running sum of the previous group's
+            // last head; a row is written when its last group has been added
+            if (lane == 0) s_chead[w] = -1;
+            __syncwarp();
+        };
+        int qn = 0;  // active entries waiting at the front of the buffer
+        // (a window whose rows are all empty still takes one, empty, piece)
+        for (int32_t p0 = es; p0 == es || p0 < ee; p0 += EPOCH_WIN) {
+            const int32_t pe = min(p0 + EPOCH_WIN, ee);
+            // compaction, in entry order: the piece's q, col and heads are
+            // loaded LD chunks of 32 at a time (coalesced), then tested
+            constexpr int LD = 8;
 #pragma unroll
-            for (int s = 0; s < LD; ++s) {
-                // floor((t+1) q / 2^24) > floor(t q / 2^24)  <=>  (t q mod 2^24) + q >= 2^24
-                const bool act = qv[s] >= 0x1000000u - ((A.t * qv[s]) & 0xFFFFFFu);
-                const unsigned m = __ballot_sync(FULL, act);
-                if (act) {
-                    const int pos = qn + __popc(m & lt_mask);
-                    act_w[pos] = make_int2(ws + 32 * (s0 + s) + lane, jv[s]);
-                    head_w[pos] = hv[s];
+            for (int s0 = 0; s0 < EPOCH_WIN / 32; s0 += LD) {
+                uint32_t qv[LD];
+                int32_t jv[LD], hv[LD];
+#pragma unroll
+                for (int s = 0; s < LD; ++s) {
+                    const int32_t e = p0 + 32 * (s0 + s) + lane;
+                    const bool in = e < pe;
+                    qv[s] = in ? A.q[e] : 0u;  // q = 0 never fires
+                    jv[s] = in ? A.col[e] : 0;
+                    hv[s] = in ? A.row_of[e] : -1;
                 }
-                qn += __popc(m);
+#pragma unroll
+                for (int s = 0; s < LD; ++s) {
+                    // floor((t+1) q / 2^24) > floor(t q / 2^24)  <=>  (t q mod 2^24) + q >= 2^24
+                    const bool act = qv[s] >= 0x1000000u - ((A.t * qv[s]) & 0xFFFFFFu);
+                    const unsigned m = __ballot_sync(FULL, act);
+                    if (act) {
+                        const int pos = qn + __popc(m & lt_mask);
+                        act_w[pos] = make_int2(p0 + 32 * (s0 + s) + lane, jv[s]);
+                        head_w[pos] = hv[s];
+                    }
+                    qn += __popc(m);
+                }
             }
+            __syncwarp();
+            if (p0 == es) start_rows();
+            // groups of 32 active entries (the last, partial group waits for
+            // the next piece unless this is the window's last piece),
+            // software-pipelined: the next group's negatives are drawn and its
+            // points gathered before this group's forces are computed
+            const int ng = pe == ee ? (qn + 31) / 32 : qn / 32;
+            EntryInputs<NEG> cur, nxt;
+            if (ng > 0) {
+                const bool v = lane < qn;
+                const int2 ej = v ? act_w[lane] : make_int2(p0, 0);
+                fetch_entry<NEG, BATCHED>(A, R, v, ej.x, ej.y, v ? head_w[lane] : -1, h_lo, h_hi, lane, cur);
+            }
+            for (int g = 0; g < ng; ++g) {
+                const int g0 = 32 * g;
+                const int cnt = qn - g0 < 32 ? qn - g0 : 32;
+                if (g + 1 < ng) {
+                    const bool v = g0 + 32 + lane < qn;
+                    const int2 ej = v ? act_w[g0 + 32 + lane] : make_int2(p0, 0);
+                    fetch_entry<NEG, BATCHED>(A, R, v, ej.x, ej.y, v ? head_w[g0 + 32 + lane] : -1, h_lo, h_hi,
+                                              lane, nxt);
+                }
+                float fx = 0.f, fy = 0.f;
+                if (cur.ok) {
+                    const float2 f = entry_math<NEG, BATCHED>(A, R, cur, two_ab, two_b);
+                    fx = f.x;
+                    fy = f.y;
+                }
+                const int32_t i = cur.i;
+                const int32_t chead = s_chead[w];
+                // the carried head ends unless this group starts with it
+                if (chead >= 0 && lane == 0 && i != chead) {
+                    const float4 cv = s_carry[w];
+                    A.Y_out[chead] = make_float2(fmaf(A.lr, 0.f + cv.x, cv.z), fmaf(A.lr, 0.f + cv.y, cv.w));
+                }
+                // segmented inclusive scan over runs of equal heads
+                const int32_t i_prev = __shfl_up_sync(FULL, i, 1);
+                const unsigned starts = __ballot_sync(FULL, lane == 0 || i_prev != i);
+                const int seg0 = 31 - __clz(starts & (FULL >> (31 - lane)));
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const float ox = __shfl_up_sync(FULL, fx, d), oy = __shfl_up_sync(FULL, fy, d);
+                    if (lane - d >= seg0) {
+                        fx = ox + fx;
+                        fy = oy + fy;
+                    }
+                }
+                if (seg0 == 0 && i == chead) {
+                    const float4 cv = s_carry[w];
+                    fx = cv.x + fx;
+                    fy = cv.y + fy;
+                }
+                // a run that ends inside the group is the row's last: write
+                // it; the group's last run is carried
+                const int32_t i_next = __shfl_down_sync(FULL, i, 1);
+                if (cur.ok && lane < cnt - 1 && i_next != i)
+                    A.Y_out[i] = make_float2(fmaf(A.lr, 0.f + fx, cur.yi.x), fmaf(A.lr, 0.f + fy, cur.yi.y));
+                __syncwarp();
+                if (lane == cnt - 1) {
+                    s_carry[w] = make_float4(fx, fy, cur.yi.x, cur.yi.y);
+                    s_chead[w] = cur.ok ? i : -1;
+                }
+                __syncwarp();
+                cur = nxt;
+            }
+            // move the waiting partial group to the front of the buffer
+            const int left = qn - 32 * ng > 0 ? qn - 32 * ng : 0;
+            int2 lv = make_int2(0, 0);
+            int32_t lh = -1;
+            if (lane < left) {
+                lv = act_w[32 * ng + lane];
+                lh = head_w[32 * ng + lane];
+            }
+            __syncwarp();
+            if (lane < left) {
+                act_w[lane] = lv;
+                head_w[lane] = lh;
+            }
+            qn = left;
+            __syncwarp();
+        }
+        if (lane == 0 && s_chead[w] >= 0) {
+            const float4 cv = s_carry[w];
+            A.Y_out[s_chead[w]] = make_float2(fmaf(A.lr, 0.f + cv.x, cv.z), fmaf(A.lr, 0.f + cv.y, cv.w));
         }
         __syncwarp();
-        // groups of 32 active entries, software-pipelined: the next group's
-        // negatives are drawn and its points gathered before this group's
-        // forces are computed.  (cx, cy) carries the running window sum of the
-        // previous group's last head.
-        float cx = 0.f, cy = 0.f;
-        int32_t chead = -1;
-        EntryInputs<NEG> cur, nxt;
-        {
-            const bool v = lane < qn;
-            const int2 ej = v ? act_w[lane] : make_int2(ws, 0);
-            fetch_entry<NEG, BATCHED>(A, R, v, ej.x, ej.y, v ? head_w[lane] : -1, h_lo, h_hi, lane, cur);
-        }
-        for (int g0 = 0; g0 < qn; g0 += 32) {
-            const int cnt = qn - g0 < 32 ? qn - g0 : 32;
-            if (g0 + 32 < qn) {
-                const bool v = g0 + 32 + lane < qn;
-                const int2 ej = v ? act_w[g0 + 32 + lane] : make_int2(ws, 0);
-                fetch_entry<NEG, BATCHED>(A, R, v, ej.x, ej.y, v ? head_w[g0 + 32 + lane] : -1, h_lo, h_hi, lane,
-                                          nxt);
-            }
-            float fx = 0.f, fy = 0.f;
-            if (cur.ok) {
-                const float2 f = entry_math<NEG, BATCHED>(A, R, cur, two_ab, two_b);
-                fx = f.x;
-                fy = f.y;
-            }
-            const int32_t i = cur.i;
-            const bool ok = cur.ok;
-            // the carried head ends unless this group starts with it
-            if (chead >= 0 && lane == 0 && i != chead)
-                A.pieces[int64_t(chead) + W] = make_float4(cx, cy, 1.0f, 0.f);
-            // segmented inclusive scan over runs of equal heads
-            const int32_t i_prev = __shfl_up_sync(FULL, i, 1);
-            const unsigned starts = __ballot_sync(FULL, lane == 0 || i_prev != i);
-            const int seg0 = 31 - __clz(starts & (FULL >> (31 - lane)));
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const float ox = __shfl_up_sync(FULL, fx, d), oy = __shfl_up_sync(FULL, fy, d);
-                if (lane - d >= seg0) {
-                    fx = ox + fx;
-                    fy = oy + fy;
-                }
-            }
-            if (seg0 == 0 && i == chead) {
-                fx = cx + fx;
-                fy = cy + fy;
-            }
-            const int32_t i_next = __shfl_down_sync(FULL, i, 1);
-            const bool last = lane == cnt - 1;
-            const bool more = g0 + 32 < qn;
-            if (ok && (last ? !more : i_next != i)) A.pieces[int64_t(i) + W] = make_float4(fx, fy, 1.0f, 0.f);
-            cx = __shfl_sync(FULL, fx, cnt - 1);
-            cy = __shfl_sync(FULL, fy, cnt - 1);
-            chead = __shfl_sync(FULL, i, cnt - 1);
-            cur = nxt;
-        }
-        __syncwarp();
-    }
-}
-
-// ------------------------------------------------------------------ update kernel
-// Row r adds its window records in window order and writes Y'_r; each record
-// read is marked consumed (z = 0) for the next epoch.
-template <bool BATCHED>
-__global__ void epoch_update_kernel(const __grid_constant__ EpochArgs A) {
-    for (int64_t r = A.row_begin + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < A.n;
-         r += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t lr = r - A.row_begin;
-        const int32_t beg = A.row_ptr[lr], end = A.row_ptr[lr + 1];
-        float ax = 0.f, ay = 0.f;
-        if (beg >= 0 && end > beg) {
-            int64_t w0, w1;
-            if (BATCHED) {
-                int lo = 0, hi = A.count - 1;  // instance of row r
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (A.inst_off[mid] <= r) lo = mid; else hi = mid - 1;
-                }
-                const int32_t eoff = A.inst_eoff[lo];
-                w0 = A.win_base[lo] + (beg - eoff) / EPOCH_WIN;
-                w1 = A.win_base[lo] + (end - 1 - eoff) / EPOCH_WIN;
-            } else {
-                w0 = beg / EPOCH_WIN;
-                w1 = (end - 1) / EPOCH_WIN;
-            }
-            if (w0 < 0 || w1 >= A.win_cap) {
-                report_status(A.status, DRGB_ERR_INVALID);
-                w1 = w0 - 1;
-            }
-            for (int64_t W = w0; W <= w1; ++W) {
-                float4* p = A.pieces + r + W;
-                const float4 v = *p;
-                if (v.z != 0.f) {
-                    ax += v.x;
-                    ay += v.y;
-                    p->z = 0.f;
-                }
-            }
-        }
-        const float2 y = A.Y_in[r];
-        A.Y_out[r] = make_float2(fmaf(A.lr, ax, y.x), fmaf(A.lr, ay, y.y));
     }
 }
 
 bool epoch_warps_supported(int warps) { return warps == 4 || warps == 8; }
 
-int launch_epoch(Ctx* c, const EpochArgs& A_in, int warps, cudaStream_t st) {
+int launch_epoch(Ctx* c, const EpochArgs& A_in, int warps, cudaStream_t st, bool after_epoch) {
     if (warps <= 0) warps = c->epoch_warps;
     if (!epoch_warps_supported(warps))
         return set_error(c, DRGB_ERR_INVALID, "epoch: unsupported force-kernel width %d", warps);
-    if (!A_in.row_of || !A_in.pieces) return set_error(c, DRGB_ERR_INVALID, "epoch: state not prepared");
+    if (!A_in.row_of || !A_in.win_row) return set_error(c, DRGB_ERR_INVALID, "epoch: state not prepared");
     EpochArgs A = A_in;
     philox_round_keys(A.k0, A.k1, A.rk);
     const int threads = warps * 32;
-    const size_t smem = size_t(warps) * EPOCH_WIN * (sizeof(int2) + sizeof(int32_t));
+    const size_t smem = size_t(warps) * EPOCH_QCAP * (sizeof(int2) + sizeof(int32_t));
     const int fgrid = grid_for(A.win_cap, warps, c->num_sms * (24 / warps));
     const bool bat = A.count > 0, n5 = A.neg == 5;
-    if (bat) {
-        if (n5) epoch_force_kernel<true, 5><<<fgrid, threads, smem, st>>>(A);
-        else epoch_force_kernel<true, -1><<<fgrid, threads, smem, st>>>(A);
-    } else {
-        if (n5) epoch_force_kernel<false, 5><<<fgrid, threads, smem, st>>>(A);
-        else epoch_force_kernel<false, -1><<<fgrid, threads, smem, st>>>(A);
-    }
-    DRGB_CHECK_LAUNCH(c);
-    const int ugrid = grid_for(A.n - A.row_begin, 256, c->num_sms * 8);
-    if (bat) epoch_update_kernel<true><<<ugrid, 256, 0, st>>>(A);
-    else epoch_update_kernel<false><<<ugrid, 256, 0, st>>>(A);
+    auto go = [&](auto kernel) -> int {
+        DRGB_CUDA(c, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(fgrid);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = after_epoch ? 1 : 0;  // only an epoch may precede with overlap
+        DRGB_CUDA(c, cudaLaunchKernelEx(&cfg, kernel, A));
+        return DRGB_OK;
+    };
+    int rc = bat ? (n5 ? go(epoch_force_kernel<true, 5>) : go(epoch_force_kernel<true, -1>))
+                 : (n5 ? go(epoch_force_kernel<false, 5>) : go(epoch_force_kernel<false, -1>));
+    if (rc) return rc;
     DRGB_CHECK_LAUNCH(c);
     return DRGB_OK;
 }
@@ -501,7 +575,7 @@ static void fill_args(EpochArgs& A, const int32_t* rp, const int32_t* col, const
     A.k1 = uint32_t(seed >> 32);
     A.status = status;
     A.row_of = es.row_of;
-    A.pieces = es.pieces;
+    A.win_row = es.win_row;
     A.nnz_cap = es.nnz_cap;
     A.win_cap = es.win_cap;
     A.count = count;
@@ -542,7 +616,7 @@ int run_epochs(Ctx* c, float2* Y, float2* Y_tmp, const int32_t* rp, const int32_
         A.Y_out = dst;
         A.lr = float(double(lr0) * (1.0 - double(t) / double(T)));
         A.t = uint32_t(t);
-        rc = launch_epoch(c, A, 0, cap);
+        rc = launch_epoch(c, A, 0, cap, t > t_begin);
         float2* tmp = src;
         src = dst;
         dst = tmp;
@@ -596,7 +670,7 @@ int autotune_epoch(Ctx* c, const float2* Y, float2* Ya, float2* Yb, const int32_
                 A.Y_out = (k & 1) ? Ya : Yb;
                 A.t = uint32_t(t0 + k);
                 A.lr = 1.0f - float(t0 + k) / float(T);
-                rc = launch_epoch(c, A, warps, st);
+                rc = launch_epoch(c, A, warps, st, k > 0);
             }
             cudaEventRecord(e1, st);
             if (cudaEventSynchronize(e1) != cudaSuccess) rc = set_error(c, DRGB_ERR_CUDA, "autotune: sync failed");

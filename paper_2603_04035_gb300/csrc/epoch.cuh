@@ -4,7 +4,7 @@
 
 namespace drgb {
 
-// CSR entries per window of the force kernel.  Part of the summation order
+// CSR entries per window of the epoch kernel.  Part of the summation order
 // (see epoch.cu), so it is a constant, not a tuning knob.
 static constexpr int EPOCH_WIN = 512;
 
@@ -21,13 +21,12 @@ struct EpochArgs {
     uint32_t k0, k1;
     uint32_t rk[20];      // Philox round keys of (k0, k1); filled by launch_epoch
     int* status;          // device status word (malformed CSR is reported here)
-    // Prepared per call (epoch_prepare): head row of every CSR entry, and one
-    // record per (row, window) pair holding a window's partial force of a row
-    // (index row + window; z = 1 while it waits for the update kernel).
+    // Prepared per call (epoch_prepare): head row of every CSR entry, and the
+    // first row of every window (win_row[w] .. win_row[w + 1] - 1 are its rows).
     const int32_t* __restrict__ row_of;
-    float4* __restrict__ pieces;
+    const int32_t* __restrict__ win_row;
     int64_t nnz_cap;      // entries row_of covers (the CSR may not hold more)
-    int64_t win_cap;      // windows the pieces array covers
+    int64_t win_cap;      // windows win_row covers
     // Batched form (count > 0): rows [inst_off[b], inst_off[b+1]) form instance b,
     // whose entries, negatives and Philox key (inst_seed[b]) are instance-local.
     // Its entries are [inst_eoff[b], inst_eoff[b+1]) and its windows start at
@@ -46,7 +45,7 @@ struct EpochArgs {
 // Device buffers an epoch needs besides the CSR and Y (carved from `scratch`).
 struct EpochScratch {
     int32_t* row_of = nullptr;
-    float4* pieces = nullptr;
+    int32_t* win_row = nullptr;
     int32_t* inst_eoff = nullptr;
     int32_t* win_base = nullptr;
     int64_t nnz_cap = 0;
@@ -58,14 +57,15 @@ struct EpochScratch {
 size_t epoch_scratch_bytes(int64_t n, int64_t nnz_cap, int count);
 
 // Build the per-call epoch state on `st`: heads of the CSR entries of rows
-// [row_begin, n), cleared piece records and, for count > 0, the instances'
+// [row_begin, n), the windows' first rows and, for count > 0, the instances'
 // entry offsets and window bases.
 int epoch_prepare(Ctx* c, const int32_t* rp, int64_t n, int64_t row_begin, int64_t nnz_cap, int count,
                   const int64_t* inst_off, void* scratch, EpochScratch* es, cudaStream_t st);
 
-// One epoch: the force kernel, then the update kernel.  `warps` = warps per
-// CTA of the force kernel (0: the context's setting).
-int launch_epoch(Ctx* c, const EpochArgs& A, int warps, cudaStream_t st);
+// One epoch (one kernel launch).  `warps` = warps per CTA (0: the context's
+// setting).  `after_epoch`: the previous launch on `st` is an epoch of the same
+// prepared state, so this one may start early (programmatic dependent launch).
+int launch_epoch(Ctx* c, const EpochArgs& A, int warps, cudaStream_t st, bool after_epoch = false);
 int launch_init(Ctx* c, float2* Y, int64_t n, float range, uint64_t seed, cudaStream_t st);
 
 // Epochs [t_begin, t_end) of a T-epoch schedule, ping-ponging between Y and
