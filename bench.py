@@ -362,10 +362,10 @@ def roofline(args, n, d, nnz, updates, stage_acc, steps, peaks, peak_src, T):
         bytes_ep = 4 * (n + 1) + 16 * n + 8 * nnz + 8 * act_per_epoch * (1 + NEG)
         achieved = bytes_ep / per_launch_s / 1e9
         peak = float(peaks["hbm_gbs"])
-        return {"kernel": "embed_epoch_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+        return {"kernel": "epoch_force_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": f"hbm_gbs ({peak_src})",
                 "bytes_per_launch": bytes_ep, "launch_ms": per_launch_s * 1e3,
-                "traffic": kernel_traffic("embed_epoch_kernel",
+                "traffic": kernel_traffic("epoch_force_kernel",
                                           "paper_2603_04035_gb300/csrc/epoch.cu")}
     if gemm_ms > 0:
         # FP16 and BF16 share the tcgen05 kind::f16 rate: the measured BF16 peak applies
