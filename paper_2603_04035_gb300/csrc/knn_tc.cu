@@ -50,24 +50,56 @@ static constexpr int TC_THREADS = 64 + TC_EPI_WARPS * 32;
 static constexpr int TC_A_BYTES = TC_BM * TC_K * 2;   // 16 KiB
 static constexpr int TC_B_BYTES = TC_BN * TC_K * 2;   // 32 KiB
 static constexpr int TC_TMEM_COLS = 512;               // two 256-column accumulators
-static constexpr int TC_QCAP = 16;                     // per-thread candidate queue slots
+static constexpr int TC_QCAP = 32;                     // per-thread candidate queue slots (one chunk)
 static constexpr size_t TC_QUEUE_BYTES = size_t(TC_EPI_WARPS) * 32 * TC_QCAP * 8;
-static constexpr size_t TC_SMEM = 1024 + TC_A_BYTES + TC_STAGES * TC_B_BYTES + 256 + TC_QUEUE_BYTES;
+static constexpr size_t TC_THR_BYTES = size_t(2) * TC_BM * 4;   // per (column half, row) threshold
+static constexpr size_t TC_SMEM =
+    1024 + TC_A_BYTES + TC_STAGES * TC_B_BYTES + 256 + TC_QUEUE_BYTES + TC_THR_BYTES;
 
-// Sorted insertion into an ascending list (precondition: v < L[KP-1]); an
-// equal value keeps the earlier (smaller) index first.
-__device__ __forceinline__ void list_insert(float (&L)[TC_KP], int32_t (&I)[TC_KP], float v, int32_t j) {
+// Compare-exchange of (value, index) pairs i < l: afterwards the pair at i is
+// the smaller (asc) or the larger (!asc) of the two values.
+__device__ __forceinline__ void cas(float& vi, int32_t& ii, float& vl, int32_t& il, bool asc) {
+    const bool sw = asc ? (vl < vi) : (vi < vl);
+    const float a = vi, b = vl;
+    const int32_t x = ii, y = il;
+    vi = sw ? b : a;
+    vl = sw ? a : b;
+    ii = sw ? y : x;
+    il = sw ? x : y;
+}
+
+// Bitonic merge of a bitonic sequence of N (power of two) into ascending order.
+template <int N>
+__device__ __forceinline__ void bitonic_merge_asc(float (&v)[N], int32_t (&ix)[N]) {
 #pragma unroll
-    for (int s = TC_KP - 1; s > 0; --s) {
-        const bool shift = v < L[s - 1];
-        const bool place = !shift && v < L[s];
-        L[s] = shift ? L[s - 1] : (place ? v : L[s]);
-        I[s] = shift ? I[s - 1] : (place ? j : I[s]);
+    for (int j = N / 2; j > 0; j >>= 1) {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if ((i & j) == 0) cas(v[i], ix[i], v[i + j], ix[i + j], true);
     }
-    if (v < L[0]) {
-        L[0] = v;
-        I[0] = j;
+}
+
+// Bitonic sort of N (power of two) into ascending order.
+template <int N>
+__device__ __forceinline__ void bitonic_sort_asc(float (&v)[N], int32_t (&ix)[N]) {
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const int l = i ^ j;
+                if (l > i) cas(v[i], ix[i], v[l], ix[l], (i & k) == 0);
+            }
+        }
     }
+}
+
+// Three-input minimum (sm_100 and later).
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
 }
 
 // ------------------------------------------------------------------ A1: staging
@@ -221,6 +253,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     // per epilogue thread: a queue of candidates that passed the threshold
     float* q_s = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bars) + 256);
     int32_t* q_j = reinterpret_cast<int32_t*>(q_s + TC_EPI_WARPS * 32 * TC_QCAP);
+    // per (column half, row): the 32nd-best value that half holds so far
+    float* s_thr = reinterpret_cast<float*>(q_j + TC_EPI_WARPS * 32 * TC_QCAP);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t q0 = int64_t(blockIdx.x) * TC_BM;
@@ -313,22 +347,42 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             L[s] = INFINITY;
             I[s] = -1;
         }
-        // Candidates below the row's current threshold L[KP-1] are appended to
-        // this thread's queue (slot s at q_*[s * 256 + tid], conflict-free);
-        // when any lane of the warp has 8 or more queued, all lanes merge
-        // their queues into their sorted lists in lockstep, so an insertion
-        // pass serves all 32 rows of the warp at once.
+        // Candidates below the row's threshold are appended to this thread's
+        // queue (slot s at q_*[s * 256 + tid], conflict-free).  The threshold
+        // is the smaller of the two column halves' 32nd-best values: a value at
+        // or above either cannot be among the row's 32 best, whichever half
+        // holds it (each half's 32nd-best bounds the row's from above, and a
+        // stale, larger, value is still a valid bound).  When a chunk would
+        // overflow any lane's queue, all lanes merge their queues into their
+        // lists in lockstep: the queue (padded with +inf) is sorted by a
+        // bitonic network, the 32 smallest of list and queue are selected by
+        // pairing the list's upper half with the reversed queue, and a bitonic
+        // merge restores the order.
         const int qb = e * 32 + lane;
+        volatile float* thr_mine = s_thr + half * TC_BM + row;
+        volatile float* thr_other = s_thr + (1 - half) * TC_BM + row;
+        *thr_mine = INFINITY;
+        asm volatile("bar.sync 1, %0;" ::"r"(TC_EPI_WARPS * 32) : "memory");
         int qn = 0;
         auto flush = [&]() {
-            const int qmax = __reduce_max_sync(0xffffffffu, qn);
-            for (int s = 0; s < qmax; ++s) {
-                if (s < qn) {
-                    const float x = q_s[s * (TC_EPI_WARPS * 32) + qb];
-                    if (x < L[TC_KP - 1]) list_insert(L, I, x, q_j[s * (TC_EPI_WARPS * 32) + qb]);
-                }
+            float qv[TC_QCAP];
+            int32_t qi[TC_QCAP];
+#pragma unroll
+            for (int s = 0; s < TC_QCAP; ++s) {
+                qv[s] = s < qn ? q_s[s * (TC_EPI_WARPS * 32) + qb] : INFINITY;
+                qi[s] = s < qn ? q_j[s * (TC_EPI_WARPS * 32) + qb] : -1;
             }
+            bitonic_sort_asc<TC_QCAP>(qv, qi);
+            // the 32 smallest of L and Q: min(L[s], Q[31 - s]) is bitonic
+#pragma unroll
+            for (int s = 0; s < TC_KP; ++s) {
+                const bool take = qv[TC_KP - 1 - s] < L[s];
+                L[s] = take ? qv[TC_KP - 1 - s] : L[s];
+                I[s] = take ? qi[TC_KP - 1 - s] : I[s];
+            }
+            bitonic_merge_asc<TC_KP>(L, I);
             qn = 0;
+            *thr_mine = L[TC_KP - 1];
         };
         for (int t = 0; t < T; ++t) {
             const int buf = t & 1, use = t >> 1;
@@ -341,27 +395,32 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 float v[32];
                 __syncwarp();
                 tmem_ld32(tbase + c * 32, v);
-                const float thr = L[TC_KP - 1];
+                float thr = fminf(L[TC_KP - 1], *thr_other);
                 float gm[4];
 #pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    gm[g] = fminf(fminf(fminf(v[8 * g], v[8 * g + 1]), fminf(v[8 * g + 2], v[8 * g + 3])),
-                                  fminf(fminf(v[8 * g + 4], v[8 * g + 5]), fminf(v[8 * g + 6], v[8 * g + 7])));
-                }
+                for (int g = 0; g < 4; ++g)
+                    gm[g] = min3f(min3f(v[8 * g], v[8 * g + 1], v[8 * g + 2]),
+                                  min3f(v[8 * g + 3], v[8 * g + 4], v[8 * g + 5]), fminf(v[8 * g + 6], v[8 * g + 7]));
+                const float m = fminf(min3f(gm[0], gm[1], gm[2]), gm[3]);
+                if (__any_sync(0xffffffffu, m < thr)) {
+                    int cnt = 0;
 #pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    if (__any_sync(0xffffffffu, gm[g] < thr)) {
-                        if (gm[g] < thr) {
+                    for (int u = 0; u < 32; ++u) cnt += v[u] < thr ? 1 : 0;
+                    if (__any_sync(0xffffffffu, qn + cnt > TC_QCAP)) {
+                        // the chunk is read again after the merge, which keeps
+                        // its 32 values out of registers meanwhile
+                        flush();
+                        __syncwarp();
+                        tmem_ld32(tbase + c * 32, v);
+                        thr = fminf(L[TC_KP - 1], *thr_other);
+                    }
 #pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                if (v[8 * g + u] < thr) {
-                                    q_s[qn * (TC_EPI_WARPS * 32) + qb] = v[8 * g + u];
-                                    q_j[qn * (TC_EPI_WARPS * 32) + qb] = j0 + c * 32 + 8 * g + u;
-                                    ++qn;
-                                }
-                            }
+                    for (int u = 0; u < 32; ++u) {
+                        if (v[u] < thr) {
+                            q_s[qn * (TC_EPI_WARPS * 32) + qb] = v[u];
+                            q_j[qn * (TC_EPI_WARPS * 32) + qb] = j0 + c * 32 + u;
+                            ++qn;
                         }
-                        if (__any_sync(0xffffffffu, qn > TC_QCAP - 8)) flush();
                     }
                 }
             }
