@@ -250,11 +250,11 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     uint64_t* mma_done = acc_empty + 2;          // [1]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    // per epilogue thread: a queue of candidates that passed the threshold
-    float* q_s = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bars) + 256);
-    int32_t* q_j = reinterpret_cast<int32_t*>(q_s + TC_EPI_WARPS * 32 * TC_QCAP);
+    // per epilogue thread: a queue of candidates (value bits, column) that
+    // passed the threshold
+    int2* q = reinterpret_cast<int2*>(reinterpret_cast<uint8_t*>(bars) + 256);
     // per (column half, row): the 32nd-best value that half holds so far
-    float* s_thr = reinterpret_cast<float*>(q_j + TC_EPI_WARPS * 32 * TC_QCAP);
+    float* s_thr = reinterpret_cast<float*>(q + TC_EPI_WARPS * 32 * TC_QCAP);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t q0 = int64_t(blockIdx.x) * TC_BM;
@@ -348,7 +348,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             I[s] = -1;
         }
         // Candidates below the row's threshold are appended to this thread's
-        // queue (slot s at q_*[s * 256 + tid], conflict-free).  The threshold
+        // queue (slot s at q[s * 256 + tid], conflict-free).  The threshold
         // is the smaller of the two column halves' 32nd-best values: a value at
         // or above either cannot be among the row's 32 best, whichever half
         // holds it (each half's 32nd-best bounds the row's from above, and a
@@ -369,8 +369,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             int32_t qi[TC_QCAP];
 #pragma unroll
             for (int s = 0; s < TC_QCAP; ++s) {
-                qv[s] = s < qn ? q_s[s * (TC_EPI_WARPS * 32) + qb] : INFINITY;
-                qi[s] = s < qn ? q_j[s * (TC_EPI_WARPS * 32) + qb] : -1;
+                const int2 c = s < qn ? q[s * (TC_EPI_WARPS * 32) + qb] : make_int2(__float_as_int(INFINITY), -1);
+                qv[s] = __int_as_float(c.x);
+                qi[s] = c.y;
             }
             bitonic_sort_asc<TC_QCAP>(qv, qi);
             // the 32 smallest of L and Q: min(L[s], Q[31 - s]) is bitonic
@@ -403,23 +404,33 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                                   min3f(v[8 * g + 3], v[8 * g + 4], v[8 * g + 5]), fminf(v[8 * g + 6], v[8 * g + 7]));
                 const float m = fminf(min3f(gm[0], gm[1], gm[2]), gm[3]);
                 if (__any_sync(0xffffffffu, m < thr)) {
-                    int cnt = 0;
+                    // room for this chunk's candidates: a bound from the groups
+                    // first, the exact count only when the bound overflows
+                    const int ub = 8 * ((gm[0] < thr) + (gm[1] < thr) + (gm[2] < thr) + (gm[3] < thr));
+                    if (__any_sync(0xffffffffu, qn + ub > TC_QCAP)) {
+                        int cnt = 0;
 #pragma unroll
-                    for (int u = 0; u < 32; ++u) cnt += v[u] < thr ? 1 : 0;
-                    if (__any_sync(0xffffffffu, qn + cnt > TC_QCAP)) {
-                        // the chunk is read again after the merge, which keeps
-                        // its 32 values out of registers meanwhile
-                        flush();
-                        __syncwarp();
-                        tmem_ld32(tbase + c * 32, v);
-                        thr = fminf(L[TC_KP - 1], *thr_other);
+                        for (int u = 0; u < 32; ++u) cnt += v[u] < thr ? 1 : 0;
+                        if (__any_sync(0xffffffffu, qn + cnt > TC_QCAP)) {
+                            // the chunk is read again after the merge, which
+                            // keeps its 32 values out of registers meanwhile
+                            flush();
+                            __syncwarp();
+                            tmem_ld32(tbase + c * 32, v);
+                            thr = fminf(L[TC_KP - 1], *thr_other);
+                        }
                     }
 #pragma unroll
-                    for (int u = 0; u < 32; ++u) {
-                        if (v[u] < thr) {
-                            q_s[qn * (TC_EPI_WARPS * 32) + qb] = v[u];
-                            q_j[qn * (TC_EPI_WARPS * 32) + qb] = j0 + c * 32 + u;
-                            ++qn;
+                    for (int g = 0; g < 4; ++g) {
+                        if (__any_sync(0xffffffffu, gm[g] < thr)) {
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                if (v[8 * g + u] < thr) {
+                                    q[qn * (TC_EPI_WARPS * 32) + qb] =
+                                        make_int2(__float_as_int(v[8 * g + u]), j0 + c * 32 + 8 * g + u);
+                                    ++qn;
+                                }
+                            }
                         }
                     }
                 }

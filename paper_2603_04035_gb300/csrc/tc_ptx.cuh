@@ -38,13 +38,27 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Try-wait that may suspend the thread for up to `hint_ns` nanoseconds; the
+// thread resumes as soon as the phase completes.
+__device__ __forceinline__ bool mbar_try_sleep(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait: gives up after TC_TIMEOUT_NS or when another role aborted.
+// Between checks the thread sleeps in the barrier (at most 20 us a time)
+// instead of spinning, so a waiting role takes no issue slots from the
+// roles that work.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                           int* status) {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = global_timer();
     while (true) {
-        if (mbar_try(bar, parity)) return true;
+        if (mbar_try_sleep(bar, parity, 20000u)) return true;
         if (*abort_flag) return false;
         if (global_timer() - t0 > TC_TIMEOUT_NS) {
             *abort_flag = 1;
