@@ -33,6 +33,14 @@ size_t knn_tc_scratch_bytes(int64_t n, int d);
 int knn_tc(Ctx* c, const float* X, int64_t n, int d, int k, bool f16, int32_t* idx_out, float* dist_out,
            cudaStream_t st, void* scratch);
 
+// Spatial order for the tensor-core k-NN (knn_order.cu): K cells from
+// farthest-point pivots; perm[p] = point at position p (p < n), cell c holds
+// positions [cell_beg[c], cell_beg[c+1]) inside the sphere (centre[c], radius[c]).
+int knn_order_cells(int64_t n);
+size_t knn_order_scratch_bytes(int64_t n, int d, int K);
+int knn_order(Ctx* c, const float* X, int64_t n, int d, int K, int32_t* perm, int32_t* cell_beg, float* centre,
+              float* radius, void* scratch, cudaStream_t st);
+
 // k-NN graph with the mode resolved (0 = auto); `scratch` holds
 // knn_scratch_bytes(n, d, k, mode) bytes (may be null when that is 0).
 int knn_resolve_mode(int64_t n, int d, int k, int mode);

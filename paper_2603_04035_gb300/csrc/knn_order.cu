@@ -1,0 +1,204 @@
+// Spatial ordering of the points for the tensor-core k-NN: K pivots chosen by
+// farthest-point sampling on a strided subsample, every point assigned to its
+// nearest pivot (exact FP32 scan), a stable counting sort by pivot ("cell"),
+// and a bounding sphere per cell.  The order only decides which database
+// tiles a query block visits first and which it may skip; the k-NN result
+// does not depend on it (skipped cells enter the certificate as a distance
+// bound, and rows the bound cannot certify are scanned exactly).
+#include "common.cuh"
+#include "knn.cuh"
+
+namespace drgb {
+
+static constexpr int ORD_SUB = 16384;     // subsample size for the pivot choice
+static constexpr int ORD_CHUNK = 4096;    // points per counting-sort chunk (one warp each)
+
+// Farthest-point step `it` (0 <= it < K): pivot it is the first subsample
+// point (it = 0) or the point step it-1 found farthest (slot[it-1]); it is
+// recorded in pivots[it] and lowers every subsample point's squared distance
+// to the pivot set.  Unless this is the last step, the farthest point (ties:
+// lowest subsample index) goes to slot[it] as (distance bits << 32) | ~index.
+__global__ void fps_step_kernel(const float* __restrict__ X, int64_t n, int d, int m, int it, int K,
+                                float* __restrict__ mind, unsigned long long* __restrict__ slot,
+                                int32_t* __restrict__ pivots) {
+    const int32_t p_sub = it > 0 ? int32_t(~uint32_t(slot[it - 1] & 0xffffffffull)) : 0;
+    const int64_t p = int64_t(p_sub) * n / m;
+    if (blockIdx.x == 0 && threadIdx.x == 0) pivots[it] = int32_t(p);
+    if (it == K - 1) return;
+    unsigned long long best = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const int64_t g = int64_t(i) * n / m;
+        float s = 0.f;
+        for (int c = 0; c < d; ++c) {
+            const float df = X[g * d + c] - X[p * d + c];
+            s = fmaf(df, df, s);
+        }
+        const float v = it == 0 ? s : fminf(mind[i], s);
+        mind[i] = v;
+        const unsigned long long key = (uint64_t(__float_as_uint(v)) << 32) | uint64_t(~uint32_t(i));
+        best = key > best ? key : best;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+        best = other > best ? other : best;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(slot + it, best);
+}
+
+__global__ void gather_rows_kernel(const float* __restrict__ X, int d, const int32_t* __restrict__ rows, int count,
+                                   float* __restrict__ out) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count * d; t += gridDim.x * blockDim.x)
+        out[t] = X[int64_t(rows[t / d]) * d + t % d];
+}
+
+// Per chunk of ORD_CHUNK points: how many fall in each cell.
+__global__ void cell_count_kernel(const int32_t* __restrict__ cell, int64_t n, int K, int nchunk,
+                                  int32_t* __restrict__ counts) {
+    extern __shared__ int32_t s_cnt[];
+    for (int c = threadIdx.x; c < K; c += blockDim.x) s_cnt[c] = 0;
+    __syncthreads();
+    const int64_t b0 = int64_t(blockIdx.x) * ORD_CHUNK;
+    for (int64_t i = b0 + threadIdx.x; i < b0 + ORD_CHUNK && i < n; i += blockDim.x) atomicAdd(&s_cnt[cell[i]], 1);
+    __syncthreads();
+    for (int c = threadIdx.x; c < K; c += blockDim.x) counts[int64_t(c) * nchunk + blockIdx.x] = s_cnt[c];
+}
+
+// Stable scatter: one warp walks its chunk in index order, 32 points a round;
+// a point's position is its cell's offset for this chunk plus the number of
+// earlier points of the chunk in the same cell.
+__global__ void cell_scatter_kernel(const int32_t* __restrict__ cell, int64_t n, int K, int nchunk,
+                                    const int32_t* __restrict__ offs, int32_t* __restrict__ perm) {
+    extern __shared__ int32_t s_run[];  // [warps][K]
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    int32_t* run = s_run + w * K;
+    const int chunk = blockIdx.x * nw + w;
+    if (chunk >= nchunk) return;
+    for (int c = lane; c < K; c += 32) run[c] = offs[int64_t(c) * nchunk + chunk];
+    __syncwarp();
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t b0 = int64_t(chunk) * ORD_CHUNK;
+    for (int64_t r = b0; r < b0 + ORD_CHUNK && r < n; r += 32) {
+        const int64_t i = r + lane;
+        const bool v = i < n && i < b0 + ORD_CHUNK;
+        const int32_t c = v ? cell[i] : -1 - lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        int32_t base = 0;
+        if (v) base = run[c];
+        __syncwarp();
+        if (v) {
+            perm[base + __popc(peers & lt)] = int32_t(i);
+            if (lane == __ffs(peers) - 1) run[c] = base + __popc(peers);
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void cell_begin_kernel(const int32_t* __restrict__ offs, int K, int nchunk, int64_t n,
+                                  int32_t* __restrict__ cell_beg) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= K; c += gridDim.x * blockDim.x)
+        cell_beg[c] = c < K ? offs[int64_t(c) * nchunk] : int32_t(n);
+}
+
+// One CTA per cell: centre (mean of its points) and radius (largest distance
+// from that centre, computed in FP32; callers widen it by a margin).
+__global__ void cell_sphere_kernel(const float* __restrict__ X, int d, const int32_t* __restrict__ perm,
+                                   const int32_t* __restrict__ cell_beg, float* __restrict__ centre,
+                                   float* __restrict__ radius) {
+    __shared__ float s_part[8][64];
+    __shared__ float s_c[64];
+    __shared__ float s_r;
+    const int c = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int32_t b = cell_beg[c], e = cell_beg[c + 1];
+    // lanes own dimensions (lane, lane + 32); warps split the points
+    float a0 = 0.f, a1 = 0.f;
+    for (int32_t p = b + w; p < e; p += 8) {
+        const int64_t i = perm[p];
+        if (lane < d) a0 += X[i * d + lane];
+        if (lane + 32 < d) a1 += X[i * d + lane + 32];
+    }
+    s_part[w][lane] = a0;
+    s_part[w][lane + 32] = a1;
+    if (threadIdx.x == 0) s_r = 0.f;
+    __syncthreads();
+    if (threadIdx.x < 64) {
+        float s = 0.f;
+        for (int q = 0; q < 8; ++q) s += s_part[q][threadIdx.x];
+        s_c[threadIdx.x] = e > b ? s / float(e - b) : 0.f;
+    }
+    __syncthreads();
+    float rmax = 0.f;
+    for (int32_t p = b + threadIdx.x; p < e; p += blockDim.x) {
+        const int64_t i = perm[p];
+        float s = 0.f;
+        for (int q = 0; q < d; ++q) {
+            const float df = X[i * d + q] - s_c[q];
+            s = fmaf(df, df, s);
+        }
+        rmax = fmaxf(rmax, sqrtf(s));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    if (lane == 0) atomicMax(reinterpret_cast<unsigned int*>(&s_r), __float_as_uint(rmax));
+    __syncthreads();
+    for (int q = threadIdx.x; q < d; q += blockDim.x) centre[int64_t(c) * d + q] = s_c[q];
+    if (threadIdx.x == 0) radius[c] = e > b ? s_r : 0.f;
+}
+
+int knn_order_cells(int64_t n) {
+    int64_t K = n / 1024;
+    if (K < 16) K = 16;
+    if (K > 128) K = 128;
+    return int(K);
+}
+
+size_t knn_order_scratch_bytes(int64_t n, int d, int K) {
+    const int64_t nchunk = (n + ORD_CHUNK - 1) / ORD_CHUNK;
+    const size_t kc = size_t(K) * nchunk;
+    return Carve::round(size_t(ORD_SUB) * 4) + Carve::round(size_t(K) * 8) + Carve::round(size_t(K) * 4) +
+           Carve::round(size_t(K) * d * 4) + Carve::round(size_t(n) * 4) * 2 + 2 * Carve::round(kc * 4) +
+           Carve::round(scan_scratch_elems(int64_t(kc)) * 4) + 4096;
+}
+
+int knn_order(Ctx* c, const float* X, int64_t n, int d, int K, int32_t* perm, int32_t* cell_beg, float* centre,
+              float* radius, void* scratch, cudaStream_t st) {
+    if (d > 64) return set_error(c, DRGB_ERR_INVALID, "knn order: d > 64");
+    const int m = int(n < ORD_SUB ? n : ORD_SUB);
+    const int nchunk = int((n + ORD_CHUNK - 1) / ORD_CHUNK);
+    const size_t kc = size_t(K) * nchunk;
+    Carve cv(scratch);
+    float* mind = cv.take<float>(ORD_SUB);
+    unsigned long long* slot = cv.take<unsigned long long>(K);
+    int32_t* pivots = cv.take<int32_t>(K);
+    float* P = cv.take<float>(size_t(K) * d);
+    int32_t* cell = cv.take<int32_t>(n);
+    float* cdist = cv.take<float>(n);
+    int32_t* counts = cv.take<int32_t>(kc);
+    int32_t* offs = cv.take<int32_t>(kc);
+    int32_t* tmp = cv.take<int32_t>(scan_scratch_elems(int64_t(kc)));
+
+    DRGB_CUDA(c, cudaMemsetAsync(slot, 0, size_t(K) * 8, st));
+    const int fb = grid_for(m, 256, c->num_sms * 2);
+    for (int it = 0; it < K; ++it) {
+        fps_step_kernel<<<fb, 256, 0, st>>>(X, n, d, m, it, K, mind, slot, pivots);
+        DRGB_CHECK_LAUNCH(c);
+    }
+    gather_rows_kernel<<<grid_for(int64_t(K) * d, 256, c->num_sms), 256, 0, st>>>(X, d, pivots, K, P);
+    DRGB_CHECK_LAUNCH(c);
+    int rc = launch_knn_query(c, X, n, P, K, d, 1, cell, cdist, st);
+    if (rc) return rc;
+    cell_count_kernel<<<nchunk, 256, size_t(K) * 4, st>>>(cell, n, K, nchunk, counts);
+    DRGB_CHECK_LAUNCH(c);
+    if ((rc = exclusive_scan(c, counts, offs, int64_t(kc), tmp, st))) return rc;
+    const int sw = 4;  // warps (chunks) per CTA of the scatter
+    cell_scatter_kernel<<<(nchunk + sw - 1) / sw, 32 * sw, size_t(sw) * K * 4, st>>>(cell, n, K, nchunk, offs,
+                                                                                    perm);
+    DRGB_CHECK_LAUNCH(c);
+    cell_begin_kernel<<<1, 256, 0, st>>>(offs, K, nchunk, n, cell_beg);
+    DRGB_CHECK_LAUNCH(c);
+    cell_sphere_kernel<<<K, 256, 0, st>>>(X, d, perm, cell_beg, centre, radius);
+    DRGB_CHECK_LAUNCH(c);
+    return DRGB_OK;
+}
+
+}  // namespace drgb

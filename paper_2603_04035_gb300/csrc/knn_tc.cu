@@ -53,8 +53,13 @@ static constexpr int TC_TMEM_COLS = 512;               // two 256-column accumul
 static constexpr int TC_QCAP = 32;                     // per-thread candidate queue slots (one chunk)
 static constexpr size_t TC_QUEUE_BYTES = size_t(TC_EPI_WARPS) * 32 * TC_QCAP * 8;
 static constexpr size_t TC_THR_BYTES = size_t(2) * TC_BM * 4;   // per (column half, row) threshold
+static constexpr int TC_CELLS = 256;                   // most cells a schedule may hold
+static constexpr int TC_RING = 16;                     // tile-index ring (slots in flight < 16)
+static constexpr int TC_MAX_TILES = 98304;             // database tiles the visited-tile bitmap covers
+static constexpr size_t TC_SCHED_BYTES =
+    size_t(TC_CELLS) * 8 + TC_BM * 4 + TC_RING * 8 + 64 + TC_MAX_TILES / 8;
 static constexpr size_t TC_SMEM =
-    1024 + TC_A_BYTES + TC_STAGES * TC_B_BYTES + 256 + TC_QUEUE_BYTES + TC_THR_BYTES;
+    1024 + TC_A_BYTES + TC_STAGES * TC_B_BYTES + 256 + TC_QUEUE_BYTES + TC_THR_BYTES + TC_SCHED_BYTES;
 
 // Compare-exchange of (value, index) pairs i < l: afterwards the pair at i is
 // the smaller (asc) or the larger (!asc) of the two values.
@@ -157,10 +162,12 @@ __global__ void tc_mean_kernel(const float* __restrict__ partial, int nblk, int 
 
 // Warp per row: lanes own dimensions (lane, lane + 32).  Norms and residuals
 // are stored in the original units (the scale S is a power of two).
+// Position i of the operands holds point perm[i] (positions >= n: padding);
+// norms and residuals are stored at the point's own index.
 template <bool F16>
 __global__ void tc_stage_kernel(const float* __restrict__ X, int64_t n, int64_t n_pad, int d,
-                                const float* __restrict__ mean, op16* __restrict__ XA,
-                                op16* __restrict__ XB, float* __restrict__ norm,
+                                const float* __restrict__ mean, const int32_t* __restrict__ perm,
+                                op16* __restrict__ XA, op16* __restrict__ XB, float* __restrict__ norm,
                                 float* __restrict__ resid, unsigned int* __restrict__ maxbits) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
@@ -170,11 +177,12 @@ __global__ void tc_stage_kernel(const float* __restrict__ X, int64_t n, int64_t 
     for (int64_t i = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n_pad; i += warps) {
         float xc[2], xb[2];
         float sq = 0.f, rs = 0.f, cs = 0.f;
+        const int64_t src = i < n ? int64_t(perm[i]) : -1;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int c = lane + 32 * h;
             float v = 0.f;
-            if (i < n && c < d) v = (X[i * d + c] - mean[c]) * inv_S;
+            if (i < n && c < d) v = (X[src * d + c] - mean[c]) * inv_S;
             xc[h] = v;
             xb[h] = from_op<F16>(to_op<F16>(v));
             sq = fmaf(xb[h], xb[h], sq);
@@ -212,8 +220,8 @@ __global__ void tc_stage_kernel(const float* __restrict__ X, int64_t n, int64_t 
             const float flush = F16 ? 6.2e-5f * sqrtf(float(d)) : 0.f;
             const float delta = (sqrtf(rs) * (1.0f + 1e-6f) + 2.4e-7f * sqrtf(cs) + flush) * S;
             if (i < n) {
-                norm[i] = sq * S * S;
-                resid[i] = delta;
+                norm[src] = sq * S * S;
+                resid[src] = delta;
                 nmax = fmaxf(nmax, sq * S * S);
                 rmax = fmaxf(rmax, delta);
             }
@@ -229,11 +237,61 @@ __global__ void tc_stage_kernel(const float* __restrict__ X, int64_t n, int64_t 
 struct TcParams {
     int64_t n;
     int n_tiles;
-    int32_t* cand_idx;   // n x TC_KP
+    int32_t* cand_idx;   // n x TC_KP (point indices, row of the original point)
     float* cand_s;       // n x TC_KP
     int* status;
+    // spatial schedule: positions p (rows of the staged operands) hold point
+    // perm[p]; cell c holds positions [cell_beg[c], cell_beg[c+1]) and lies
+    // in the sphere (cell_c[c], cell_r[c]) (original units)
+    const float* X;
+    int d;
+    const int32_t* perm;
+    int K;
+    const int32_t* cell_beg;
+    const float* cell_c;
+    const float* cell_r;
+    const float* norm;          // per point, original units (see the staging)
+    const float* resid;
+    const unsigned int* maxbits;
+    float* lbstop;       // per point: no point of a skipped cell is nearer (original units)
 };
 
+// Bitonic sort (ascending by (value, index)) of TC_CELLS pairs in shared
+// memory by the whole CTA.
+__device__ __forceinline__ void cta_sort_pairs(float* v, int32_t* ix) {
+    for (int k = 2; k <= TC_CELLS; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < TC_CELLS; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool asc = (i & k) == 0;
+                    const float a = v[i], b = v[l];
+                    const int32_t x = ix[i], y = ix[l];
+                    const bool gt = a > b || (a == b && x > y);
+                    if (gt == asc) {
+                        v[i] = b;
+                        v[l] = a;
+                        ix[i] = y;
+                        ix[l] = x;
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// One CTA per 128 query positions.  Before the pipeline starts, the CTA bounds
+// its rows by a sphere, computes for every cell a lower bound on the distance
+// between any of its rows and any point of the cell, and sorts the cells by
+// that bound.  Warp 0 then streams the database tiles of the cells in that
+// order (each tile once), and stops at the first cell whose bound exceeds
+// every row's current upper bound on its 32nd-nearest distance: no point of
+// that or any later cell can enter any row's list.  The bound at which it
+// stopped is returned per row for the certificate.  Tile indices travel to
+// the MMA and epilogue warps through a small ring; a slot holding -1 ends the
+// stream.
 template <bool F16>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams P) {
@@ -255,10 +313,19 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     int2* q = reinterpret_cast<int2*>(reinterpret_cast<uint8_t*>(bars) + 256);
     // per (column half, row): the 32nd-best value that half holds so far
     float* s_thr = reinterpret_cast<float*>(q + TC_EPI_WARPS * 32 * TC_QCAP);
+    // schedule: sorted cell bounds and cells, per-row distance bounds, the
+    // tile ring (slot number and tile), misc words, visited-tile bitmap
+    float* s_lb = s_thr + 2 * TC_BM;
+    int32_t* s_cl = reinterpret_cast<int32_t*>(s_lb + TC_CELLS);
+    volatile float* s_U = reinterpret_cast<volatile float*>(s_cl + TC_CELLS);
+    volatile int32_t* ring_t = reinterpret_cast<volatile int32_t*>(s_U + TC_BM);
+    volatile int32_t* ring_tile = ring_t + TC_RING;
+    float* s_misc = const_cast<float*>(reinterpret_cast<volatile float*>(ring_tile + TC_RING));  // [16]
+    uint32_t* s_done = reinterpret_cast<uint32_t*>(s_misc + 16);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t q0 = int64_t(blockIdx.x) * TC_BM;
-    const int T = P.n_tiles;
+    const int nrow = int(P.n - q0 < TC_BM ? P.n - q0 : TC_BM);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
@@ -280,27 +347,131 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                      ::"r"(smem_u32(tmem_slot)), "r"(TC_TMEM_COLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    // ---------------- schedule (all warps; the B ring is still idle and holds
+    // the block's rows meanwhile)
+    {
+        float* s_rows = reinterpret_cast<float*>(sB);    // [TC_BM][64]
+        float* s_cen = s_rows + TC_BM * 64;              // [64]
+        for (int t = threadIdx.x; t < TC_BM * 64; t += blockDim.x) {
+            const int r = t >> 6, c = t & 63;
+            s_rows[t] = (r < nrow && c < P.d) ? P.X[int64_t(P.perm[q0 + r]) * P.d + c] : 0.f;
+        }
+        for (int t = threadIdx.x; t < TC_MAX_TILES / 32; t += blockDim.x) s_done[t] = 0u;
+        if (threadIdx.x < TC_BM) s_U[threadIdx.x] = INFINITY;
+        if (threadIdx.x < TC_RING) {
+            ring_t[threadIdx.x] = -1;
+            ring_tile[threadIdx.x] = -1;
+        }
+        if (threadIdx.x == 0) {
+            s_misc[0] = 0.f;        // block radius (bits are compared as unsigned)
+            s_misc[1] = INFINITY;   // stopping bound
+        }
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            float sum = 0.f;
+            for (int r = 0; r < nrow; ++r) sum += s_rows[r * 64 + threadIdx.x];
+            s_cen[threadIdx.x] = sum / float(nrow > 0 ? nrow : 1);
+        }
+        __syncthreads();
+        if (threadIdx.x < nrow) {
+            float sq = 0.f;
+            for (int c = 0; c < P.d; ++c) {
+                const float df = s_rows[threadIdx.x * 64 + c] - s_cen[c];
+                sq = fmaf(df, df, sq);
+            }
+            atomicMax(reinterpret_cast<unsigned int*>(&s_misc[0]), __float_as_uint(sqrtf(sq)));
+        }
+        __syncthreads();
+        const float rb = s_misc[0];
+        float cb2 = 0.f;
+        for (int c = 0; c < P.d; ++c) cb2 = fmaf(s_cen[c], s_cen[c], cb2);
+        const float cbn = sqrtf(cb2);
+        for (int ci = threadIdx.x; ci < TC_CELLS; ci += blockDim.x) {
+            float lb = INFINITY;
+            if (ci < P.K && P.cell_beg[ci + 1] > P.cell_beg[ci]) {
+                float dd = 0.f, cc = 0.f;
+                for (int c = 0; c < P.d; ++c) {
+                    const float v = P.cell_c[int64_t(ci) * P.d + c];
+                    const float df = s_cen[c] - v;
+                    dd = fmaf(df, df, dd);
+                    cc = fmaf(v, v, cc);
+                }
+                const float dist = sqrtf(dd), rc = P.cell_r[ci];
+                // FP32 rounding of the centres, radii and this distance is
+                // covered by a relative margin on everything involved
+                lb = fmaxf(0.f, dist - rb - rc - 1e-5f * (dist + rb + rc + cbn + sqrtf(cc)));
+            }
+            s_lb[ci] = lb;
+            s_cl[ci] = ci;
+        }
+        cta_sort_pairs(s_lb, s_cl);   // ends with __syncthreads
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        // ---------------- TMA producer
+        // ---------------- schedule + TMA producer (lane 0 issues)
+        bool stop_ok = true;
         if (lane == 0) {
             mbar_expect_tx(a_full, TC_A_BYTES);
             tma_load_2d(sA, &tmA, 0, int(q0), a_full);
-            int t = 0;
-            for (; t < T; ++t) {
-                const int s = t % TC_STAGES;
-                if (t >= TC_STAGES && !mbar_wait(&empty[s], ((t / TC_STAGES) & 1) ^ 1, abort_flag, P.status))
-                    break;
-                mbar_expect_tx(&full[s], TC_B_BYTES);
-                tma_load_2d(sB + s * TC_B_BYTES, &tmB, 0, t * TC_BN, &full[s]);
+        }
+        int t = 0;
+        float lbstop = INFINITY;
+        for (int ci = 0; ci < P.K && stop_ok; ++ci) {
+            const float lb = s_lb[ci];
+            if (!(lb < INFINITY)) break;  // empty cells sort last
+            float u = fmaxf(fmaxf(s_U[lane], s_U[lane + 32]), fmaxf(s_U[lane + 64], s_U[lane + 96]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) u = fmaxf(u, __shfl_xor_sync(0xffffffffu, u, o));
+            if (lb > u) {
+                lbstop = lb;
+                break;
             }
-            if (t < T) {
+            const int cell = s_cl[ci];
+            const int tb = P.cell_beg[cell] / TC_BN, te = (P.cell_beg[cell + 1] - 1) / TC_BN;
+            for (int tile = tb; tile <= te && stop_ok; ++tile) {
+                if (P.K > 1) {  // one cell covers every tile once: no bitmap needed
+                    int seen = 0;
+                    if (lane == 0) {
+                        const uint32_t bit = 1u << (tile & 31);
+                        seen = (s_done[tile >> 5] & bit) != 0;
+                        s_done[tile >> 5] |= bit;
+                    }
+                    if (__shfl_sync(0xffffffffu, seen, 0)) continue;
+                }
+                if (lane == 0) {
+                    const int s = t % TC_STAGES;
+                    if (t >= TC_STAGES && !mbar_wait(&empty[s], ((t / TC_STAGES) & 1) ^ 1, abort_flag, P.status)) {
+                        stop_ok = false;
+                    } else {
+                        ring_tile[t % TC_RING] = tile;
+                        __threadfence_block();
+                        ring_t[t % TC_RING] = t;
+                        mbar_expect_tx(&full[s], TC_B_BYTES);
+                        tma_load_2d(sB + s * TC_B_BYTES, &tmB, 0, tile * TC_BN, &full[s]);
+                    }
+                }
+                stop_ok = __shfl_sync(0xffffffffu, stop_ok, 0);
+                ++t;
+            }
+        }
+        if (lane == 0) {
+            s_misc[1] = lbstop;
+            if (stop_ok) {
+                // end of the stream: slot t carries tile -1 (no data)
+                const int s = t % TC_STAGES;
+                if (t < TC_STAGES || mbar_wait(&empty[s], ((t / TC_STAGES) & 1) ^ 1, abort_flag, P.status)) {
+                    ring_tile[t % TC_RING] = -1;
+                    __threadfence_block();
+                    ring_t[t % TC_RING] = t;
+                    mbar_arrive(&full[s]);
+                }
+            } else {
                 // aborted: let the loads already issued land before the CTA exits
-                for (int u = (t > TC_STAGES ? t - TC_STAGES : 0); u < t; ++u) {
+                for (int u = (t > TC_STAGES ? t - TC_STAGES : 0); u < t - 1; ++u) {
                     const unsigned long long t0 = global_timer();
                     while (!mbar_try(&full[u % TC_STAGES], (u / TC_STAGES) & 1) &&
                            global_timer() - t0 < 100000000ull) {
@@ -315,12 +486,16 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             const uint32_t idesc = idesc_f16kind(TC_BM, TC_BN, F16);
             const uint64_t adesc = sdesc_sw128(smem_u32(sA));
             bool ok = mbar_wait(a_full, 0, abort_flag, P.status);
-            for (int t = 0; ok && t < T; ++t) {
+            for (int t = 0; ok; ++t) {
                 const int s = t % TC_STAGES, buf = t & 1, use = t >> 1;
                 if (t >= 2 && !mbar_wait(&acc_empty[buf], (use & 1) ^ 1, abort_flag, P.status)) break;
                 tc_fence_after();
                 if (!mbar_wait(&full[s], (t / TC_STAGES) & 1, abort_flag, P.status)) break;
                 tc_fence_after();
+                if (ring_t[t % TC_RING] != t || ring_tile[t % TC_RING] < 0) {
+                    mbar_arrive(&acc_full[buf]);  // end of the stream: pass it on
+                    break;
+                }
                 const uint64_t bdesc = sdesc_sw128(smem_u32(sB + s * TC_B_BYTES));
 #pragma unroll
                 for (int k = 0; k < TC_K / 16; ++k)  // K step of 16 BF16 = 32 bytes = 2 descriptor units
@@ -347,6 +522,17 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             L[s] = INFINITY;
             I[s] = -1;
         }
+        // this row's conversion of a threshold on s into an upper bound on the
+        // distance (original units) of its 32nd candidate
+        const float S = operand_scale<F16>(P.maxbits);
+        const float r_max = __uint_as_float(P.maxbits[1]), n_max = __uint_as_float(P.maxbits[0]);
+        float ni = 0.f, di = 0.f;
+        if (row < nrow) {
+            const int64_t g = P.perm[q0 + row];
+            ni = P.norm[g];
+            di = P.resid[g];
+        }
+        const float eps_i = 6.103515625e-05f * (ni + n_max);
         // Candidates below the row's threshold are appended to this thread's
         // queue (slot s at q[s * 256 + tid], conflict-free).  The threshold
         // is the smaller of the two column halves' 32nd-best values: a value at
@@ -384,13 +570,27 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             bitonic_merge_asc<TC_KP>(L, I);
             qn = 0;
             *thr_mine = L[TC_KP - 1];
+            const float thr = fminf(L[TC_KP - 1], *thr_other);
+            if (row < nrow && thr < INFINITY)
+                s_U[row] = (sqrtf(fmaxf(ni + thr * (S * S) + eps_i, 0.f)) + di + r_max) * (1.0f + 1e-5f);
         };
-        for (int t = 0; t < T; ++t) {
+        for (int t = 0;; ++t) {
             const int buf = t & 1, use = t >> 1;
             if (!mbar_wait(&acc_full[buf], use & 1, abort_flag, P.status)) break;
             tc_fence_after();
+            // the slot's tile (written before its data was requested)
+            int tile = -1;
+            {
+                const unsigned long long w0 = global_timer();
+                while (ring_t[t % TC_RING] != t) {
+                    if (*abort_flag || global_timer() - w0 > TC_TIMEOUT_NS) break;
+                }
+                __threadfence_block();
+                if (ring_t[t % TC_RING] == t) tile = ring_tile[t % TC_RING];
+            }
+            if (tile < 0) break;
             const uint32_t tbase = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(buf * TC_BN + half * 128);
-            const int32_t j0 = t * TC_BN + half * 128;
+            const int32_t j0 = tile * TC_BN + half * 128;
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 float v[32];
@@ -451,8 +651,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             mi[(half * TC_BM + row) * TC_KP + s] = I[s];
         }
         asm volatile("bar.sync 1, %0;" ::"r"(TC_EPI_WARPS * 32) : "memory");
-        const int64_t g = q0 + row;
-        if (half == 0 && g < P.n && !*abort_flag) {
+        if (half == 0 && row < nrow && !*abort_flag) {
+            const int64_t g = P.perm[q0 + row];
             const float* As = ms + row * TC_KP;
             const int32_t* Ai = mi + row * TC_KP;
             const float* Bs = ms + (TC_BM + row) * TC_KP;
@@ -460,10 +660,12 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             int a = 0, b = 0;
             for (int o = 0; o < TC_KP; ++o) {
                 const bool take_a = (As[a] < Bs[b]) || (As[a] == Bs[b] && uint32_t(Ai[a]) <= uint32_t(Bi[b]));
+                const int32_t pos = take_a ? Ai[a] : Bi[b];
                 P.cand_s[g * TC_KP + o] = take_a ? As[a] : Bs[b];
-                P.cand_idx[g * TC_KP + o] = take_a ? Ai[a] : Bi[b];
+                P.cand_idx[g * TC_KP + o] = pos >= 0 ? P.perm[pos] : -1;
                 if (take_a) ++a; else ++b;
             }
+            P.lbstop[g] = s_misc[1];
         }
     }
     tc_fence_before();
@@ -480,7 +682,8 @@ template <int K, bool F16>
 __global__ void tc_rerank_kernel(const float* __restrict__ X, int64_t n, int d, int k,
                                  const int32_t* __restrict__ cand_idx, const float* __restrict__ cand_s,
                                  const float* __restrict__ norm, const float* __restrict__ resid,
-                                 const unsigned int* __restrict__ maxbits, int32_t* __restrict__ idx_out,
+                                 const unsigned int* __restrict__ maxbits, const float* __restrict__ lbstop,
+                                 int32_t* __restrict__ idx_out,
                                  float* __restrict__ dist_out, int32_t* __restrict__ fail_rows,
                                  int32_t* __restrict__ fail_count) {
     const float n_max = __uint_as_float(maxbits[0]);
@@ -523,7 +726,8 @@ __global__ void tc_rerank_kernel(const float* __restrict__ X, int64_t n, int d, 
         const float ni = norm[i];
         const float eps = 6.103515625e-05f * (ni + n_max);  // 2^-14 (n_i + n_max)
         const float lb2 = ni + s_thr - eps;
-        const float lb = sqrtf(fmaxf(lb2, 0.f)) - resid[i] - r_max;
+        // points never compared lie in skipped cells, beyond lbstop
+        const float lb = fminf(sqrtf(fmaxf(lb2, 0.f)) - resid[i] - r_max, lbstop[i]);
         float dk2 = 0.f;
 #pragma unroll
         for (int s = 0; s < K; ++s)
@@ -544,16 +748,34 @@ __global__ void tc_rerank_kernel(const float* __restrict__ X, int64_t n, int d, 
     }
 }
 
+// Positions past n hold themselves (padding); with a single cell the whole
+// order is the identity and the cell covers every position.
+__global__ void tc_identity_kernel(int32_t* __restrict__ perm, int64_t n, int64_t n_pad, bool all,
+                                   int32_t* __restrict__ cell_beg, float* __restrict__ cell_r) {
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < n_pad; p += int64_t(gridDim.x) * blockDim.x)
+        if (all || p >= n) perm[p] = int32_t(p);
+    if (all && blockIdx.x == 0 && threadIdx.x == 0) {
+        cell_beg[0] = 0;
+        cell_beg[1] = int32_t(n);
+        cell_r[0] = INFINITY;
+    }
+}
+
 // ------------------------------------------------------------------ host
 bool knn_tc_preferred(int64_t n, int d, int k) { return n >= 4096 && d + 3 <= TC_K && k < TC_KP; }
 
 // partial lists of the exact re-scan of uncertified rows (up to this many bytes)
 static constexpr size_t TC_PART_BYTES = size_t(64) << 20;
 
+static int tc_cells(int64_t n_pad, int64_t n) { return n_pad / TC_BN > TC_MAX_TILES ? 1 : knn_order_cells(n); }
+
 static size_t tc_scratch_bytes(int64_t n, int d, int64_t n_pad, int nblk) {
+    const int K = tc_cells(n_pad, n);
     return Carve::round(size_t(nblk) * d * 4) + Carve::round(d * 4) + 2 * Carve::round(n_pad * TC_K * 2) +
            2 * Carve::round(n_pad * 4) + Carve::round(64) + 2 * Carve::round(n_pad * TC_KP * 4) +
-           Carve::round(n * 4) + Carve::round(64) + TC_PART_BYTES + 8192;
+           Carve::round(n * 4) + Carve::round(64) + TC_PART_BYTES + Carve::round(n_pad * 4) +
+           Carve::round((TC_CELLS + 1) * 4) + Carve::round(size_t(TC_CELLS) * d * 4) + Carve::round(TC_CELLS * 4) +
+           Carve::round(n * 4) + (K > 1 ? knn_order_scratch_bytes(n, d, K) : 0) + 16384;
 }
 
 static constexpr int TC_COLSUM_BLOCKS = 256;
@@ -585,6 +807,13 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
     int32_t* fail_rows = cv.take<int32_t>(n);
     int32_t* fail_count = cv.take<int32_t>(16);
     void* part = cv.take<char>(TC_PART_BYTES);
+    int32_t* perm = cv.take<int32_t>(n_pad);
+    int32_t* cell_beg = cv.take<int32_t>(TC_CELLS + 1);
+    float* cell_c = cv.take<float>(size_t(TC_CELLS) * d);
+    float* cell_r = cv.take<float>(TC_CELLS);
+    float* lbstop = cv.take<float>(n);
+    const int K = tc_cells(n_pad, n);
+    void* order_scratch = K > 1 ? cv.take<char>(knn_order_scratch_bytes(n, d, K)) : nullptr;
 
     DRGB_CUDA(c, cudaMemsetAsync(maxbits, 0, 64, st));
     DRGB_CUDA(c, cudaMemsetAsync(fail_count, 0, 64, st));
@@ -596,8 +825,14 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
         tc_absmax_kernel<<<grid_for(n * d, 256, c->num_sms * 8), 256, 0, st>>>(X, n, d, mean, maxbits);
         DRGB_CHECK_LAUNCH(c);
     }
-    tc_stage_kernel<F16><<<grid_for(n_pad, 8, c->num_sms * 16), 256, 0, st>>>(X, n, n_pad, d, mean, XA, XB,
-                                                                              norm, resid, maxbits);
+    // spatial order (K > 1) or the identity with one cell holding everything
+    if (K == 1) DRGB_CUDA(c, cudaMemsetAsync(cell_c, 0, size_t(d) * 4, st));
+    tc_identity_kernel<<<grid_for(n_pad, 256, c->num_sms * 8), 256, 0, st>>>(perm, n, n_pad, K == 1, cell_beg,
+                                                                           cell_r);
+    DRGB_CHECK_LAUNCH(c);
+    if (K > 1 && (rc = knn_order(c, X, n, d, K, perm, cell_beg, cell_c, cell_r, order_scratch, st))) return rc;
+    tc_stage_kernel<F16><<<grid_for(n_pad, 8, c->num_sms * 16), 256, 0, st>>>(X, n, n_pad, d, mean, perm, XA,
+                                                                              XB, norm, resid, maxbits);
     DRGB_CHECK_LAUNCH(c);
 
     CUtensorMap mA, mB;
@@ -615,6 +850,17 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
     P.cand_idx = cand_idx;
     P.cand_s = cand_s;
     P.status = c->d_status;
+    P.X = X;
+    P.d = d;
+    P.perm = perm;
+    P.K = K;
+    P.cell_beg = cell_beg;
+    P.cell_c = cell_c;
+    P.cell_r = cell_r;
+    P.norm = norm;
+    P.resid = resid;
+    P.maxbits = maxbits;
+    P.lbstop = lbstop;
     const int grid = int((n + TC_BM - 1) / TC_BM);
     if ((rc = stage_mark(c, 6, st))) return rc;
     knn_tc_kernel<F16><<<grid, TC_THREADS, TC_SMEM, st>>>(mA, mB, P);
@@ -623,11 +869,11 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
 
     const int rb = grid_for(n, 128, c->num_sms * 8);
     if (k <= 16)
-        tc_rerank_kernel<16, F16><<<rb, 128, 0, st>>>(X, n, d, k, cand_idx, cand_s, norm, resid, maxbits, idx_out,
-                                                 dist_out, fail_rows, fail_count);
+        tc_rerank_kernel<16, F16><<<rb, 128, 0, st>>>(X, n, d, k, cand_idx, cand_s, norm, resid, maxbits, lbstop,
+                                                 idx_out, dist_out, fail_rows, fail_count);
     else
-        tc_rerank_kernel<32, F16><<<rb, 128, 0, st>>>(X, n, d, k, cand_idx, cand_s, norm, resid, maxbits, idx_out,
-                                                 dist_out, fail_rows, fail_count);
+        tc_rerank_kernel<32, F16><<<rb, 128, 0, st>>>(X, n, d, k, cand_idx, cand_s, norm, resid, maxbits, lbstop,
+                                                 idx_out, dist_out, fail_rows, fail_count);
     DRGB_CHECK_LAUNCH(c);
     // exact FP32 scan of the uncertified rows (row list and count on the device)
     DRGB_CUDA(c, cudaMemcpyAsync(c->d_counter, fail_count, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
