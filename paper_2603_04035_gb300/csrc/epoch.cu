@@ -405,9 +405,11 @@ __global__ void __launch_bounds__(256, 3) epoch_force_kernel(const __grid_consta
                 for (int s = 0; s < LD; ++s) {
                     const int32_t e = p0 + 32 * (s0 + s) + lane;
                     const bool in = e < pe;
-                    qv[s] = in ? A.q[e] : 0u;  // q = 0 never fires
-                    jv[s] = in ? A.col[e] : 0;
-                    hv[s] = in ? A.row_of[e] : -1;
+                    // the CSR streams through once per epoch: evict-first
+                    // loads keep L2 for the gathered positions Y
+                    qv[s] = in ? __ldcs(A.q + e) : 0u;  // q = 0 never fires
+                    jv[s] = in ? __ldcs(A.col + e) : 0;
+                    hv[s] = in ? __ldcs(A.row_of + e) : -1;
                 }
 #pragma unroll
                 for (int s = 0; s < LD; ++s) {
