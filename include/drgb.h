@@ -139,9 +139,16 @@ int drgb_stage_times(drgb_ctx* ctx, float* ms, int max);
 int drgb_knn_graph(drgb_ctx* ctx, const float* X, int64_t n, int32_t d, int32_t k,
                    int32_t mode, int32_t* idx_out, float* dist_out, void* stream);
 
-/* Number of rows whose BF16 candidate set was not certified during the last
- * mode-2 drgb_knn_graph call on `ctx` (synchronous: waits for that call). */
+/* Number of rows whose 16-bit candidate set was not certified during the last
+ * tensor-core (mode 2 or 3) drgb_knn_graph call on `ctx` (synchronous: waits
+ * for that call). */
 int drgb_knn_uncertified(drgb_ctx* ctx, int64_t* count, void* stream);
+
+/* Work of the last tensor-core drgb_knn_graph call on `ctx`: the number of
+ * (128-row block, 256-column tile) products the distance GEMM computed, and
+ * the number a full scan would compute; blocks skip the tiles of cells that
+ * their distance bound rules out (synchronous). */
+int drgb_knn_tiles(drgb_ctx* ctx, int64_t* done, int64_t* total, void* stream);
 
 /* -------------------------------------------------------- fuzzy weights */
 

@@ -33,7 +33,7 @@ from ._lib import MAX_K, Params  # noqa: F401
 __all__ = ["DrgbError", "Graph", "UMAP", "knn_graph", "fuzzy_weights", "find_ab",
            "init_embedding", "embed_epoch", "embed_epochs", "fit_transform", "eval_recall",
            "eval_trust", "default_params", "context", "knn_uncertified", "launch_count",
-           "set_profiling", "stage_times", "set_tuning", "get_tuning", "fit_transform_batched",
+           "set_profiling", "stage_times", "set_tuning", "get_tuning", "knn_tiles", "fit_transform_batched",
            "autotune_epoch", "mlp_param_count", "mlp_init", "mlp_sample", "mlp_grad", "mlp_train",
            "mlp_embed", "ParametricUMAP", "transform"]
 
@@ -177,6 +177,16 @@ def knn_uncertified(device=None) -> int:
     dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
     _check(_lib.load().drgb_knn_uncertified(ctx, C.byref(out), _stream(dev)), ctx)
     return out.value
+
+
+def knn_tiles(device=None) -> tuple[int, int]:
+    """(tile products computed, tile products of a full scan) of the last
+    tensor-core k-NN call on the device."""
+    ctx = context(device)
+    done, total = C.c_int64(), C.c_int64()
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    _check(_lib.load().drgb_knn_tiles(ctx, C.byref(done), C.byref(total), _stream(dev)), ctx)
+    return done.value, total.value
 
 
 # ---------------------------------------------------------------- fuzzy graph

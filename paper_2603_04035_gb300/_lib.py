@@ -57,6 +57,7 @@ SIGNATURES = {
     "drgb_stage_times": (C.c_int, [vp, C.POINTER(C.c_float), C.c_int]),
     "drgb_knn_graph": (C.c_int, [vp, vp, i64, i32, i32, i32, vp, vp, vp]),
     "drgb_knn_uncertified": (C.c_int, [vp, C.POINTER(C.c_int64), vp]),
+    "drgb_knn_tiles": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), vp]),
     "drgb_fuzzy_weights": (C.c_int, [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, i64, vp, vp, vp]),
     "drgb_fuzzy_weights_static": (C.c_int, [vp, vp, i64, i32, i32, vp, vp, vp, vp, i64, vp, vp, vp]),
     "drgb_find_ab": (C.c_int, [f32, f32, C.POINTER(C.c_float), C.POINTER(C.c_float)]),

@@ -21,7 +21,8 @@ struct Ctx {
     void* scratch = nullptr;      // grown on demand, 256-byte aligned carve-outs
     size_t scratch_bytes = 0;
     int* d_status = nullptr;      // device status word (0 = ok, else DRGB_ERR_*)
-    unsigned long long* d_counter = nullptr;  // diagnostic counter (uncertified rows)
+    unsigned long long* d_counter = nullptr;  // [0] uncertified rows, [4] k-NN tile products computed
+    int64_t knn_tiles_total = 0;              // tile products of a full scan (last tensor-core k-NN)
     int64_t launches = 0;         // kernels launched (host-side count)
     int epoch_warps = 8;          // warps per CTA of the epoch force kernel (tuning)
     int knn_tile_n = 256;         // database tile width of the tensor-core k-NN (tuning)

@@ -254,6 +254,7 @@ struct TcParams {
     const float* resid;
     const unsigned int* maxbits;
     float* lbstop;       // per point: no point of a skipped cell is nearer (original units)
+    unsigned long long* tiles_done;  // += tiles this CTA multiplied
 };
 
 // Bitonic sort (ascending by (value, index)) of TC_CELLS pairs in shared
@@ -460,6 +461,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         }
         if (lane == 0) {
             s_misc[1] = lbstop;
+            atomicAdd(P.tiles_done, static_cast<unsigned long long>(t));
             if (stop_ok) {
                 // end of the stream: slot t carries tile -1 (no data)
                 const int s = t % TC_STAGES;
@@ -861,6 +863,9 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
     P.resid = resid;
     P.maxbits = maxbits;
     P.lbstop = lbstop;
+    P.tiles_done = c->d_counter + 4;
+    c->knn_tiles_total = int64_t((n + TC_BM - 1) / TC_BM) * (n_pad / TC_BN);
+    DRGB_CUDA(c, cudaMemsetAsync(c->d_counter + 4, 0, 8, st));
     const int grid = int((n + TC_BM - 1) / TC_BM);
     if ((rc = stage_mark(c, 6, st))) return rc;
     knn_tc_kernel<F16><<<grid, TC_THREADS, TC_SMEM, st>>>(mA, mB, P);
@@ -889,6 +894,16 @@ int knn_tc(Ctx* c, const float* X, int64_t n, int d, int k, bool f16, int32_t* i
 }
 
 }  // namespace drgb
+
+extern "C" int drgb_knn_tiles(drgb_ctx* c, int64_t* done, int64_t* total, void* stream) {
+    if (!c || !done || !total) return DRGB_ERR_INVALID;
+    unsigned long long v = 0;
+    DRGB_CUDA(c, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    DRGB_CUDA(c, cudaMemcpy(&v, c->d_counter + 4, sizeof(v), cudaMemcpyDeviceToHost));
+    *done = int64_t(v);
+    *total = c->knn_tiles_total;
+    return DRGB_OK;
+}
 
 extern "C" int drgb_knn_uncertified(drgb_ctx* c, int64_t* count, void* stream) {
     if (!c || !count) return DRGB_ERR_INVALID;
