@@ -1,49 +1,85 @@
 // Spatial ordering of the points for the tensor-core k-NN: K pivots chosen by
-// farthest-point sampling on a strided subsample, every point assigned to its
+// farthest-point sampling on a strided subsample (one CTA), every point assigned to its
 // nearest pivot (exact FP32 scan), a stable counting sort by pivot ("cell"),
 // and a bounding sphere per cell.  The order only decides which database
 // tiles a query block visits first and which it may skip; the k-NN result
 // does not depend on it (skipped cells enter the certificate as a distance
 // bound, and rows the bound cannot certify are scanned exactly).
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "knn.cuh"
 
 namespace drgb {
 
-static constexpr int ORD_SUB = 16384;     // subsample size for the pivot choice
+static constexpr int ORD_SUB = 1536;      // subsample size for the pivot choice (one CTA)
+static constexpr int ORD_THREADS = 1024;
 static constexpr int ORD_CHUNK = 4096;    // points per counting-sort chunk (one warp each)
 
-// Farthest-point step `it` (0 <= it < K): pivot it is the first subsample
-// point (it = 0) or the point step it-1 found farthest (slot[it-1]); it is
-// recorded in pivots[it] and lowers every subsample point's squared distance
-// to the pivot set.  Unless this is the last step, the farthest point (ties:
-// lowest subsample index) goes to slot[it] as (distance bits << 32) | ~index.
-__global__ void fps_step_kernel(const float* __restrict__ X, int64_t n, int d, int m, int it, int K,
-                                float* __restrict__ mind, unsigned long long* __restrict__ slot,
-                                int32_t* __restrict__ pivots) {
-    const int32_t p_sub = it > 0 ? int32_t(~uint32_t(slot[it - 1] & 0xffffffffull)) : 0;
-    const int64_t p = int64_t(p_sub) * n / m;
-    if (blockIdx.x == 0 && threadIdx.x == 0) pivots[it] = int32_t(p);
-    if (it == K - 1) return;
-    unsigned long long best = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-        const int64_t g = int64_t(i) * n / m;
-        float s = 0.f;
-        for (int c = 0; c < d; ++c) {
-            const float df = X[g * d + c] - X[p * d + c];
-            s = fmaf(df, df, s);
+// Subsample point i of m: splitmix64(i) mod n, a fixed pseudo-random sample
+// (a strided sample aliases with periodic point orders such as labels i mod c).
+__device__ __forceinline__ int64_t sub_point(int i, int64_t n, int m) {
+    (void)m;
+    uint64_t z = uint64_t(i) + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return int64_t(z % uint64_t(n));
+}
+
+// Farthest-point sampling in one CTA: the subsample is held in shared memory
+// as FP16 (the pivot choice is a heuristic; any deterministic choice is
+// valid).  Pivot 0 is the first subsample point;
+// pivot it + 1 is the subsample point farthest from pivots 0..it (ties: the
+// lowest subsample index).
+__global__ void __launch_bounds__(ORD_THREADS) fps_cta_kernel(const float* __restrict__ X, int64_t n, int d, int m,
+                                                           int K, int32_t* __restrict__ pivots) {
+    extern __shared__ __align__(16) uint8_t s_raw[];
+    float* s_min = reinterpret_cast<float*>(s_raw);                 // [m]
+    unsigned long long* s_best = reinterpret_cast<unsigned long long*>(s_min + ORD_SUB);  // [32]
+    __half* s_x = reinterpret_cast<__half*>(s_best + 32);          // [m][d]
+    for (int t = threadIdx.x; t < m * d; t += blockDim.x) {
+        const int i = t / d, c = t % d;
+        s_x[t] = __float2half_rn(X[sub_point(i, n, m) * d + c]);
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s_min[i] = INFINITY;
+    __syncthreads();
+    int p = 0;
+    for (int it = 0; it < K; ++it) {
+        if (threadIdx.x == 0) pivots[it] = int32_t(sub_point(p, n, m));
+        if (it == K - 1) break;
+        unsigned long long best = 0;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            float sq = 0.f;
+            for (int c = 0; c < d; ++c) {
+                const float df = __half2float(s_x[i * d + c]) - __half2float(s_x[p * d + c]);
+                sq = fmaf(df, df, sq);
+            }
+            const float v = fminf(s_min[i], sq);
+            s_min[i] = v;
+            const unsigned long long key = (uint64_t(__float_as_uint(v)) << 32) | uint64_t(~uint32_t(i));
+            best = key > best ? key : best;
         }
-        const float v = it == 0 ? s : fminf(mind[i], s);
-        mind[i] = v;
-        const unsigned long long key = (uint64_t(__float_as_uint(v)) << 32) | uint64_t(~uint32_t(i));
-        best = key > best ? key : best;
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
-        best = other > best ? other : best;
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+            best = other > best ? other : best;
+        }
+        if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            unsigned long long b = threadIdx.x < (blockDim.x >> 5) ? s_best[threadIdx.x] : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xffffffffu, b, o);
+                b = other > b ? other : b;
+            }
+            if (threadIdx.x == 0) s_best[0] = b;
+        }
+        __syncthreads();
+        p = int(~uint32_t(s_best[0] & 0xffffffffull));
+        __syncthreads();
     }
-    if ((threadIdx.x & 31) == 0) atomicMax(slot + it, best);
 }
 
 __global__ void gather_rows_kernel(const float* __restrict__ X, int d, const int32_t* __restrict__ rows, int count,
@@ -155,7 +191,7 @@ int knn_order_cells(int64_t n) {
 size_t knn_order_scratch_bytes(int64_t n, int d, int K) {
     const int64_t nchunk = (n + ORD_CHUNK - 1) / ORD_CHUNK;
     const size_t kc = size_t(K) * nchunk;
-    return Carve::round(size_t(ORD_SUB) * 4) + Carve::round(size_t(K) * 8) + Carve::round(size_t(K) * 4) +
+    return Carve::round(size_t(K) * 4) +
            Carve::round(size_t(K) * d * 4) + Carve::round(size_t(n) * 4) * 2 + 2 * Carve::round(kc * 4) +
            Carve::round(scan_scratch_elems(int64_t(kc)) * 4) + 4096;
 }
@@ -167,8 +203,6 @@ int knn_order(Ctx* c, const float* X, int64_t n, int d, int K, int32_t* perm, in
     const int nchunk = int((n + ORD_CHUNK - 1) / ORD_CHUNK);
     const size_t kc = size_t(K) * nchunk;
     Carve cv(scratch);
-    float* mind = cv.take<float>(ORD_SUB);
-    unsigned long long* slot = cv.take<unsigned long long>(K);
     int32_t* pivots = cv.take<int32_t>(K);
     float* P = cv.take<float>(size_t(K) * d);
     int32_t* cell = cv.take<int32_t>(n);
@@ -177,12 +211,10 @@ int knn_order(Ctx* c, const float* X, int64_t n, int d, int K, int32_t* perm, in
     int32_t* offs = cv.take<int32_t>(kc);
     int32_t* tmp = cv.take<int32_t>(scan_scratch_elems(int64_t(kc)));
 
-    DRGB_CUDA(c, cudaMemsetAsync(slot, 0, size_t(K) * 8, st));
-    const int fb = grid_for(m, 256, c->num_sms * 2);
-    for (int it = 0; it < K; ++it) {
-        fps_step_kernel<<<fb, 256, 0, st>>>(X, n, d, m, it, K, mind, slot, pivots);
-        DRGB_CHECK_LAUNCH(c);
-    }
+    const size_t fsm = size_t(ORD_SUB) * 4 + 32 * 8 + size_t(m) * d * 2;
+    DRGB_CUDA(c, cudaFuncSetAttribute(fps_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fsm)));
+    fps_cta_kernel<<<1, ORD_THREADS, fsm, st>>>(X, n, d, m, K, pivots);
+    DRGB_CHECK_LAUNCH(c);
     gather_rows_kernel<<<grid_for(int64_t(K) * d, 256, c->num_sms), 256, 0, st>>>(X, d, pivots, K, P);
     DRGB_CHECK_LAUNCH(c);
     int rc = launch_knn_query(c, X, n, P, K, d, 1, cell, cdist, st);

@@ -680,73 +680,82 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 }
 
 // ------------------------------------------------------------------ A3: re-rank + certify
-template <int K, bool F16>
-__global__ void tc_rerank_kernel(const float* __restrict__ X, int64_t n, int d, int k,
-                                 const int32_t* __restrict__ cand_idx, const float* __restrict__ cand_s,
-                                 const float* __restrict__ norm, const float* __restrict__ resid,
-                                 const unsigned int* __restrict__ maxbits, const float* __restrict__ lbstop,
-                                 int32_t* __restrict__ idx_out,
-                                 float* __restrict__ dist_out, int32_t* __restrict__ fail_rows,
-                                 int32_t* __restrict__ fail_count) {
+// One warp per row: lane l takes candidate l.  The 32 candidate rows are
+// staged in shared memory (coalesced), each lane sums its candidate's squared
+// distance over the dimensions in order (the FP32 scan's arithmetic, so every
+// mode returns the same bits), and a bitonic network over the lanes orders the
+// candidates by (distance, index).
+static constexpr int RR_WARPS = 4;
+static constexpr int RR_PITCH = 65;  // floats per staged row (d <= 64), odd: conflict-free
+
+template <bool F16>
+__global__ void __launch_bounds__(RR_WARPS * 32)
+tc_rerank_kernel(const float* __restrict__ X, int64_t n, int d, int k, const int32_t* __restrict__ cand_idx,
+                 const float* __restrict__ cand_s, const float* __restrict__ norm, const float* __restrict__ resid,
+                 const unsigned int* __restrict__ maxbits, const float* __restrict__ lbstop,
+                 int32_t* __restrict__ idx_out, float* __restrict__ dist_out, int32_t* __restrict__ fail_rows,
+                 int32_t* __restrict__ fail_count) {
+    __shared__ float s_rows[RR_WARPS][32 * RR_PITCH];
+    __shared__ float s_q[RR_WARPS][64];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float n_max = __uint_as_float(maxbits[0]);
     const float r_max = __uint_as_float(maxbits[1]);
     const float S = operand_scale<F16>(maxbits);
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        float D[K];
-        int32_t J[K];
-#pragma unroll
-        for (int s = 0; s < K; ++s) {
-            D[s] = INFINITY;
-            J[s] = INT32_MAX;
+    const int64_t warps = int64_t(gridDim.x) * RR_WARPS;
+    for (int64_t i = int64_t(blockIdx.x) * RR_WARPS + w; i < n; i += warps) {
+        const int32_t j = cand_idx[i * TC_KP + lane];
+        const bool valid = j >= 0 && j < n && j != i;
+        // stage the query row and the 32 candidate rows
+        for (int c = lane; c < d; c += 32) s_q[w][c] = X[i * d + c];
+        for (int t = 0; t < 32; ++t) {
+            const int32_t jt = __shfl_sync(0xffffffffu, j, t);
+            const bool vt = __shfl_sync(0xffffffffu, valid ? 1 : 0, t) != 0;
+            for (int c = lane; c < d; c += 32) s_rows[w][t * RR_PITCH + c] = vt ? X[int64_t(jt) * d + c] : 0.f;
         }
-        int valid = 0;
-        for (int s = 0; s < TC_KP; ++s) {
-            const int32_t j = cand_idx[i * TC_KP + s];
-            if (j < 0 || j >= n || j == i) continue;
-            ++valid;
-            float a = 0.f;
+        __syncwarp();
+        float a = INFINITY;
+        int32_t jj = INT32_MAX;
+        if (valid) {
+            a = 0.f;
             for (int c = 0; c < d; ++c) {
-                const float df = X[i * d + c] - X[int64_t(j) * d + c];
+                const float df = s_q[w][c] - s_rows[w][lane * RR_PITCH + c];
                 a = fmaf(df, df, a);
             }
-            if (a < D[K - 1] || (a == D[K - 1] && j < J[K - 1])) {
+            jj = j;
+        }
+        // bitonic sort across the lanes, ascending by (a, index)
 #pragma unroll
-                for (int t = K - 1; t > 0; --t) {
-                    const bool shift = a < D[t - 1] || (a == D[t - 1] && j < J[t - 1]);
-                    const bool place = !shift && (a < D[t] || (a == D[t] && j < J[t]));
-                    D[t] = shift ? D[t - 1] : (place ? a : D[t]);
-                    J[t] = shift ? J[t - 1] : (place ? j : J[t]);
-                }
-                if (a < D[0] || (a == D[0] && j < J[0])) {
-                    D[0] = a;
-                    J[0] = j;
+        for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+            for (int st = kk >> 1; st > 0; st >>= 1) {
+                const float oa = __shfl_xor_sync(0xffffffffu, a, st);
+                const int32_t oj = __shfl_xor_sync(0xffffffffu, jj, st);
+                const bool up = (lane & kk) == 0, lower = (lane & st) == 0;
+                const bool self_less = a < oa || (a == oa && jj < oj);
+                if (self_less != (lower == up)) {
+                    a = oa;
+                    jj = oj;
                 }
             }
         }
-        // certificate
-        const float s_thr = cand_s[i * TC_KP + TC_KP - 1] * (S * S);
-        const float ni = norm[i];
-        const float eps = 6.103515625e-05f * (ni + n_max);  // 2^-14 (n_i + n_max)
-        const float lb2 = ni + s_thr - eps;
-        // points never compared lie in skipped cells, beyond lbstop
-        const float lb = fminf(sqrtf(fmaxf(lb2, 0.f)) - resid[i] - r_max, lbstop[i]);
-        float dk2 = 0.f;
-#pragma unroll
-        for (int s = 0; s < K; ++s)
-            if (s == k - 1) dk2 = D[s];
-        const float dk = sqrtf(dk2);
-        const bool ok = valid >= k && lb > dk * (1.0f + 3.8e-6f);
-        if (!ok) {
-            const int32_t pos = atomicAdd(fail_count, 1);
-            fail_rows[pos] = int32_t(i);
+        const int n_valid = __popc(__ballot_sync(0xffffffffu, valid));
+        const float dk2 = __shfl_sync(0xffffffffu, a, k - 1);
+        if (lane < k) {
+            idx_out[i * k + lane] = jj;
+            dist_out[i * k + lane] = sqrtf(a);
         }
-#pragma unroll
-        for (int s = 0; s < K; ++s) {
-            if (s < k) {
-                idx_out[i * k + s] = J[s];
-                dist_out[i * k + s] = sqrtf(D[s]);
-            }
+        if (lane == 0) {
+            // certificate: every point outside the list is beyond lb (points
+            // never compared lie in skipped cells, beyond lbstop)
+            const float s_thr = cand_s[i * TC_KP + TC_KP - 1] * (S * S);
+            const float ni = norm[i];
+            const float eps = 6.103515625e-05f * (ni + n_max);  // 2^-14 (n_i + n_max)
+            const float lb2 = ni + s_thr - eps;
+            const float lb = fminf(sqrtf(fmaxf(lb2, 0.f)) - resid[i] - r_max, lbstop[i]);
+            const bool ok = n_valid >= k && lb > sqrtf(dk2) * (1.0f + 3.8e-6f);
+            if (!ok) fail_rows[atomicAdd(fail_count, 1)] = int32_t(i);
         }
+        __syncwarp();
     }
 }
 
@@ -872,13 +881,8 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
     DRGB_CHECK_LAUNCH(c);
     if ((rc = stage_mark(c, 7, st))) return rc;
 
-    const int rb = grid_for(n, 128, c->num_sms * 8);
-    if (k <= 16)
-        tc_rerank_kernel<16, F16><<<rb, 128, 0, st>>>(X, n, d, k, cand_idx, cand_s, norm, resid, maxbits, lbstop,
-                                                 idx_out, dist_out, fail_rows, fail_count);
-    else
-        tc_rerank_kernel<32, F16><<<rb, 128, 0, st>>>(X, n, d, k, cand_idx, cand_s, norm, resid, maxbits, lbstop,
-                                                 idx_out, dist_out, fail_rows, fail_count);
+    tc_rerank_kernel<F16><<<grid_for(n, RR_WARPS, c->num_sms * 8), RR_WARPS * 32, 0, st>>>(
+        X, n, d, k, cand_idx, cand_s, norm, resid, maxbits, lbstop, idx_out, dist_out, fail_rows, fail_count);
     DRGB_CHECK_LAUNCH(c);
     // exact FP32 scan of the uncertified rows (row list and count on the device)
     DRGB_CUDA(c, cudaMemcpyAsync(c->d_counter, fail_count, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
