@@ -163,12 +163,14 @@ __global__ void tc_mean_kernel(const float* __restrict__ partial, int nblk, int 
 // Warp per row: lanes own dimensions (lane, lane + 32).  Norms and residuals
 // are stored in the original units (the scale S is a power of two).
 // Position i of the operands holds point perm[i] (positions >= n: padding);
-// norms and residuals are stored at the point's own index.
+// norms and residuals are stored at the point's own index, and Xp (FP32, n x d)
+// receives the rows in position order.
 template <bool F16>
 __global__ void tc_stage_kernel(const float* __restrict__ X, int64_t n, int64_t n_pad, int d,
                                 const float* __restrict__ mean, const int32_t* __restrict__ perm,
                                 op16* __restrict__ XA, op16* __restrict__ XB, float* __restrict__ norm,
-                                float* __restrict__ resid, unsigned int* __restrict__ maxbits) {
+                                float* __restrict__ resid, unsigned int* __restrict__ maxbits,
+                                float* __restrict__ Xp) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
     const float S = operand_scale<F16>(maxbits), inv_S = 1.0f / S;
@@ -182,7 +184,11 @@ __global__ void tc_stage_kernel(const float* __restrict__ X, int64_t n, int64_t 
         for (int h = 0; h < 2; ++h) {
             const int c = lane + 32 * h;
             float v = 0.f;
-            if (i < n && c < d) v = (X[src * d + c] - mean[c]) * inv_S;
+            if (i < n && c < d) {
+                const float x = X[src * d + c];
+                Xp[i * d + c] = x;
+                v = (x - mean[c]) * inv_S;
+            }
             xc[h] = v;
             xb[h] = from_op<F16>(to_op<F16>(v));
             sq = fmaf(xb[h], xb[h], sq);
@@ -237,7 +243,7 @@ __global__ void tc_stage_kernel(const float* __restrict__ X, int64_t n, int64_t 
 struct TcParams {
     int64_t n;
     int n_tiles;
-    int32_t* cand_idx;   // n x TC_KP (point indices, row of the original point)
+    int32_t* cand_idx;   // n x TC_KP candidate positions, by query position
     float* cand_s;       // n x TC_KP
     int* status;
     // spatial schedule: positions p (rows of the staged operands) hold point
@@ -253,7 +259,7 @@ struct TcParams {
     const float* norm;          // per point, original units (see the staging)
     const float* resid;
     const unsigned int* maxbits;
-    float* lbstop;       // per point: no point of a skipped cell is nearer (original units)
+    float* lbstop;       // per position: no point of a skipped cell is nearer (original units)
     unsigned long long* tiles_done;  // += tiles this CTA multiplied
 };
 
@@ -524,17 +530,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             L[s] = INFINITY;
             I[s] = -1;
         }
-        // this row's conversion of a threshold on s into an upper bound on the
-        // distance (original units) of its 32nd candidate
-        const float S = operand_scale<F16>(P.maxbits);
-        const float r_max = __uint_as_float(P.maxbits[1]), n_max = __uint_as_float(P.maxbits[0]);
-        float ni = 0.f, di = 0.f;
-        if (row < nrow) {
-            const int64_t g = P.perm[q0 + row];
-            ni = P.norm[g];
-            di = P.resid[g];
-        }
-        const float eps_i = 6.103515625e-05f * (ni + n_max);
+        // this row's point (its norm and residual convert a threshold on s
+        // into an upper bound on the distance of its 32nd candidate)
+        const int64_t g_row = row < nrow ? int64_t(P.perm[q0 + row]) : -1;
         // Candidates below the row's threshold are appended to this thread's
         // queue (slot s at q[s * 256 + tid], conflict-free).  The threshold
         // is the smaller of the two column halves' 32nd-best values: a value at
@@ -573,8 +571,13 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             qn = 0;
             *thr_mine = L[TC_KP - 1];
             const float thr = fminf(L[TC_KP - 1], *thr_other);
-            if (row < nrow && thr < INFINITY)
-                s_U[row] = (sqrtf(fmaxf(ni + thr * (S * S) + eps_i, 0.f)) + di + r_max) * (1.0f + 1e-5f);
+            if (g_row >= 0 && thr < INFINITY) {
+                const float S = operand_scale<F16>(P.maxbits);
+                const float r_max = __uint_as_float(P.maxbits[1]), n_max = __uint_as_float(P.maxbits[0]);
+                const float ni = P.norm[g_row];
+                const float eps_i = 6.103515625e-05f * (ni + n_max);
+                s_U[row] = (sqrtf(fmaxf(ni + thr * (S * S) + eps_i, 0.f)) + P.resid[g_row] + r_max) * (1.0f + 1e-5f);
+            }
         };
         for (int t = 0;; ++t) {
             const int buf = t & 1, use = t >> 1;
@@ -654,7 +657,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         }
         asm volatile("bar.sync 1, %0;" ::"r"(TC_EPI_WARPS * 32) : "memory");
         if (half == 0 && row < nrow && !*abort_flag) {
-            const int64_t g = P.perm[q0 + row];
+            const int64_t g = q0 + row;
             const float* As = ms + row * TC_KP;
             const int32_t* Ai = mi + row * TC_KP;
             const float* Bs = ms + (TC_BM + row) * TC_KP;
@@ -664,7 +667,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 const bool take_a = (As[a] < Bs[b]) || (As[a] == Bs[b] && uint32_t(Ai[a]) <= uint32_t(Bi[b]));
                 const int32_t pos = take_a ? Ai[a] : Bi[b];
                 P.cand_s[g * TC_KP + o] = take_a ? As[a] : Bs[b];
-                P.cand_idx[g * TC_KP + o] = pos >= 0 ? P.perm[pos] : -1;
+                P.cand_idx[g * TC_KP + o] = pos;
                 if (take_a) ++a; else ++b;
             }
             P.lbstop[g] = s_misc[1];
@@ -690,8 +693,9 @@ static constexpr int RR_PITCH = 65;  // floats per staged row (d <= 64), odd: co
 
 template <bool F16>
 __global__ void __launch_bounds__(RR_WARPS * 32)
-tc_rerank_kernel(const float* __restrict__ X, int64_t n, int d, int k, const int32_t* __restrict__ cand_idx,
-                 const float* __restrict__ cand_s, const float* __restrict__ norm, const float* __restrict__ resid,
+tc_rerank_kernel(const float* __restrict__ Xp, const int32_t* __restrict__ perm, int64_t n, int d, int k,
+                 const int32_t* __restrict__ cand_pos, const float* __restrict__ cand_s,
+                 const float* __restrict__ norm, const float* __restrict__ resid,
                  const unsigned int* __restrict__ maxbits, const float* __restrict__ lbstop,
                  int32_t* __restrict__ idx_out, float* __restrict__ dist_out, int32_t* __restrict__ fail_rows,
                  int32_t* __restrict__ fail_count) {
@@ -702,15 +706,17 @@ tc_rerank_kernel(const float* __restrict__ X, int64_t n, int d, int k, const int
     const float r_max = __uint_as_float(maxbits[1]);
     const float S = operand_scale<F16>(maxbits);
     const int64_t warps = int64_t(gridDim.x) * RR_WARPS;
-    for (int64_t i = int64_t(blockIdx.x) * RR_WARPS + w; i < n; i += warps) {
-        const int32_t j = cand_idx[i * TC_KP + lane];
-        const bool valid = j >= 0 && j < n && j != i;
+    // rows in position order: neighbouring warps share candidates in L2
+    for (int64_t p = int64_t(blockIdx.x) * RR_WARPS + w; p < n; p += warps) {
+        const int64_t i = perm[p];
+        const int32_t q = cand_pos[p * TC_KP + lane];
+        const bool valid = q >= 0 && q < n && q != p;
         // stage the query row and the 32 candidate rows
-        for (int c = lane; c < d; c += 32) s_q[w][c] = X[i * d + c];
+        for (int c = lane; c < d; c += 32) s_q[w][c] = Xp[p * d + c];
+#pragma unroll 8
         for (int t = 0; t < 32; ++t) {
-            const int32_t jt = __shfl_sync(0xffffffffu, j, t);
-            const bool vt = __shfl_sync(0xffffffffu, valid ? 1 : 0, t) != 0;
-            for (int c = lane; c < d; c += 32) s_rows[w][t * RR_PITCH + c] = vt ? X[int64_t(jt) * d + c] : 0.f;
+            const int32_t qt = __shfl_sync(0xffffffffu, valid ? q : -1, t);
+            for (int c = lane; c < d; c += 32) s_rows[w][t * RR_PITCH + c] = qt >= 0 ? Xp[int64_t(qt) * d + c] : 0.f;
         }
         __syncwarp();
         float a = INFINITY;
@@ -721,9 +727,9 @@ tc_rerank_kernel(const float* __restrict__ X, int64_t n, int d, int k, const int
                 const float df = s_q[w][c] - s_rows[w][lane * RR_PITCH + c];
                 a = fmaf(df, df, a);
             }
-            jj = j;
+            jj = perm[q];
         }
-        // bitonic sort across the lanes, ascending by (a, index)
+        // bitonic sort across the lanes, ascending by (a, point index)
 #pragma unroll
         for (int kk = 2; kk <= 32; kk <<= 1) {
 #pragma unroll
@@ -747,11 +753,11 @@ tc_rerank_kernel(const float* __restrict__ X, int64_t n, int d, int k, const int
         if (lane == 0) {
             // certificate: every point outside the list is beyond lb (points
             // never compared lie in skipped cells, beyond lbstop)
-            const float s_thr = cand_s[i * TC_KP + TC_KP - 1] * (S * S);
+            const float s_thr = cand_s[p * TC_KP + TC_KP - 1] * (S * S);
             const float ni = norm[i];
             const float eps = 6.103515625e-05f * (ni + n_max);  // 2^-14 (n_i + n_max)
             const float lb2 = ni + s_thr - eps;
-            const float lb = fminf(sqrtf(fmaxf(lb2, 0.f)) - resid[i] - r_max, lbstop[i]);
+            const float lb = fminf(sqrtf(fmaxf(lb2, 0.f)) - resid[i] - r_max, lbstop[p]);
             const bool ok = n_valid >= k && lb > sqrtf(dk2) * (1.0f + 3.8e-6f);
             if (!ok) fail_rows[atomicAdd(fail_count, 1)] = int32_t(i);
         }
@@ -786,7 +792,8 @@ static size_t tc_scratch_bytes(int64_t n, int d, int64_t n_pad, int nblk) {
            2 * Carve::round(n_pad * 4) + Carve::round(64) + 2 * Carve::round(n_pad * TC_KP * 4) +
            Carve::round(n * 4) + Carve::round(64) + TC_PART_BYTES + Carve::round(n_pad * 4) +
            Carve::round((TC_CELLS + 1) * 4) + Carve::round(size_t(TC_CELLS) * d * 4) + Carve::round(TC_CELLS * 4) +
-           Carve::round(n * 4) + (K > 1 ? knn_order_scratch_bytes(n, d, K) : 0) + 16384;
+           Carve::round(n * 4) + Carve::round(size_t(n) * d * 4) + (K > 1 ? knn_order_scratch_bytes(n, d, K) : 0) +
+           16384;
 }
 
 static constexpr int TC_COLSUM_BLOCKS = 256;
@@ -823,6 +830,7 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
     float* cell_c = cv.take<float>(size_t(TC_CELLS) * d);
     float* cell_r = cv.take<float>(TC_CELLS);
     float* lbstop = cv.take<float>(n);
+    float* Xp = cv.take<float>(size_t(n) * d);
     const int K = tc_cells(n_pad, n);
     void* order_scratch = K > 1 ? cv.take<char>(knn_order_scratch_bytes(n, d, K)) : nullptr;
 
@@ -843,7 +851,7 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
     DRGB_CHECK_LAUNCH(c);
     if (K > 1 && (rc = knn_order(c, X, n, d, K, perm, cell_beg, cell_c, cell_r, order_scratch, st))) return rc;
     tc_stage_kernel<F16><<<grid_for(n_pad, 8, c->num_sms * 16), 256, 0, st>>>(X, n, n_pad, d, mean, perm, XA,
-                                                                              XB, norm, resid, maxbits);
+                                                                              XB, norm, resid, maxbits, Xp);
     DRGB_CHECK_LAUNCH(c);
 
     CUtensorMap mA, mB;
@@ -882,7 +890,8 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
     if ((rc = stage_mark(c, 7, st))) return rc;
 
     tc_rerank_kernel<F16><<<grid_for(n, RR_WARPS, c->num_sms * 8), RR_WARPS * 32, 0, st>>>(
-        X, n, d, k, cand_idx, cand_s, norm, resid, maxbits, lbstop, idx_out, dist_out, fail_rows, fail_count);
+        Xp, perm, n, d, k, cand_idx, cand_s, norm, resid, maxbits, lbstop, idx_out, dist_out, fail_rows,
+        fail_count);
     DRGB_CHECK_LAUNCH(c);
     // exact FP32 scan of the uncertified rows (row list and count on the device)
     DRGB_CUDA(c, cudaMemcpyAsync(c->d_counter, fail_count, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
