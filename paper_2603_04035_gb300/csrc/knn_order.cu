@@ -1,7 +1,8 @@
 // Spatial ordering of the points for the tensor-core k-NN: K pivots chosen by
-// farthest-point sampling on a strided subsample (one CTA), every point assigned to its
+// farthest-point sampling on a hashed subsample (one CTA), every point assigned to its
 // nearest pivot (exact FP32 scan), a stable counting sort by pivot ("cell"),
-// and a bounding sphere per cell.  The order only decides which database
+// and a bounding sphere per cell (the pivot and the largest distance of the
+// cell's points to it).  The order only decides which database
 // tiles a query block visits first and which it may skip; the k-NN result
 // does not depend on it (skipped cells enter the certificate as a distance
 // bound, and rows the bound cannot certify are scanned exactly).
@@ -13,13 +14,12 @@
 namespace drgb {
 
 static constexpr int ORD_SUB = 1536;      // subsample size for the pivot choice (one CTA)
-static constexpr int ORD_THREADS = 1024;
+static constexpr int ORD_THREADS = 256;
 static constexpr int ORD_CHUNK = 4096;    // points per counting-sort chunk (one warp each)
 
 // Subsample point i of m: splitmix64(i) mod n, a fixed pseudo-random sample
 // (a strided sample aliases with periodic point orders such as labels i mod c).
-__device__ __forceinline__ int64_t sub_point(int i, int64_t n, int m) {
-    (void)m;
+__device__ __forceinline__ int64_t sub_point(int i, int64_t n) {
     uint64_t z = uint64_t(i) + 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
@@ -40,13 +40,13 @@ __global__ void __launch_bounds__(ORD_THREADS) fps_cta_kernel(const float* __res
     __half* s_x = reinterpret_cast<__half*>(s_best + 32);          // [m][d]
     for (int t = threadIdx.x; t < m * d; t += blockDim.x) {
         const int i = t / d, c = t % d;
-        s_x[t] = __float2half_rn(X[sub_point(i, n, m) * d + c]);
+        s_x[t] = __float2half_rn(X[sub_point(i, n) * d + c]);
     }
     for (int i = threadIdx.x; i < m; i += blockDim.x) s_min[i] = INFINITY;
     __syncthreads();
     int p = 0;
     for (int it = 0; it < K; ++it) {
-        if (threadIdx.x == 0) pivots[it] = int32_t(sub_point(p, n, m));
+        if (threadIdx.x == 0) pivots[it] = int32_t(sub_point(p, n));
         if (it == K - 1) break;
         unsigned long long best = 0;
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -88,16 +88,27 @@ __global__ void gather_rows_kernel(const float* __restrict__ X, int d, const int
         out[t] = X[int64_t(rows[t / d]) * d + t % d];
 }
 
-// Per chunk of ORD_CHUNK points: how many fall in each cell.
-__global__ void cell_count_kernel(const int32_t* __restrict__ cell, int64_t n, int K, int nchunk,
-                                  int32_t* __restrict__ counts) {
-    extern __shared__ int32_t s_cnt[];
-    for (int c = threadIdx.x; c < K; c += blockDim.x) s_cnt[c] = 0;
+// Per chunk of ORD_CHUNK points: how many fall in each cell, and (radius
+// bits, atomicMax) the largest distance of a point to its cell's pivot.
+__global__ void cell_count_kernel(const int32_t* __restrict__ cell, const float* __restrict__ cdist, int64_t n,
+                                  int K, int nchunk, int32_t* __restrict__ counts, unsigned int* __restrict__ rbits) {
+    extern __shared__ int32_t s_cnt[];  // [K] counts, [K] radius bits
+    unsigned int* s_r = reinterpret_cast<unsigned int*>(s_cnt + K);
+    for (int c = threadIdx.x; c < K; c += blockDim.x) {
+        s_cnt[c] = 0;
+        s_r[c] = 0u;
+    }
     __syncthreads();
     const int64_t b0 = int64_t(blockIdx.x) * ORD_CHUNK;
-    for (int64_t i = b0 + threadIdx.x; i < b0 + ORD_CHUNK && i < n; i += blockDim.x) atomicAdd(&s_cnt[cell[i]], 1);
+    for (int64_t i = b0 + threadIdx.x; i < b0 + ORD_CHUNK && i < n; i += blockDim.x) {
+        atomicAdd(&s_cnt[cell[i]], 1);
+        atomicMax(&s_r[cell[i]], __float_as_uint(cdist[i]));
+    }
     __syncthreads();
-    for (int c = threadIdx.x; c < K; c += blockDim.x) counts[int64_t(c) * nchunk + blockIdx.x] = s_cnt[c];
+    for (int c = threadIdx.x; c < K; c += blockDim.x) {
+        counts[int64_t(c) * nchunk + blockIdx.x] = s_cnt[c];
+        if (s_r[c]) atomicMax(&rbits[c], s_r[c]);
+    }
 }
 
 // Stable scatter: one warp walks its chunk in index order, 32 points a round;
@@ -136,53 +147,8 @@ __global__ void cell_begin_kernel(const int32_t* __restrict__ offs, int K, int n
         cell_beg[c] = c < K ? offs[int64_t(c) * nchunk] : int32_t(n);
 }
 
-// One CTA per cell: centre (mean of its points) and radius (largest distance
-// from that centre, computed in FP32; callers widen it by a margin).
-__global__ void cell_sphere_kernel(const float* __restrict__ X, int d, const int32_t* __restrict__ perm,
-                                   const int32_t* __restrict__ cell_beg, float* __restrict__ centre,
-                                   float* __restrict__ radius) {
-    __shared__ float s_part[8][64];
-    __shared__ float s_c[64];
-    __shared__ float s_r;
-    const int c = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int32_t b = cell_beg[c], e = cell_beg[c + 1];
-    // lanes own dimensions (lane, lane + 32); warps split the points
-    float a0 = 0.f, a1 = 0.f;
-    for (int32_t p = b + w; p < e; p += 8) {
-        const int64_t i = perm[p];
-        if (lane < d) a0 += X[i * d + lane];
-        if (lane + 32 < d) a1 += X[i * d + lane + 32];
-    }
-    s_part[w][lane] = a0;
-    s_part[w][lane + 32] = a1;
-    if (threadIdx.x == 0) s_r = 0.f;
-    __syncthreads();
-    if (threadIdx.x < 64) {
-        float s = 0.f;
-        for (int q = 0; q < 8; ++q) s += s_part[q][threadIdx.x];
-        s_c[threadIdx.x] = e > b ? s / float(e - b) : 0.f;
-    }
-    __syncthreads();
-    float rmax = 0.f;
-    for (int32_t p = b + threadIdx.x; p < e; p += blockDim.x) {
-        const int64_t i = perm[p];
-        float s = 0.f;
-        for (int q = 0; q < d; ++q) {
-            const float df = X[i * d + q] - s_c[q];
-            s = fmaf(df, df, s);
-        }
-        rmax = fmaxf(rmax, sqrtf(s));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-    if (lane == 0) atomicMax(reinterpret_cast<unsigned int*>(&s_r), __float_as_uint(rmax));
-    __syncthreads();
-    for (int q = threadIdx.x; q < d; q += blockDim.x) centre[int64_t(c) * d + q] = s_c[q];
-    if (threadIdx.x == 0) radius[c] = e > b ? s_r : 0.f;
-}
-
 int knn_order_cells(int64_t n) {
-    int64_t K = n / 1024;
+    int64_t K = n / 2048;
     if (K < 16) K = 16;
     if (K > 128) K = 128;
     return int(K);
@@ -191,8 +157,7 @@ int knn_order_cells(int64_t n) {
 size_t knn_order_scratch_bytes(int64_t n, int d, int K) {
     const int64_t nchunk = (n + ORD_CHUNK - 1) / ORD_CHUNK;
     const size_t kc = size_t(K) * nchunk;
-    return Carve::round(size_t(K) * 4) +
-           Carve::round(size_t(K) * d * 4) + Carve::round(size_t(n) * 4) * 2 + 2 * Carve::round(kc * 4) +
+    return Carve::round(size_t(K) * 4) + Carve::round(size_t(n) * 4) * 2 + 2 * Carve::round(kc * 4) +
            Carve::round(scan_scratch_elems(int64_t(kc)) * 4) + 4096;
 }
 
@@ -204,7 +169,6 @@ int knn_order(Ctx* c, const float* X, int64_t n, int d, int K, int32_t* perm, in
     const size_t kc = size_t(K) * nchunk;
     Carve cv(scratch);
     int32_t* pivots = cv.take<int32_t>(K);
-    float* P = cv.take<float>(size_t(K) * d);
     int32_t* cell = cv.take<int32_t>(n);
     float* cdist = cv.take<float>(n);
     int32_t* counts = cv.take<int32_t>(kc);
@@ -215,11 +179,15 @@ int knn_order(Ctx* c, const float* X, int64_t n, int d, int K, int32_t* perm, in
     DRGB_CUDA(c, cudaFuncSetAttribute(fps_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fsm)));
     fps_cta_kernel<<<1, ORD_THREADS, fsm, st>>>(X, n, d, m, K, pivots);
     DRGB_CHECK_LAUNCH(c);
-    gather_rows_kernel<<<grid_for(int64_t(K) * d, 256, c->num_sms), 256, 0, st>>>(X, d, pivots, K, P);
+    // the pivots are the cells' centres; a cell's radius is the largest
+    // distance from its points to its pivot (the assignment's own distances)
+    gather_rows_kernel<<<grid_for(int64_t(K) * d, 256, c->num_sms), 256, 0, st>>>(X, d, pivots, K, centre);
     DRGB_CHECK_LAUNCH(c);
-    int rc = launch_knn_query(c, X, n, P, K, d, 1, cell, cdist, st);
+    int rc = launch_knn_query(c, X, n, centre, K, d, 1, cell, cdist, st);
     if (rc) return rc;
-    cell_count_kernel<<<nchunk, 256, size_t(K) * 4, st>>>(cell, n, K, nchunk, counts);
+    DRGB_CUDA(c, cudaMemsetAsync(radius, 0, size_t(K) * 4, st));
+    cell_count_kernel<<<nchunk, 256, size_t(K) * 8, st>>>(cell, cdist, n, K, nchunk, counts,
+                                                         reinterpret_cast<unsigned int*>(radius));
     DRGB_CHECK_LAUNCH(c);
     if ((rc = exclusive_scan(c, counts, offs, int64_t(kc), tmp, st))) return rc;
     const int sw = 4;  // warps (chunks) per CTA of the scatter
@@ -227,8 +195,6 @@ int knn_order(Ctx* c, const float* X, int64_t n, int d, int K, int32_t* perm, in
                                                                                     perm);
     DRGB_CHECK_LAUNCH(c);
     cell_begin_kernel<<<1, 256, 0, st>>>(offs, K, nchunk, n, cell_beg);
-    DRGB_CHECK_LAUNCH(c);
-    cell_sphere_kernel<<<K, 256, 0, st>>>(X, d, perm, cell_beg, centre, radius);
     DRGB_CHECK_LAUNCH(c);
     return DRGB_OK;
 }

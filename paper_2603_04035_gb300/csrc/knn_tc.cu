@@ -713,10 +713,22 @@ tc_rerank_kernel(const float* __restrict__ Xp, const int32_t* __restrict__ perm,
         const bool valid = q >= 0 && q < n && q != p;
         // stage the query row and the 32 candidate rows
         for (int c = lane; c < d; c += 32) s_q[w][c] = Xp[p * d + c];
-#pragma unroll 8
-        for (int t = 0; t < 32; ++t) {
-            const int32_t qt = __shfl_sync(0xffffffffu, valid ? q : -1, t);
-            for (int c = lane; c < d; c += 32) s_rows[w][t * RR_PITCH + c] = qt >= 0 ? Xp[int64_t(qt) * d + c] : 0.f;
+        {
+            // every lane loads dimensions (lane, lane + 32) of all 32 rows
+            // before storing any, so the 64 loads are in flight together
+            float v0[32], v1[32];
+            const int qv = valid ? q : -1;
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                const int32_t qt = __shfl_sync(0xffffffffu, qv, t);
+                v0[t] = (qt >= 0 && lane < d) ? Xp[int64_t(qt) * d + lane] : 0.f;
+                v1[t] = (qt >= 0 && lane + 32 < d) ? Xp[int64_t(qt) * d + lane + 32] : 0.f;
+            }
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                s_rows[w][t * RR_PITCH + lane] = v0[t];
+                s_rows[w][t * RR_PITCH + lane + 32] = v1[t];
+            }
         }
         __syncwarp();
         float a = INFINITY;
