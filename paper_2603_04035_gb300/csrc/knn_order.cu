@@ -13,9 +13,12 @@
 
 namespace drgb {
 
-static constexpr int ORD_SUB = 1536;      // subsample size for the pivot choice (one CTA)
-static constexpr int ORD_THREADS = 256;
-static constexpr int ORD_CHUNK = 4096;    // points per counting-sort chunk (one warp each)
+static constexpr int ORD_SUB = 1536;      // largest subsample for the pivot choice (one CTA; 203 KB at d = 64)
+static constexpr int ORD_PER_PIVOT = 16;  // subsample points per pivot
+static constexpr int ORD_THREADS = 1024;
+static constexpr int ORD_PPT = (ORD_SUB + ORD_THREADS - 1) / ORD_THREADS;  // subsample points per thread
+static constexpr int ORD_CHUNK = 512;     // points per counting-sort chunk (one warp each)
+static constexpr int ORD_DMAX = 64;       // widest row the order supports
 
 // Subsample point i of m: splitmix64(i) mod n, a fixed pseudo-random sample
 // (a strided sample aliases with periodic point orders such as labels i mod c).
@@ -27,59 +30,125 @@ __device__ __forceinline__ int64_t sub_point(int i, int64_t n) {
     return int64_t(z % uint64_t(n));
 }
 
-// Farthest-point sampling in one CTA: the subsample is held in shared memory
-// as FP16 (the pivot choice is a heuristic; any deterministic choice is
-// valid).  Pivot 0 is the first subsample point;
-// pivot it + 1 is the subsample point farthest from pivots 0..it (ties: the
-// lowest subsample index).
-__global__ void __launch_bounds__(ORD_THREADS) fps_cta_kernel(const float* __restrict__ X, int64_t n, int d, int m,
-                                                           int K, int32_t* __restrict__ pivots) {
-    extern __shared__ __align__(16) uint8_t s_raw[];
-    float* s_min = reinterpret_cast<float*>(s_raw);                 // [m]
-    unsigned long long* s_best = reinterpret_cast<unsigned long long*>(s_min + ORD_SUB);  // [32]
-    __half* s_x = reinterpret_cast<__half*>(s_best + 32);          // [m][d]
-    for (int t = threadIdx.x; t < m * d; t += blockDim.x) {
-        const int i = t / d, c = t % d;
-        s_x[t] = __float2half_rn(X[sub_point(i, n) * d + c]);
+// Row pitch of the FP16 subsample in half2 words: odd, so that the rows the
+// lanes of a warp read at one offset fall in distinct shared-memory banks.
+static inline int sub_pitch(int d) { return ((d + 1) / 2) | 1; }
+
+// S[i][c] = dimensions (2c, 2c + 1) of subsample point i as FP16 (zero past d).
+__global__ void sub_gather_kernel(const float* __restrict__ X, int64_t n, int d, int m, int pitch,
+                                  __half2* __restrict__ S) {
+    const int64_t total = int64_t(m) * pitch;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+        const int i = int(t / pitch), c = int(t % pitch) * 2;
+        const int64_t r = sub_point(i, n) * d;
+        S[t] = __floats2half2_rn(c < d ? X[r + c] : 0.f, c + 1 < d ? X[r + c + 1] : 0.f);
     }
-    for (int i = threadIdx.x; i < m; i += blockDim.x) s_min[i] = INFINITY;
+}
+
+// Farthest-point sampling in one CTA over the FP16 subsample S (the pivot
+// choice is a heuristic; any deterministic choice is valid).  Pivot 0 is the
+// first subsample point; pivot it + 1 is the subsample point farthest from
+// pivots 0..it (ties: the lowest subsample index).  Each thread keeps the
+// running minimum distances of its ORD_PPT points in registers; one barrier
+// per step (the per-warp maxima are double-buffered by step parity).
+__global__ void __launch_bounds__(ORD_THREADS) fps_cta_kernel(const __half2* __restrict__ S, int64_t n, int m,
+                                                           int pitch, int K, int32_t* __restrict__ pivots) {
+    extern __shared__ __align__(16) uint8_t s_raw[];
+    unsigned long long* s_best = reinterpret_cast<unsigned long long*>(s_raw);  // [2][32]
+    __half2* s_x = reinterpret_cast<__half2*>(s_best + 64);                    // [m][pitch]
+    const int words = m * pitch;
+#pragma unroll 4
+    for (int t = threadIdx.x; t < words; t += ORD_THREADS) s_x[t] = S[t];
+    float mn[ORD_PPT];
+#pragma unroll
+    for (int j = 0; j < ORD_PPT; ++j) mn[j] = INFINITY;
     __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int p = 0;
     for (int it = 0; it < K; ++it) {
         if (threadIdx.x == 0) pivots[it] = int32_t(sub_point(p, n));
         if (it == K - 1) break;
+        const __half2* pv = s_x + p * pitch;
         unsigned long long best = 0;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            float sq = 0.f;
-            for (int c = 0; c < d; ++c) {
-                const float df = __half2float(s_x[i * d + c]) - __half2float(s_x[p * d + c]);
-                sq = fmaf(df, df, sq);
+#pragma unroll
+        for (int j = 0; j < ORD_PPT; ++j) {
+            const int i = threadIdx.x + j * ORD_THREADS;
+            if (i < m) {
+                const __half2* xv = s_x + i * pitch;
+                float sq = 0.f;
+#pragma unroll 4
+                for (int c = 0; c < pitch; ++c) {
+                    const float2 a = __half22float2(xv[c]), b = __half22float2(pv[c]);
+                    float df = a.x - b.x;
+                    sq = fmaf(df, df, sq);
+                    df = a.y - b.y;
+                    sq = fmaf(df, df, sq);
+                }
+                mn[j] = fminf(mn[j], sq);
+                const unsigned long long key = (uint64_t(__float_as_uint(mn[j])) << 32) | uint64_t(~uint32_t(i));
+                best = key > best ? key : best;
             }
-            const float v = fminf(s_min[i], sq);
-            s_min[i] = v;
-            const unsigned long long key = (uint64_t(__float_as_uint(v)) << 32) | uint64_t(~uint32_t(i));
-            best = key > best ? key : best;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
             best = other > best ? other : best;
         }
-        if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
+        unsigned long long* sb = s_best + (it & 1) * 32;
+        if (lane == 0) sb[warp] = best;
         __syncthreads();
-        if (threadIdx.x < 32) {
-            unsigned long long b = threadIdx.x < (blockDim.x >> 5) ? s_best[threadIdx.x] : 0ull;
+        unsigned long long bb = sb[lane];  // ORD_THREADS / 32 = 32 warps
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long other = __shfl_xor_sync(0xffffffffu, b, o);
-                b = other > b ? other : b;
-            }
-            if (threadIdx.x == 0) s_best[0] = b;
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, bb, o);
+            bb = other > bb ? other : bb;
         }
-        __syncthreads();
-        p = int(~uint32_t(s_best[0] & 0xffffffffull));
-        __syncthreads();
+        p = int(~uint32_t(bb & 0xffffffffull));
     }
+}
+
+// Nearest centre of every point (exact FP32, dimensions summed in order; ties:
+// the lower centre) and its distance.  Centres are zero-padded to ORD_DMAX
+// dimensions in shared memory and the point's row to ORD_DMAX registers, so
+// the padded terms add exactly 0.
+__global__ void __launch_bounds__(256) cell_assign_kernel(const float* __restrict__ X, int64_t n, int d,
+                                                         const float* __restrict__ centre, int K,
+                                                         int32_t* __restrict__ cell, float* __restrict__ cdist) {
+    extern __shared__ __align__(16) float s_c[];  // [K][ORD_DMAX]
+    for (int t = threadIdx.x; t < K * ORD_DMAX; t += blockDim.x) {
+        const int k = t / ORD_DMAX, c = t % ORD_DMAX;
+        s_c[t] = c < d ? centre[k * d + c] : 0.f;
+    }
+    __syncthreads();
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float x[ORD_DMAX];
+#pragma unroll
+    for (int c = 0; c < ORD_DMAX; ++c) x[c] = c < d ? X[i * d + c] : 0.f;
+    float bd = INFINITY;
+    int32_t bk = 0;
+    for (int k = 0; k < K; ++k) {
+        const float4* cv = reinterpret_cast<const float4*>(s_c + k * ORD_DMAX);
+        float sq = 0.f;
+#pragma unroll
+        for (int c4 = 0; c4 < ORD_DMAX / 4; ++c4) {
+            const float4 v = cv[c4];
+            float df = x[4 * c4] - v.x;
+            sq = fmaf(df, df, sq);
+            df = x[4 * c4 + 1] - v.y;
+            sq = fmaf(df, df, sq);
+            df = x[4 * c4 + 2] - v.z;
+            sq = fmaf(df, df, sq);
+            df = x[4 * c4 + 3] - v.w;
+            sq = fmaf(df, df, sq);
+        }
+        if (sq < bd) {
+            bd = sq;
+            bk = k;
+        }
+    }
+    cell[i] = bk;
+    cdist[i] = sqrtf(bd);
 }
 
 __global__ void gather_rows_kernel(const float* __restrict__ X, int d, const int32_t* __restrict__ rows, int count,
@@ -157,34 +226,45 @@ int knn_order_cells(int64_t n) {
 size_t knn_order_scratch_bytes(int64_t n, int d, int K) {
     const int64_t nchunk = (n + ORD_CHUNK - 1) / ORD_CHUNK;
     const size_t kc = size_t(K) * nchunk;
-    return Carve::round(size_t(K) * 4) + Carve::round(size_t(n) * 4) * 2 + 2 * Carve::round(kc * 4) +
+    const int64_t m = n < ORD_SUB ? n : ORD_SUB;
+    return Carve::round(size_t(K) * 4) + Carve::round(size_t(m) * sub_pitch(d) * 4) + Carve::round(size_t(n) * 4) * 2 + 2 * Carve::round(kc * 4) +
            Carve::round(scan_scratch_elems(int64_t(kc)) * 4) + 4096;
 }
 
 int knn_order(Ctx* c, const float* X, int64_t n, int d, int K, int32_t* perm, int32_t* cell_beg, float* centre,
               float* radius, void* scratch, cudaStream_t st) {
-    if (d > 64) return set_error(c, DRGB_ERR_INVALID, "knn order: d > 64");
-    const int m = int(n < ORD_SUB ? n : ORD_SUB);
+    if (d > ORD_DMAX) return set_error(c, DRGB_ERR_INVALID, "knn order: d > 64");
+    if (K > 128) return set_error(c, DRGB_ERR_INVALID, "knn order: more than 128 cells");
+    int64_t m64 = int64_t(K) * ORD_PER_PIVOT;
+    if (m64 > ORD_SUB) m64 = ORD_SUB;
+    if (m64 > n) m64 = n;
+    const int m = int(m64), pitch = sub_pitch(d);
     const int nchunk = int((n + ORD_CHUNK - 1) / ORD_CHUNK);
     const size_t kc = size_t(K) * nchunk;
     Carve cv(scratch);
     int32_t* pivots = cv.take<int32_t>(K);
+    __half2* S = cv.take<__half2>(size_t(m) * pitch);
     int32_t* cell = cv.take<int32_t>(n);
     float* cdist = cv.take<float>(n);
     int32_t* counts = cv.take<int32_t>(kc);
     int32_t* offs = cv.take<int32_t>(kc);
     int32_t* tmp = cv.take<int32_t>(scan_scratch_elems(int64_t(kc)));
 
-    const size_t fsm = size_t(ORD_SUB) * 4 + 32 * 8 + size_t(m) * d * 2;
+    sub_gather_kernel<<<grid_for(int64_t(m) * pitch, 256, c->num_sms), 256, 0, st>>>(X, n, d, m, pitch, S);
+    DRGB_CHECK_LAUNCH(c);
+    const size_t fsm = 64 * 8 + size_t(m) * pitch * 4;
     DRGB_CUDA(c, cudaFuncSetAttribute(fps_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fsm)));
-    fps_cta_kernel<<<1, ORD_THREADS, fsm, st>>>(X, n, d, m, K, pivots);
+    fps_cta_kernel<<<1, ORD_THREADS, fsm, st>>>(S, n, m, pitch, K, pivots);
     DRGB_CHECK_LAUNCH(c);
     // the pivots are the cells' centres; a cell's radius is the largest
     // distance from its points to its pivot (the assignment's own distances)
     gather_rows_kernel<<<grid_for(int64_t(K) * d, 256, c->num_sms), 256, 0, st>>>(X, d, pivots, K, centre);
     DRGB_CHECK_LAUNCH(c);
-    int rc = launch_knn_query(c, X, n, centre, K, d, 1, cell, cdist, st);
-    if (rc) return rc;
+    const size_t asm_bytes = size_t(K) * ORD_DMAX * 4;
+    DRGB_CUDA(c, cudaFuncSetAttribute(cell_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(asm_bytes)));
+    cell_assign_kernel<<<unsigned((n + 255) / 256), 256, asm_bytes, st>>>(X, n, d, centre, K, cell, cdist);
+    DRGB_CHECK_LAUNCH(c);
+    int rc = DRGB_OK;
     DRGB_CUDA(c, cudaMemsetAsync(radius, 0, size_t(K) * 4, st));
     cell_count_kernel<<<nchunk, 256, size_t(K) * 8, st>>>(cell, cdist, n, K, nchunk, counts,
                                                          reinterpret_cast<unsigned int*>(radius));
