@@ -82,12 +82,18 @@ __device__ __forceinline__ void tile_distances(const float* __restrict__ X, int6
 // With p_end > 0 the scan covers only database points [p_begin, p_end) and the
 // k best of that range are written as partial list blockIdx.y of row r
 // (idx_out/dist_out + (blockIdx.y * n_rows + r) * k, squared distances).
+//
+// With ub, ub[qi * k + k - 1] is the distance (FP32, square-rooted) of the
+// k-th of k distinct points other than qi, or INFINITY; only points at most
+// that far are kept (the k nearest all are), so lists may end early with
+// index -1.
 template <int K>
 __global__ void __launch_bounds__(KNN_THREADS)
 knn_exact_kernel(const float* __restrict__ X, int64_t n, int d, int k,
                  const int64_t* __restrict__ rows, int64_t n_rows, int32_t* __restrict__ idx_out,
                  float* __restrict__ dist_out, int write_sqrt, const int32_t* __restrict__ rows32,
-                 const int32_t* __restrict__ n_rows_dev, int64_t chunk = 0, const float* __restrict__ Qx = nullptr) {
+                 const int32_t* __restrict__ n_rows_dev, int64_t chunk = 0, const float* __restrict__ Qx = nullptr,
+                 const float* __restrict__ ub = nullptr) {
     // queries come from Qx (a separate matrix, no self to exclude) or from X
     const float* Q = Qx ? Qx : X;
     const int64_t self_off = Qx ? -1 : 0;
@@ -106,11 +112,19 @@ knn_exact_kernel(const float* __restrict__ X, int64_t n, int d, int k,
         p_end = p_begin + chunk < n ? p_begin + chunk : n;
         orow = int64_t(blockIdx.y) * n_rows + r;
     }
+    // admission bound: the square of the k-th listed distance, rounded up past
+    // the rounding of the square root and of this square
+    float T = INFINITY;
+    if (ub && valid) {
+        const float u = ub[qi * k + k - 1];
+        T = u * u * (1.0f + 1e-6f);
+        if (!(T < INFINITY)) T = INFINITY;
+    }
     float D[K];
     int32_t I[K];
 #pragma unroll
     for (int s = 0; s < K; ++s) {
-        D[s] = INFINITY;
+        D[s] = T;
         I[s] = -1;
     }
     float acc[TP];
@@ -158,11 +172,22 @@ __global__ void merge_partials_kernel(const int32_t* __restrict__ pidx, const fl
             D[s] = INFINITY;
             I[s] = INT32_MAX;
         }
-        for (int c = lane; c < C; c += 32) {
-            const int64_t base = (int64_t(c) * cnt + r) * k;
+        for (int c0 = lane; c0 < C; c0 += 4 * 32) {
+          // the heads of four lists are loaded together; a list whose head
+          // is empty (-1) or not better than the current K-th is skipped
+          int32_t hj[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+              const int c = c0 + u * 32;
+              hj[u] = c < C ? pidx[(int64_t(c) * cnt + r) * k] : -1;
+          }
+#pragma unroll 1
+          for (int u = 0; u < 4; ++u) {
+            if (hj[u] < 0) continue;
+            const int64_t base = (int64_t(c0 + u * 32) * cnt + r) * k;
             for (int s = 0; s < k; ++s) {
                 const float a = pd2[base + s];
-                const int32_t j = pidx[base + s];
+                const int32_t j = s ? pidx[base + s] : hj[u];
                 if (j < 0 || !lex_less<K>(a, j, D[K - 1], I[K - 1])) break;  // each list is ascending
 #pragma unroll
                 for (int t = K - 1; t > 0; --t) {
@@ -176,6 +201,7 @@ __global__ void merge_partials_kernel(const int32_t* __restrict__ pidx, const fl
                     I[0] = j;
                 }
             }
+          }
         }
         const int64_t row = rows32[r];
         for (int s = 0; s < k; ++s) {
@@ -233,10 +259,10 @@ int launch_knn_exact_rows(Ctx* c, const float* X, int64_t n, int d, int k, const
         const int blocks = row_blocks;
         if (k <= 16)
             knn_exact_kernel<16><<<blocks, KNN_THREADS, 0, st>>>(X, n, d, k, nullptr, cnt, idx_out, dist_out, 1,
-                                                                rows32, n_rows_dev);
+                                                                rows32, n_rows_dev, 0, nullptr, dist_out);
         else
             knn_exact_kernel<32><<<blocks, KNN_THREADS, 0, st>>>(X, n, d, k, nullptr, cnt, idx_out, dist_out, 1,
-                                                                rows32, n_rows_dev);
+                                                                rows32, n_rows_dev, 0, nullptr, dist_out);
         DRGB_CHECK_LAUNCH(c);
         return DRGB_OK;
     }
@@ -247,10 +273,10 @@ int launch_knn_exact_rows(Ctx* c, const float* X, int64_t n, int d, int k, const
     dim3 grid(row_blocks, unsigned(C));
     if (k <= 16)
         knn_exact_kernel<16><<<grid, KNN_THREADS, 0, st>>>(X, n, d, k, nullptr, cnt, pidx, pd2, 0, rows32,
-                                                          nullptr, chunk);
+                                                          nullptr, chunk, nullptr, dist_out);
     else
         knn_exact_kernel<32><<<grid, KNN_THREADS, 0, st>>>(X, n, d, k, nullptr, cnt, pidx, pd2, 0, rows32,
-                                                          nullptr, chunk);
+                                                          nullptr, chunk, nullptr, dist_out);
     DRGB_CHECK_LAUNCH(c);
     const int mb = grid_for(cnt, 4, c->num_sms * 8);   // one warp per row, 4 warps per CTA
     if (k <= 16)

@@ -11,9 +11,13 @@ int launch_knn_exact(Ctx* c, const float* X, int64_t n, int d, int k, const int6
                      int64_t n_rows, int32_t* idx_out, float* dist_out, bool write_sqrt,
                      cudaStream_t st);
 // Exact FP32 scan of the rows listed in rows32[0 .. *n_rows_dev) (at most
-// max_rows); results are written to those rows.  Synchronises `st` once to
-// read the count, then splits the scan over database chunks (partial lists in
-// part_scratch, merged by a second kernel).
+// max_rows); results are written to those rows.  On entry each listed row of
+// idx_out/dist_out must already hold k distinct points other than the row in
+// ascending order of their FP32 distances (the direct sum over dimensions),
+// INFINITY where it has fewer: the scan keeps only points within the listed
+// k-th distance.  Synchronises `st` once to read the count, then splits the
+// scan over database chunks (partial lists in part_scratch, merged by a
+// second kernel).
 int launch_knn_exact_rows(Ctx* c, const float* X, int64_t n, int d, int k, const int32_t* rows32,
                           const int32_t* n_rows_dev, int64_t max_rows, int32_t* idx_out,
                           float* dist_out, cudaStream_t st, void* part_scratch, size_t part_bytes);

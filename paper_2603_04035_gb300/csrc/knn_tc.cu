@@ -132,31 +132,82 @@ __device__ __forceinline__ float operand_scale(const unsigned int* maxbits) {
     return ldexpf(1.0f, e - 10);
 }
 
-__global__ void tc_absmax_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ mean,
-                                 unsigned int* __restrict__ maxbits) {
-    float m = 0.f;
-    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n * d; t += int64_t(gridDim.x) * blockDim.x)
-        m = fmaxf(m, fabsf(X[t] - mean[t % d]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(&maxbits[2], __float_as_uint(m));
-}
+// Column statistics of X (d <= 64) for the operand staging.  Block b sums,
+// and takes the minimum and maximum of, every column over its range of rows
+// (a warp per row, lanes on dimensions (lane, lane + 32)) into partial[b]; the
+// last block to finish (ticket maxbits[3]) reduces the partials to the column
+// means (summed in double) and the largest |x - mean| (maxbits[2]).  Rounding
+// is monotone, so over a column the largest fl(x - m) is fl(max - m) and the
+// largest fl(m - x) is fl(m - min): this equals max |fl(x - m)| elementwise.
+static constexpr int TC_STAT_WARPS = 8;
 
-__global__ void tc_colsum_kernel(const float* __restrict__ X, int64_t n, int d, float* __restrict__ partial) {
-    // partial[blockIdx.x * d + c] = sum over this block's rows of X[., c]; thread c strides rows
-    for (int c = threadIdx.x; c < d; c += blockDim.x) {
-        float s = 0.f;
-        for (int64_t i = blockIdx.x; i < n; i += gridDim.x) s += X[i * d + c];
-        partial[int64_t(blockIdx.x) * d + c] = s;
+__global__ void __launch_bounds__(TC_STAT_WARPS * 32)
+tc_colstats_kernel(const float* __restrict__ X, int64_t n, int d, float* __restrict__ partial,
+                   float* __restrict__ mean, unsigned int* __restrict__ maxbits) {
+    __shared__ float s_sum[TC_STAT_WARPS][64], s_lo[TC_STAT_WARPS][64], s_hi[TC_STAT_WARPS][64];
+    __shared__ bool s_last;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = int64_t(blockIdx.x) * per;
+    const int64_t r1 = r0 + per < n ? r0 + per : n;
+    const bool in0 = lane < d, in1 = lane + 32 < d;
+    float s0 = 0.f, s1 = 0.f, lo0 = INFINITY, lo1 = INFINITY, hi0 = -INFINITY, hi1 = -INFINITY;
+#pragma unroll 4
+    for (int64_t r = r0 + w; r < r1; r += TC_STAT_WARPS) {
+        const float* xr = X + r * d;
+        if (in0) {
+            const float v = xr[lane];
+            s0 += v;
+            lo0 = fminf(lo0, v);
+            hi0 = fmaxf(hi0, v);
+        }
+        if (in1) {
+            const float v = xr[lane + 32];
+            s1 += v;
+            lo1 = fminf(lo1, v);
+            hi1 = fmaxf(hi1, v);
+        }
     }
-}
-
-__global__ void tc_mean_kernel(const float* __restrict__ partial, int nblk, int d, int64_t n,
-                               float* __restrict__ mean) {
-    for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    s_sum[w][lane] = s0;
+    s_sum[w][lane + 32] = s1;
+    s_lo[w][lane] = lo0;
+    s_lo[w][lane + 32] = lo1;
+    s_hi[w][lane] = hi0;
+    s_hi[w][lane + 32] = hi1;
+    __syncthreads();
+    if (threadIdx.x < 64) {
+        const int c = threadIdx.x;
+        float s = 0.f, lo = INFINITY, hi = -INFINITY;
+        for (int u = 0; u < TC_STAT_WARPS; ++u) {
+            s += s_sum[u][c];
+            lo = fminf(lo, s_lo[u][c]);
+            hi = fmaxf(hi, s_hi[u][c]);
+        }
+        float* pb = partial + int64_t(blockIdx.x) * 3 * 64;
+        pb[c] = s;
+        pb[64 + c] = lo;
+        pb[128 + c] = hi;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&maxbits[3], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x < d) {
+        const int c = threadIdx.x;
         double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += partial[int64_t(b) * d + c];
-        mean[c] = float(s / double(n));
+        float lo = INFINITY, hi = -INFINITY;
+        for (int b = 0; b < int(gridDim.x); ++b) {
+            const float* pb = partial + int64_t(b) * 3 * 64;
+            s += double(__ldcg(pb + c));
+            lo = fminf(lo, __ldcg(pb + 64 + c));
+            hi = fmaxf(hi, __ldcg(pb + 128 + c));
+        }
+        const float m = float(s / double(n));
+        mean[c] = m;
+        const float amax = fmaxf(0.f, fmaxf(hi - m, m - lo));
+        atomicMax(&maxbits[2], __float_as_uint(amax));
     }
 }
 
@@ -800,7 +851,7 @@ static int tc_cells(int64_t n_pad, int64_t n) { return n_pad / TC_BN > TC_MAX_TI
 
 static size_t tc_scratch_bytes(int64_t n, int d, int64_t n_pad, int nblk) {
     const int K = tc_cells(n_pad, n);
-    return Carve::round(size_t(nblk) * d * 4) + Carve::round(d * 4) + 2 * Carve::round(n_pad * TC_K * 2) +
+    return Carve::round(size_t(nblk) * 3 * 64 * 4) + Carve::round(d * 4) + 2 * Carve::round(n_pad * TC_K * 2) +
            2 * Carve::round(n_pad * 4) + Carve::round(64) + 2 * Carve::round(n_pad * TC_KP * 4) +
            Carve::round(n * 4) + Carve::round(64) + TC_PART_BYTES + Carve::round(n_pad * 4) +
            Carve::round((TC_CELLS + 1) * 4) + Carve::round(size_t(TC_CELLS) * d * 4) + Carve::round(TC_CELLS * 4) +
@@ -825,7 +876,7 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
     const int nblk = TC_COLSUM_BLOCKS;
     int rc = DRGB_OK;
     Carve cv(scratch);
-    float* partial = cv.take<float>(size_t(nblk) * d);
+    float* partial = cv.take<float>(size_t(nblk) * 3 * 64);
     float* mean = cv.take<float>(d);
     op16* XA = cv.take<op16>(n_pad * TC_K);
     op16* XB = cv.take<op16>(n_pad * TC_K);
@@ -848,14 +899,8 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
 
     DRGB_CUDA(c, cudaMemsetAsync(maxbits, 0, 64, st));
     DRGB_CUDA(c, cudaMemsetAsync(fail_count, 0, 64, st));
-    tc_colsum_kernel<<<nblk, 64, 0, st>>>(X, n, d, partial);
+    tc_colstats_kernel<<<nblk, TC_STAT_WARPS * 32, 0, st>>>(X, n, d, partial, mean, maxbits);
     DRGB_CHECK_LAUNCH(c);
-    tc_mean_kernel<<<1, 64, 0, st>>>(partial, nblk, d, n, mean);
-    DRGB_CHECK_LAUNCH(c);
-    if (F16) {
-        tc_absmax_kernel<<<grid_for(n * d, 256, c->num_sms * 8), 256, 0, st>>>(X, n, d, mean, maxbits);
-        DRGB_CHECK_LAUNCH(c);
-    }
     // spatial order (K > 1) or the identity with one cell holding everything
     if (K == 1) DRGB_CUDA(c, cudaMemsetAsync(cell_c, 0, size_t(d) * 4, st));
     tc_identity_kernel<<<grid_for(n_pad, 256, c->num_sms * 8), 256, 0, st>>>(perm, n, n_pad, K == 1, cell_beg,
