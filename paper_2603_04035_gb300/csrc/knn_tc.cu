@@ -53,11 +53,12 @@ static constexpr int TC_TMEM_COLS = 512;               // two 256-column accumul
 static constexpr int TC_QCAP = 32;                     // per-thread candidate queue slots (one chunk)
 static constexpr size_t TC_QUEUE_BYTES = size_t(TC_EPI_WARPS) * 32 * TC_QCAP * 8;
 static constexpr size_t TC_THR_BYTES = size_t(2) * TC_BM * 4;   // per (column half, row) threshold
-static constexpr int TC_CELLS = 256;                   // most cells a schedule may hold
+static constexpr int TC_CELLS = 128;                   // most cells a schedule may hold
+static constexpr int TC_GROUPS = 4;                    // row groups (runs of one cell) bounded separately
 static constexpr int TC_RING = 16;                     // tile-index ring (slots in flight < 16)
 static constexpr int TC_MAX_TILES = 98304;             // database tiles the visited-tile bitmap covers
 static constexpr size_t TC_SCHED_BYTES =
-    size_t(TC_CELLS) * 8 + TC_BM * 4 + TC_RING * 8 + 64 + TC_MAX_TILES / 8;
+    size_t(TC_CELLS) * 8 + size_t(TC_GROUPS) * TC_CELLS * 4 + 32 + TC_BM * 4 + TC_RING * 8 + 64 + TC_MAX_TILES / 8;
 static constexpr size_t TC_SMEM =
     1024 + TC_A_BYTES + TC_STAGES * TC_B_BYTES + 256 + TC_QUEUE_BYTES + TC_THR_BYTES + TC_SCHED_BYTES;
 
@@ -340,14 +341,28 @@ __device__ __forceinline__ void cta_sort_pairs(float* v, int32_t* ix) {
     __syncthreads();
 }
 
-// One CTA per 128 query positions.  Before the pipeline starts, the CTA bounds
-// its rows by a sphere, computes for every cell a lower bound on the distance
-// between any of its rows and any point of the cell, and sorts the cells by
-// that bound.  Warp 0 then streams the database tiles of the cells in that
-// order (each tile once), and stops at the first cell whose bound exceeds
-// every row's current upper bound on its 32nd-nearest distance: no point of
-// that or any later cell can enter any row's list.  The bound at which it
-// stopped is returned per row for the certificate.  Tile indices travel to
+// Cell of position p: the c with cell_beg[c] <= p < cell_beg[c + 1].
+__device__ __forceinline__ int cell_of(const int32_t* __restrict__ cell_beg, int K, int64_t p) {
+    int lo = 0, hi = K - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cell_beg[mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One CTA per 128 query positions.  Before the pipeline starts, the CTA splits
+// its rows into groups (rows are in cell order: each run of one cell is a
+// group; rows past the fourth run join the last group), bounds every group by
+// a sphere, computes for every (group, cell) a lower bound on the distance
+// between any row of the group and any point of the cell, and sorts the cells
+// by their smallest bound.  Warp 0 then streams the database tiles of the
+// cells in that order (each tile once).  A cell is skipped when, for every
+// group, its bound exceeds the largest current upper bound on a row's
+// 32nd-nearest distance in that group (its points cannot enter any row's
+// list), and the stream stops at the first cell whose smallest bound exceeds
+// every group's: the same then holds for it and every later cell.  The bound
+// at which it stopped is returned per row for the certificate.  Tile indices travel to
 // the MMA and epilogue warps through a small ring; a slot holding -1 ends the
 // stream.
 template <bool F16>
@@ -375,7 +390,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     // tile ring (slot number and tile), misc words, visited-tile bitmap
     float* s_lb = s_thr + 2 * TC_BM;
     int32_t* s_cl = reinterpret_cast<int32_t*>(s_lb + TC_CELLS);
-    volatile float* s_U = reinterpret_cast<volatile float*>(s_cl + TC_CELLS);
+    float* s_glb = reinterpret_cast<float*>(s_cl + TC_CELLS);                // [TC_GROUPS][TC_CELLS]
+    int32_t* s_gb = reinterpret_cast<int32_t*>(s_glb + TC_GROUPS * TC_CELLS);  // [TC_GROUPS + 1] (+pad)
+    volatile float* s_U = reinterpret_cast<volatile float*>(s_gb + 8);
     volatile int32_t* ring_t = reinterpret_cast<volatile int32_t*>(s_U + TC_BM);
     volatile int32_t* ring_tile = ring_t + TC_RING;
     float* s_misc = const_cast<float*>(reinterpret_cast<volatile float*>(ring_tile + TC_RING));  // [16]
@@ -409,7 +426,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     // the block's rows meanwhile)
     {
         float* s_rows = reinterpret_cast<float*>(sB);    // [TC_BM][64]
-        float* s_cen = s_rows + TC_BM * 64;              // [64]
+        float* s_gcen = s_rows + TC_BM * 64;             // [TC_GROUPS][64] group centres
+        unsigned int* s_grad = reinterpret_cast<unsigned int*>(s_gcen + TC_GROUPS * 64);  // radius bits
+        float* s_gcn = reinterpret_cast<float*>(s_grad + TC_GROUPS);                     // |centre|
         for (int t = threadIdx.x; t < TC_BM * 64; t += blockDim.x) {
             const int r = t >> 6, c = t & 63;
             s_rows[t] = (r < nrow && c < P.d) ? P.X[int64_t(P.perm[q0 + r]) * P.d + c] : 0.f;
@@ -420,46 +439,79 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             ring_t[threadIdx.x] = -1;
             ring_tile[threadIdx.x] = -1;
         }
+        if (threadIdx.x <= TC_GROUPS) s_gb[threadIdx.x] = nrow;
+        if (threadIdx.x < TC_GROUPS) s_grad[threadIdx.x] = 0u;
+        if (threadIdx.x == 0) s_misc[1] = INFINITY;   // stopping bound
+        __syncthreads();
+        int grp = -1;
+        if (threadIdx.x < nrow) {
+            const int c0 = cell_of(P.cell_beg, P.K, q0);
+            const int cr = cell_of(P.cell_beg, P.K, q0 + threadIdx.x);
+            grp = cr - c0 < TC_GROUPS - 1 ? cr - c0 : TC_GROUPS - 1;
+            atomicMin(&s_gb[grp], int32_t(threadIdx.x));
+        }
+        __syncthreads();
         if (threadIdx.x == 0) {
-            s_misc[0] = 0.f;        // block radius (bits are compared as unsigned)
-            s_misc[1] = INFINITY;   // stopping bound
+            // group g holds rows [s_gb[g], s_gb[g + 1]) (empty groups: equal ends)
+            for (int g = TC_GROUPS - 1; g >= 0; --g) s_gb[g] = s_gb[g] < s_gb[g + 1] ? s_gb[g] : s_gb[g + 1];
         }
         __syncthreads();
         if (threadIdx.x < 64) {
-            float sum = 0.f;
-            for (int r = 0; r < nrow; ++r) sum += s_rows[r * 64 + threadIdx.x];
-            s_cen[threadIdx.x] = sum / float(nrow > 0 ? nrow : 1);
+            for (int g = 0; g < TC_GROUPS; ++g) {
+                const int r0 = s_gb[g], r1 = s_gb[g + 1];
+                float sum = 0.f;
+                for (int r = r0; r < r1; ++r) sum += s_rows[r * 64 + threadIdx.x];
+                s_gcen[g * 64 + threadIdx.x] = r1 > r0 ? sum / float(r1 - r0) : 0.f;
+            }
         }
         __syncthreads();
-        if (threadIdx.x < nrow) {
+        if (grp >= 0) {
             float sq = 0.f;
             for (int c = 0; c < P.d; ++c) {
-                const float df = s_rows[threadIdx.x * 64 + c] - s_cen[c];
+                const float df = s_rows[threadIdx.x * 64 + c] - s_gcen[grp * 64 + c];
                 sq = fmaf(df, df, sq);
             }
-            atomicMax(reinterpret_cast<unsigned int*>(&s_misc[0]), __float_as_uint(sqrtf(sq)));
+            atomicMax(&s_grad[grp], __float_as_uint(sqrtf(sq)));
+        }
+        if (threadIdx.x < TC_GROUPS) {
+            float cb2 = 0.f;
+            for (int c = 0; c < P.d; ++c) cb2 = fmaf(s_gcen[threadIdx.x * 64 + c], s_gcen[threadIdx.x * 64 + c], cb2);
+            s_gcn[threadIdx.x] = sqrtf(cb2);
         }
         __syncthreads();
-        const float rb = s_misc[0];
-        float cb2 = 0.f;
-        for (int c = 0; c < P.d; ++c) cb2 = fmaf(s_cen[c], s_cen[c], cb2);
-        const float cbn = sqrtf(cb2);
         for (int ci = threadIdx.x; ci < TC_CELLS; ci += blockDim.x) {
-            float lb = INFINITY;
+            float lbmin = INFINITY;
+            float lbg[TC_GROUPS];
+#pragma unroll
+            for (int g = 0; g < TC_GROUPS; ++g) lbg[g] = INFINITY;
             if (ci < P.K && P.cell_beg[ci + 1] > P.cell_beg[ci]) {
-                float dd = 0.f, cc = 0.f;
+                float dd[TC_GROUPS], cc = 0.f;
+#pragma unroll
+                for (int g = 0; g < TC_GROUPS; ++g) dd[g] = 0.f;
                 for (int c = 0; c < P.d; ++c) {
                     const float v = P.cell_c[int64_t(ci) * P.d + c];
-                    const float df = s_cen[c] - v;
-                    dd = fmaf(df, df, dd);
                     cc = fmaf(v, v, cc);
+#pragma unroll
+                    for (int g = 0; g < TC_GROUPS; ++g) {
+                        const float df = s_gcen[g * 64 + c] - v;
+                        dd[g] = fmaf(df, df, dd[g]);
+                    }
                 }
-                const float dist = sqrtf(dd), rc = P.cell_r[ci];
-                // FP32 rounding of the centres, radii and this distance is
-                // covered by a relative margin on everything involved
-                lb = fmaxf(0.f, dist - rb - rc - 1e-5f * (dist + rb + rc + cbn + sqrtf(cc)));
+                const float rc = P.cell_r[ci], cn = sqrtf(cc);
+#pragma unroll
+                for (int g = 0; g < TC_GROUPS; ++g) {
+                    if (s_gb[g + 1] > s_gb[g]) {
+                        const float dist = sqrtf(dd[g]), rb = __uint_as_float(s_grad[g]);
+                        // FP32 rounding of the centres, radii and this distance
+                        // is covered by a relative margin on everything involved
+                        lbg[g] = fmaxf(0.f, dist - rb - rc - 1e-5f * (dist + rb + rc + s_gcn[g] + cn));
+                        lbmin = fminf(lbmin, lbg[g]);
+                    }
+                }
             }
-            s_lb[ci] = lb;
+#pragma unroll
+            for (int g = 0; g < TC_GROUPS; ++g) s_glb[g * TC_CELLS + ci] = lbg[g];
+            s_lb[ci] = lbmin;
             s_cl[ci] = ci;
         }
         cta_sort_pairs(s_lb, s_cl);   // ends with __syncthreads
@@ -481,14 +533,26 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         for (int ci = 0; ci < P.K && stop_ok; ++ci) {
             const float lb = s_lb[ci];
             if (!(lb < INFINITY)) break;  // empty cells sort last
-            float u = fmaxf(fmaxf(s_U[lane], s_U[lane + 32]), fmaxf(s_U[lane + 64], s_U[lane + 96]));
+            const int cell = s_cl[ci];
+            // per group: the largest current bound of its rows; the cell is
+            // needed when its bound for some group does not exceed that
+            float umax = -INFINITY;
+            bool need = false;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) u = fmaxf(u, __shfl_xor_sync(0xffffffffu, u, o));
-            if (lb > u) {
+            for (int g = 0; g < TC_GROUPS; ++g) {
+                const int r0 = s_gb[g], r1 = s_gb[g + 1];
+                float u = -INFINITY;
+                for (int r = r0 + lane; r < r1; r += 32) u = fmaxf(u, s_U[r]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) u = fmaxf(u, __shfl_xor_sync(0xffffffffu, u, o));
+                umax = fmaxf(umax, u);
+                need = need || s_glb[g * TC_CELLS + cell] <= u;
+            }
+            if (lb > umax) {
                 lbstop = lb;
                 break;
             }
-            const int cell = s_cl[ci];
+            if (!need) continue;
             const int tb = P.cell_beg[cell] / TC_BN, te = (P.cell_beg[cell + 1] - 1) / TC_BN;
             for (int tile = tb; tile <= te && stop_ok; ++tile) {
                 if (P.K > 1) {  // one cell covers every tile once: no bitmap needed
