@@ -83,7 +83,9 @@ __global__ void __launch_bounds__(G_THREADS, 1)
 mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs G) {
     using SM = GemmSmem<BN>;
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // 1024-byte aligned (swizzled operand tiles); an offset from the shared
+    // array, so that every pointer below stays a known shared-memory address
+    uint8_t* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint8_t* sA = base;
     uint8_t* sB = base + G_STAGES * SM::A_BYTES;
     uint64_t* bars = reinterpret_cast<uint64_t*>(sB + G_STAGES * SM::B_BYTES);
