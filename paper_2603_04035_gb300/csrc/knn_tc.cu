@@ -58,7 +58,8 @@ static constexpr int TC_GROUPS = 4;                    // row groups (runs of on
 static constexpr int TC_RING = 16;                     // tile-index ring (slots in flight < 16)
 static constexpr int TC_MAX_TILES = 98304;             // database tiles the visited-tile bitmap covers
 static constexpr size_t TC_SCHED_BYTES =
-    size_t(TC_CELLS) * 8 + size_t(TC_GROUPS) * TC_CELLS * 4 + 32 + TC_BM * 4 + TC_RING * 8 + 64 + TC_MAX_TILES / 8;
+    size_t(TC_CELLS) * 8 + size_t(TC_GROUPS) * TC_CELLS * 4 + 32 + TC_BM * 4 + TC_RING * 8 + 64 + TC_MAX_TILES / 8 +
+    size_t(2) * TC_BM * 4;
 static constexpr size_t TC_SMEM =
     1024 + TC_A_BYTES + TC_STAGES * TC_B_BYTES + 256 + TC_QUEUE_BYTES + TC_THR_BYTES + TC_SCHED_BYTES;
 
@@ -399,6 +400,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     volatile int32_t* ring_tile = ring_t + TC_RING;
     float* s_misc = const_cast<float*>(reinterpret_cast<volatile float*>(ring_tile + TC_RING));  // [16]
     uint32_t* s_done = reinterpret_cast<uint32_t*>(s_misc + 16);
+    // per row: the constant parts of its distance bound (see the epilogue)
+    float* s_ua = reinterpret_cast<float*>(s_done + TC_MAX_TILES / 32);
+    float* s_uc = s_ua + TC_BM;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t q0 = int64_t(blockIdx.x) * TC_BM;
@@ -443,7 +447,11 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         }
         if (threadIdx.x <= TC_GROUPS) s_gb[threadIdx.x] = nrow;
         if (threadIdx.x < TC_GROUPS) s_grad[threadIdx.x] = 0u;
-        if (threadIdx.x == 0) s_misc[1] = INFINITY;   // stopping bound
+        if (threadIdx.x == 0) {
+            s_misc[1] = INFINITY;   // stopping bound
+            const float S = operand_scale<F16>(P.maxbits);
+            s_misc[2] = S * S;      // threshold units -> squared distance units
+        }
         __syncthreads();
         int grp = -1;
         if (threadIdx.x < nrow) {
@@ -650,6 +658,20 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         // this row's point (its norm and residual convert a threshold on s
         // into an upper bound on the distance of its 32nd candidate)
         const int64_t g_row = row < nrow ? int64_t(P.perm[q0 + row]) : -1;
+        // the row's bound on its 32nd candidate's distance for threshold thr
+        // is (sqrt(max(ua + thr S^2, 0)) + uc)(1 + 1e-5), ua = n_i + eps_i and
+        // uc = resid_i + r_max (the relative margin covers FP32 rounding)
+        if (half == 0) {
+            float ua = INFINITY, uc = 0.f;
+            if (g_row >= 0) {
+                const float r_max = __uint_as_float(P.maxbits[1]), n_max = __uint_as_float(P.maxbits[0]);
+                const float ni = P.norm[g_row];
+                ua = ni + 6.103515625e-05f * (ni + n_max);
+                uc = P.resid[g_row] + r_max;
+            }
+            s_ua[row] = ua;
+            s_uc[row] = uc;
+        }
         // Candidates below the row's threshold are appended to this thread's
         // queue (slot s at q[s * 256 + tid], conflict-free).  The threshold
         // is the smaller of the two column halves' 32nd-best values: a value at
@@ -688,13 +710,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             qn = 0;
             *thr_mine = L[TC_KP - 1];
             const float thr = fminf(L[TC_KP - 1], *thr_other);
-            if (g_row >= 0 && thr < INFINITY) {
-                const float S = operand_scale<F16>(P.maxbits);
-                const float r_max = __uint_as_float(P.maxbits[1]), n_max = __uint_as_float(P.maxbits[0]);
-                const float ni = P.norm[g_row];
-                const float eps_i = 6.103515625e-05f * (ni + n_max);
-                s_U[row] = (sqrtf(fmaxf(ni + thr * (S * S) + eps_i, 0.f)) + P.resid[g_row] + r_max) * (1.0f + 1e-5f);
-            }
+            if (g_row >= 0 && thr < INFINITY)
+                s_U[row] = (sqrtf(fmaxf(s_ua[row] + thr * s_misc[2], 0.f)) + s_uc[row]) * (1.0f + 1e-5f);
         };
         for (int t = 0;; ++t) {
             const int buf = t & 1, use = t >> 1;
@@ -713,12 +730,15 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             if (tile < 0) break;
             const uint32_t tbase = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(buf * TC_BN + half * 128);
             const int32_t j0 = tile * TC_BN + half * 128;
+            // the other half's threshold, read once per tile (a stale, larger,
+            // value is still a valid bound)
+            const float thr_o = *thr_other;
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 float v[32];
                 __syncwarp();
                 tmem_ld32(tbase + c * 32, v);
-                float thr = fminf(L[TC_KP - 1], *thr_other);
+                float thr = fminf(L[TC_KP - 1], thr_o);
                 float gm[4];
 #pragma unroll
                 for (int g = 0; g < 4; ++g)
