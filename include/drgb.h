@@ -163,12 +163,14 @@ int drgb_knn_tiles(drgb_ctx* ctx, int64_t* done, int64_t* total, void* stream);
  * Output is a CSR holding both (i,j) and (j,i), rows sorted by column, with
  * schedule words q = round(2^24 w / w_max); entries with n_epochs * q < 2^24
  * (never active in n_epochs epochs) are dropped.
- *   idx, dist  n x k (as produced by drgb_knn_graph; dist ascending per row).
+ *   idx, dist  n x k (as produced by drgb_knn_graph; dist ascending per row;
+ *              the k neighbours of a row distinct and other than the row).
  *   row_ptr    n + 1 int32 (row_ptr[n] = number of entries, written on device).
  *   col, w, q  capacity `cap` entries each (int32, FP32, uint32); cap >= 2 n k
  *              always suffices.
  *   rho, sigma optional n-float outputs (may be NULL).
- * Errors: DRGB_ERR_INVALID (bad sizes/pointers), DRGB_ERR_WORKSPACE if
+ * Errors: DRGB_ERR_INVALID (bad sizes/pointers; malformed neighbour lists
+ * are reported through the context's status word), DRGB_ERR_WORKSPACE if
  * cap < 2 n k. */
 int drgb_fuzzy_weights(drgb_ctx* ctx, const int32_t* idx, const float* dist, int64_t n,
                        int32_t k, int32_t n_epochs, int32_t* row_ptr, int32_t* col, float* w,

@@ -14,6 +14,7 @@
 //   7 count     entries kept (T q >= 2^24)
 //   8 scan      row_ptr
 //   9 fill      col, w, q
+// Passes 6, 7 and 9 take a warp per row.
 #include <mutex>
 
 #include "common.cuh"
@@ -55,7 +56,11 @@ __global__ void fuzzy_rows_kernel(const int32_t* __restrict__ idx, const float* 
             } else {
                 lo = mid;
             }
-            mid = (hi == INFINITY) ? mid * 2.f : 0.5f * (lo + hi);
+            const float nxt = (hi == INFINITY) ? mid * 2.f : 0.5f * (lo + hi);
+            // a step that leaves mid unchanged repeats itself (same test, same
+            // bound): every later step would too, so the 64-step result is mid
+            if (nxt == mid) break;
+            mid = nxt;
         }
         const float sigma = fmaxf(mid, 1e-3f * mean);
         if (rho_out) rho_out[i] = rho;
@@ -79,10 +84,13 @@ __global__ void fuzzy_rows_kernel(const int32_t* __restrict__ idx, const float* 
             jr[t + 1] = jj;
             wr[t + 1] = ww;
         }
+        bool dup = false;
         for (int s = 0; s < k; ++s) {
             out_col[i * k + s] = jr[s];
             out_w[i * k + s] = wr[s];
+            dup |= s > 0 && jr[s] == jr[s - 1];
         }
+        if (dup) report_status(status, DRGB_ERR_INVALID);  // a neighbour listed twice
     }
 }
 
@@ -138,56 +146,98 @@ __device__ __forceinline__ float fuzzy_union(float a, float b) {
     return fmaf(lo, 1.0f - hi, hi);
 }
 
+// Warp per row.  Out-list entry a (lane a < k; sorted by column, entries
+// reported invalid by pass 1 skipped) and in-list entry b (sorted by source,
+// hence by column) go straight to their place in the union sorted by column:
+// for a column x that place is #(valid out columns < x) + #(in columns < x)
+// - #(columns < x present in both), and a column present in both is written
+// once, by its out entry, with the fuzzy union of the two weights.  Columns
+// are distinct within each list.
 __global__ void merge_kernel(const int32_t* __restrict__ out_col, const float* __restrict__ out_w,
                              const int32_t* __restrict__ in_ptr, const int32_t* __restrict__ in_sorted,
                              const float* __restrict__ w_dir, int64_t n, int k,
                              int32_t* __restrict__ tcol, float* __restrict__ tw,
                              int32_t* __restrict__ tcnt, unsigned int* __restrict__ wmax_bits) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
     float local_max = 0.f;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t base = i * k + in_ptr[i];
-        const int32_t* oc = out_col + i * k;
-        const float* ow = out_w + i * k;
-        const int32_t ib = in_ptr[i], ie = in_ptr[i + 1];
-        int a = 0, bpos = ib, c = 0;
-        // skip invalid out entries (reported by pass 1)
-        while (a < k || bpos < ie) {
-            int32_t ca = INT32_MAX, cb = INT32_MAX;
-            if (a < k) {
-                ca = oc[a];
-                if (ca < 0 || ca >= n || ca == i) {
-                    ++a;
-                    continue;
+    for (int64_t i = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const int32_t ib = in_ptr[i], m = in_ptr[i + 1] - ib;
+        const int64_t base = i * k + ib;
+        int32_t ca = INT32_MAX;  // this lane's out column (INT32_MAX: none or invalid)
+        float wa = 0.f;
+        if (lane < k) {
+            const int32_t c0 = out_col[i * k + lane];
+            if (c0 >= 0 && c0 < n && c0 != i) {
+                ca = c0;
+                wa = out_w[i * k + lane];
+            }
+        }
+        // out entries: in columns below ca, and ca's in weight if present
+        int32_t in_less = 0;
+        bool matched = false;
+        float w_in = 0.f;
+        for (int32_t t0 = 0; t0 < m; t0 += 32) {
+            int32_t cb = INT32_MAX;
+            float wb = 0.f;
+            if (t0 + lane < m) {
+                const int32_t p = in_sorted[ib + t0 + lane];
+                cb = p / k;
+                wb = w_dir[p];
+            }
+            const int cnt = m - t0 < 32 ? m - t0 : 32;
+            for (int u = 0; u < cnt; ++u) {
+                const int32_t cu = __shfl_sync(0xffffffffu, cb, u);
+                const float wu = __shfl_sync(0xffffffffu, wb, u);
+                in_less += cu < ca;
+                if (cu == ca) {
+                    matched = true;
+                    w_in = wu;
                 }
             }
-            if (bpos < ie) cb = int32_t(in_sorted[bpos] / k);
-            float w;
-            int32_t col;
-            if (ca == cb) {
-                w = fuzzy_union(ow[a], w_dir[in_sorted[bpos]]);
-                col = ca;
-                ++a;
-                ++bpos;
-            } else if (ca < cb) {
-                w = ow[a];
-                col = ca;
-                ++a;
-            } else {
-                w = w_dir[in_sorted[bpos]];
-                col = cb;
-                ++bpos;
-            }
-            tcol[base + c] = col;
-            tw[base + c] = w;
-            ++c;
-            local_max = fmaxf(local_max, w);
         }
-        tcnt[i] = c;
+        const bool va = ca != INT32_MAX;
+        const unsigned vmask = __ballot_sync(0xffffffffu, va);
+        const unsigned mmask = __ballot_sync(0xffffffffu, va && matched);
+        if (va) {
+            const int32_t pos = __popc(vmask & lt) + in_less - __popc(mmask & lt);
+            const float wv = matched ? fuzzy_union(wa, w_in) : wa;
+            tcol[base + pos] = ca;
+            tw[base + pos] = wv;
+            local_max = fmaxf(local_max, wv);
+        }
+        // in entries without an out partner
+        for (int32_t t0 = 0; t0 < m; t0 += 32) {
+            const int32_t t = t0 + lane;
+            int32_t cb = INT32_MAX;
+            float wb = 0.f;
+            if (t < m) {
+                const int32_t p = in_sorted[ib + t];
+                cb = p / k;
+                wb = w_dir[p];
+            }
+            int32_t out_less = 0, both_less = 0;
+            bool partner = false;
+            for (int a = 0; a < k; ++a) {
+                const int32_t c_a = __shfl_sync(0xffffffffu, ca, a);
+                const bool lt_a = c_a < cb;
+                out_less += lt_a;
+                both_less += lt_a && ((mmask >> a) & 1u);
+                partner |= c_a == cb && c_a != INT32_MAX;
+            }
+            if (t < m && !partner) {
+                const int32_t pos = t + out_less - both_less;
+                tcol[base + pos] = cb;
+                tw[base + pos] = wb;
+                local_max = fmaxf(local_max, wb);
+            }
+        }
+        if (lane == 0) tcnt[i] = __popc(vmask) + m - __popc(mmask);
     }
     // non-negative floats order like their bit patterns
     for (int o = 16; o > 0; o >>= 1) local_max = fmaxf(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(wmax_bits, __float_as_uint(local_max));
+    if (lane == 0) atomicMax(wmax_bits, __float_as_uint(local_max));
 }
 
 __device__ __forceinline__ uint32_t schedule_word(float w, float w_max) {
@@ -195,18 +245,24 @@ __device__ __forceinline__ uint32_t schedule_word(float w, float w_max) {
 }
 
 // ---------------------------------------------------------------- passes 7, 9
+// Warp per row; the kept entries keep their order.
 __global__ void prune_count_kernel(const int32_t* __restrict__ in_ptr, const float* __restrict__ tw,
                                    const int32_t* __restrict__ tcnt, int64_t n, int k, int T,
                                    const unsigned int* __restrict__ wmax_bits,
                                    int32_t* __restrict__ keep_cnt) {
     const float w_max = __uint_as_float(*wmax_bits);
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += int64_t(gridDim.x) * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t i = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
         const int64_t base = i * k + in_ptr[i];
+        const int32_t cnt = tcnt[i];
         int32_t c = 0;
-        for (int32_t t = 0; t < tcnt[i]; ++t)
-            c += uint64_t(T) * schedule_word(tw[base + t], w_max) >= Q_ONE;
-        keep_cnt[i] = c;
+        for (int32_t t0 = 0; t0 < cnt; t0 += 32) {
+            const int32_t t = t0 + lane;
+            const bool keep = t < cnt && uint64_t(T) * schedule_word(tw[base + t], w_max) >= Q_ONE;
+            c += __popc(__ballot_sync(0xffffffffu, keep));
+        }
+        if (lane == 0) keep_cnt[i] = c;
     }
 }
 
@@ -216,19 +272,31 @@ __global__ void fill_kernel(const int32_t* __restrict__ in_ptr, const int32_t* _
                             const int32_t* __restrict__ row_ptr, int32_t* __restrict__ col,
                             float* __restrict__ w, uint32_t* __restrict__ q) {
     const float w_max = __uint_as_float(*wmax_bits);
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += int64_t(gridDim.x) * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t i = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
         const int64_t base = i * k + in_ptr[i];
+        const int32_t cnt = tcnt[i];
         int64_t o = row_ptr[i];
-        for (int32_t t = 0; t < tcnt[i]; ++t) {
-            const float wt = tw[base + t];
-            const uint32_t qt = schedule_word(wt, w_max);
-            if (uint64_t(T) * qt >= Q_ONE) {
-                col[o] = tcol[base + t];
-                w[o] = wt;
-                q[o] = qt;
-                ++o;
+        for (int32_t t0 = 0; t0 < cnt; t0 += 32) {
+            const int32_t t = t0 + lane;
+            float wt = 0.f;
+            uint32_t qt = 0;
+            bool keep = false;
+            if (t < cnt) {
+                wt = tw[base + t];
+                qt = schedule_word(wt, w_max);
+                keep = uint64_t(T) * qt >= Q_ONE;
             }
+            const unsigned km = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int64_t d = o + __popc(km & lt);
+                col[d] = tcol[base + t];
+                w[d] = wt;
+                q[d] = qt;
+            }
+            o += __popc(km);
         }
     }
 }
@@ -292,15 +360,15 @@ int build_fuzzy_graph(Ctx* c, const int32_t* idx, const float* dist, int64_t n, 
     DRGB_CHECK_LAUNCH(c);
     in_sort_kernel<<<grid_for(n, TB / 32, gmax), TB, 0, st>>>(in_ptr, in_src, in_sorted, n);
     DRGB_CHECK_LAUNCH(c);
-    merge_kernel<<<grid_for(n, TB, gmax), TB, 0, st>>>(out_col, out_w, in_ptr, in_sorted, w_dir, n, k,
-                                                      tcol, tw, tcnt, wmax);
+    merge_kernel<<<grid_for(n, TB / 32, gmax), TB, 0, st>>>(out_col, out_w, in_ptr, in_sorted, w_dir, n, k,
+                                                           tcol, tw, tcnt, wmax);
     DRGB_CHECK_LAUNCH(c);
-    prune_count_kernel<<<grid_for(n, TB, gmax), TB, 0, st>>>(in_ptr, tw, tcnt, n, k, T, wmax, keep_cnt);
+    prune_count_kernel<<<grid_for(n, TB / 32, gmax), TB, 0, st>>>(in_ptr, tw, tcnt, n, k, T, wmax, keep_cnt);
     DRGB_CHECK_LAUNCH(c);
     rc = exclusive_scan(c, keep_cnt, row_ptr, n, scan_tmp, st);
     if (rc) return rc;
-    fill_kernel<<<grid_for(n, TB, gmax), TB, 0, st>>>(in_ptr, tcol, tw, tcnt, n, k, T, wmax, row_ptr,
-                                                     col, w, q);
+    fill_kernel<<<grid_for(n, TB / 32, gmax), TB, 0, st>>>(in_ptr, tcol, tw, tcnt, n, k, T, wmax, row_ptr,
+                                                          col, w, q);
     DRGB_CHECK_LAUNCH(c);
     return DRGB_OK;
 }

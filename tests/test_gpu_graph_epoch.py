@@ -72,6 +72,21 @@ def test_fuzzy_graph_matches_oracle(drgb, n, k, T):
     assert int(rp[-1]) == len(col)
 
 
+def test_fuzzy_reports_a_neighbour_listed_twice(drgb):
+    import torch
+    X, _ = datagen.mixture(300, 50, 5, seed=7)
+    idx, dist = drgb.knn_graph(_t(X, np.float32), 15)
+    bad = idx.clone()
+    bad[3, 1] = bad[3, 0]
+    lib, ctx = drgb._lib.load(), drgb.context(0)
+    stream = torch.cuda.current_stream().cuda_stream
+    assert lib.drgb_sync(ctx, stream) == 0
+    drgb.fuzzy_weights(bad, dist, 200)           # runs; the status word records the error
+    assert lib.drgb_sync(ctx, stream) == drgb._lib.ERR_INVALID
+    drgb.fuzzy_weights(idx, dist, 200)           # well-formed lists: no error, status cleared
+    assert lib.drgb_sync(ctx, stream) == 0
+
+
 def test_fuzzy_row_sums(drgb):
     X, _ = datagen.mixture(3000, 50, 10, seed=3)
     idx, dist, g = _gpu_graph(drgb, X, 15, 200)
