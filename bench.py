@@ -125,9 +125,10 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- traffic record
-def kernel_traffic(kernel: str, source_rel: str):
-    """DRAM bytes per launch recorded from an ncu capture of `kernel`, if the
-    capture was taken from the current source of that kernel; else None."""
+def kernel_traffic(kernel: str, source_rel: str, workload: str):
+    """DRAM bytes per launch recorded from an ncu capture of `kernel` on this
+    workload, if the capture was taken from the current source of that kernel;
+    else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.md")
     src = os.path.join(ROOT, source_rel)
     if not (os.path.exists(path) and os.path.exists(src)):
@@ -135,7 +136,7 @@ def kernel_traffic(kernel: str, source_rel: str):
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
     for ln in open(path):
         cells = [c.strip() for c in ln.strip().strip("|").split("|")]
-        if len(cells) >= 4 and cells[0] == kernel and cells[3] == sha:
+        if len(cells) >= 4 and cells[0] == kernel and cells[1] == workload and cells[3] == sha:
             try:
                 return float(cells[2])
             except ValueError:
@@ -369,7 +370,7 @@ def roofline(args, n, d, nnz, updates, stage_acc, steps, peaks, peak_src, T, til
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": f"hbm_gbs ({peak_src})",
                 "bytes_per_launch": bytes_ep, "launch_ms": per_launch_s * 1e3,
                 "traffic": kernel_traffic("epoch_force_kernel",
-                                          "paper_2603_04035_gb300/csrc/epoch.cu")}
+                                          "paper_2603_04035_gb300/csrc/epoch.cu", args.workload)}
     if gemm_ms > 0:
         # FP16 and BF16 share the tcgen05 kind::f16 rate: the measured BF16 peak
         # applies.  Work = the (128-row block, 256-column tile) products the
@@ -381,7 +382,7 @@ def roofline(args, n, d, nnz, updates, stage_acc, steps, peaks, peak_src, T, til
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": f"bf16_tflops_sustained ({peak_src}); FP16 has the same nominal rate",
                 "flops_per_launch": flops, "launch_ms": gemm_ms, "knn_stage_ms": knn_ms,
-                "traffic": kernel_traffic("knn_tc_kernel", "paper_2603_04035_gb300/csrc/knn_tc.cu")}
+                "traffic": kernel_traffic("knn_tc_kernel", "paper_2603_04035_gb300/csrc/knn_tc.cu", args.workload)}
     flops = 3.0 * n * n * d      # subtract, multiply, add per pair and dimension
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
@@ -391,7 +392,7 @@ def roofline(args, n, d, nnz, updates, stage_acc, steps, peaks, peak_src, T, til
             "peak_source": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
                            f"{mhz:.0f} MHz ({peak_src} clock)",
             "flops_per_launch": flops, "launch_ms": knn_ms,
-            "traffic": kernel_traffic("knn_exact_kernel", "paper_2603_04035_gb300/csrc/knn.cu")}
+            "traffic": kernel_traffic("knn_exact_kernel", "paper_2603_04035_gb300/csrc/knn.cu", args.workload)}
 
 
 # ---------------------------------------------------------------- batched form
