@@ -108,6 +108,23 @@ int drgb_set_tuning(drgb_ctx* ctx, int32_t param, int32_t value);
  * parameter or a NULL pointer. */
 int drgb_get_tuning(const drgb_ctx* ctx, int32_t param, int32_t* value);
 
+/* Tuning cache (host only; no counterpart in the paper, for repeated batched runs):
+ * a JSON file mapping "device name|SM count|rows 2^a|instances 2^b|k c" keys
+ * to tuned settings, one entry per line: {"<key>": {"epoch_warps": 8}, ...}.
+ * drgb_set_tuning_cache makes drgb_fit_transform_batched with
+ * DRGB_FLAG_AUTOTUNE use the file's setting for its key when there is one,
+ * and otherwise time the choices and add the winner to the file (path NULL
+ * or "": no cache).  drgb_tuning_cache_lookup writes the stored force-kernel
+ * width of `key` to *epoch_warps (DRGB_ERR_INVALID if the file or key is
+ * missing or the stored value unsupported); drgb_tuning_cache_store adds or
+ * replaces the entry, rewriting the file through a temporary file and a
+ * rename (DRGB_ERR_INVALID for a bad key or value, or an I/O failure).  Keys
+ * are printable ASCII without quotes or backslashes, shorter than 256 bytes.
+ * Calls that update one file concurrently may lose each other's entries. */
+int drgb_set_tuning_cache(drgb_ctx* ctx, const char* path);
+int drgb_tuning_cache_lookup(const char* path, const char* key, int32_t* epoch_warps);
+int drgb_tuning_cache_store(const char* path, const char* key, int32_t epoch_warps);
+
 /* Stage timing of drgb_fit_transform.  When enabled (on != 0), each fit
  * records CUDA events on its stream between its stages; drgb_stage_times
  * (synchronous: waits for the events) writes up to `max` elapsed times in

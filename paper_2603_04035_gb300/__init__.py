@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import atexit
 import ctypes as C
+import os
 from dataclasses import dataclass
 
 import torch
@@ -33,7 +34,8 @@ from ._lib import MAX_K, Params  # noqa: F401
 __all__ = ["DrgbError", "Graph", "UMAP", "knn_graph", "fuzzy_weights", "find_ab",
            "init_embedding", "embed_epoch", "embed_epochs", "fit_transform", "eval_recall",
            "eval_trust", "default_params", "context", "knn_uncertified", "launch_count",
-           "set_profiling", "stage_times", "set_tuning", "get_tuning", "knn_tiles", "fit_transform_batched",
+           "set_profiling", "stage_times", "set_tuning", "get_tuning", "set_tuning_cache",
+           "tuning_cache_lookup", "tuning_cache_store", "knn_tiles", "fit_transform_batched",
            "autotune_epoch", "mlp_param_count", "mlp_init", "mlp_sample", "mlp_grad", "mlp_train",
            "mlp_embed", "ParametricUMAP", "transform"]
 
@@ -139,6 +141,27 @@ def get_tuning(param: int, device=None) -> int:
     v = C.c_int32(0)
     _check(_lib.load().drgb_get_tuning(ctx, param, C.byref(v)), ctx)
     return int(v.value)
+
+
+def set_tuning_cache(path: str | None, device=None) -> None:
+    """Use (or with None stop using) a JSON tuning cache for the device's
+    context: autotuned batched fits reuse its settings (see include/drgb.h)."""
+    ctx = context(device)
+    _check(_lib.load().drgb_set_tuning_cache(ctx, None if path is None else os.fsencode(path)), ctx)
+
+
+def tuning_cache_lookup(path: str, key: str) -> int | None:
+    """Force-kernel width stored for `key` in the tuning cache, or None."""
+    v = C.c_int32(0)
+    rc = _lib.load().drgb_tuning_cache_lookup(os.fsencode(path), key.encode("ascii"), C.byref(v))
+    return int(v.value) if rc == 0 else None
+
+
+def tuning_cache_store(path: str, key: str, epoch_warps: int) -> None:
+    """Add or replace the entry of `key` in the tuning cache."""
+    rc = _lib.load().drgb_tuning_cache_store(os.fsencode(path), key.encode("ascii"), epoch_warps)
+    if rc != 0:
+        raise DrgbError(rc, f"tuning cache: cannot store {key!r} = {epoch_warps} in {path}")
 
 
 def set_profiling(on: bool, device=None) -> None:

@@ -53,6 +53,9 @@ SIGNATURES = {
     "drgb_launch_count": (C.c_int64, [vp]),
     "drgb_set_tuning": (C.c_int, [vp, i32, i32]),
     "drgb_get_tuning": (C.c_int, [vp, i32, C.POINTER(i32)]),
+    "drgb_set_tuning_cache": (C.c_int, [vp, C.c_char_p]),
+    "drgb_tuning_cache_lookup": (C.c_int, [C.c_char_p, C.c_char_p, C.POINTER(i32)]),
+    "drgb_tuning_cache_store": (C.c_int, [C.c_char_p, C.c_char_p, i32]),
     "drgb_set_profiling": (C.c_int, [vp, C.c_int]),
     "drgb_stage_times": (C.c_int, [vp, C.POINTER(C.c_float), C.c_int]),
     "drgb_knn_graph": (C.c_int, [vp, vp, i64, i32, i32, i32, vp, vp, vp]),

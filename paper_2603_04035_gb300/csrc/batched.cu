@@ -123,12 +123,25 @@ int drgb_fit_transform_batched(drgb_ctx* c, const float* X_cat, const int64_t* o
     float2* Y = reinterpret_cast<float2*>(Y_cat);
     if ((rc = launch_init_batched(c, Y, N, p->init_range, count, d_off, d_seed_init, st))) return rc;
     if (p->flags & DRGB_FLAG_AUTOTUNE) {
-        float us = 0.f;
-        EpochScratch es;
-        if ((rc = epoch_prepare(c, row_ptr, N, 0, int64_t(2 * Nk), count, d_off, ep, &es, st))) return rc;
-        rc = autotune_epoch(c, Y, Y_tune, Y_tmp, row_ptr, col, q, N, a, bb, p->neg, p->n_epochs, 0, 3, st, es, count,
-                            d_off, d_seed_neg, &us);
-        if (rc) return rc;
+        // a setting tuned earlier for this device and problem size, if the
+        // context has a tuning cache that holds one; else time the choices
+        // (and record the winner there)
+        const std::string key = tuning_key(c, N, count, k);
+        int32_t cached = 0;
+        if (!c->tuning_cache.empty() &&
+            drgb_tuning_cache_lookup(c->tuning_cache.c_str(), key.c_str(), &cached) == DRGB_OK) {
+            c->epoch_warps = cached;
+        } else {
+            float us = 0.f;
+            EpochScratch es;
+            if ((rc = epoch_prepare(c, row_ptr, N, 0, int64_t(2 * Nk), count, d_off, ep, &es, st))) return rc;
+            rc = autotune_epoch(c, Y, Y_tune, Y_tmp, row_ptr, col, q, N, a, bb, p->neg, p->n_epochs, 0, 3, st, es,
+                                count, d_off, d_seed_neg, &us);
+            if (rc) return rc;
+            if (!c->tuning_cache.empty() &&
+                drgb_tuning_cache_store(c->tuning_cache.c_str(), key.c_str(), c->epoch_warps) != DRGB_OK)
+                return set_error(c, DRGB_ERR_INVALID, "tuning cache %s could not be written", c->tuning_cache.c_str());
+        }
     }
     if ((rc = stage_mark(c, 3, st))) return rc;
     rc = run_epochs(c, Y, Y_tmp, row_ptr, col, q, N, a, bb, p->lr0, p->neg, 0, p->n_epochs, p->n_epochs, 0, st,

@@ -26,6 +26,8 @@ struct Ctx {
     int64_t launches = 0;         // kernels launched (host-side count)
     int epoch_warps = 8;          // warps per CTA of the epoch force kernel (tuning)
     int knn_tile_n = 256;         // database tile width of the tensor-core k-NN (tuning)
+    std::string device_name;      // for tuning-cache keys
+    std::string tuning_cache;     // JSON file of tuned settings ("" = none)
     bool profiling = false;       // record stage events in fit_transform
     cudaEvent_t stage_ev[8] = {};
     int stage_marks = 0;
@@ -35,6 +37,13 @@ struct Ctx {
 
 // Record stage boundary `idx` on `st` when profiling is enabled.
 int stage_mark(Ctx* c, int idx, cudaStream_t st);
+
+// Force-kernel widths (warps per CTA) the epoch kernel supports.
+bool epoch_warps_supported(int warps);
+
+// Tuning-cache key of a problem on this context's device: device name, SM
+// count, and the powers of two below the row and instance counts, and k.
+std::string tuning_key(const Ctx* c, int64_t rows, int64_t instances, int k);
 
 // Record a formatted error message in the context; returns `code`.
 int set_error(Ctx* c, int code, const char* fmt, ...);

@@ -1,7 +1,10 @@
 // Context management, error plumbing, device-wide scan and the host a,b fit.
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <string>
 
 #include "common.cuh"
 
@@ -145,6 +148,86 @@ int exclusive_scan(Ctx* c, const int32_t* in, int32_t* out, int64_t n, int32_t* 
     return scan_rec(c, in, out, n, tmp, st);
 }
 
+// ------------------------------------------------------------------ tuning cache
+// The file is a JSON object with one entry per line, written by this library:
+//   {
+//     "<key>": {"epoch_warps": 8},
+//     ...
+//   }
+// Keys are printable ASCII without quotes or backslashes.  Reading accepts
+// exactly the lines of that form and ignores every other line.
+
+bool cache_key_ok(const char* k) {
+    if (!k || !*k) return false;
+    size_t n = 0;
+    for (const char* p = k; *p; ++p, ++n) {
+        const unsigned char ch = static_cast<unsigned char>(*p);
+        if (ch < 0x20 || ch > 0x7e || ch == '"' || ch == '\\') return false;
+    }
+    return n < 256;
+}
+
+std::map<std::string, int> cache_read(const char* path) {
+    std::map<std::string, int> m;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return m;
+    char line[1024];
+    while (std::fgets(line, sizeof(line), f)) {
+        const char* p = std::strchr(line, '"');
+        if (!p) continue;
+        const char* q = std::strchr(p + 1, '"');
+        if (!q) continue;
+        const std::string key(p + 1, q);
+        const char* v = std::strstr(q + 1, "\"epoch_warps\":");
+        if (!v || !cache_key_ok(key.c_str())) continue;
+        char* end = nullptr;
+        const long w = std::strtol(v + std::strlen("\"epoch_warps\":"), &end, 10);
+        if (end == v || w < 1 || w > 1024) continue;
+        m[key] = int(w);
+    }
+    std::fclose(f);
+    return m;
+}
+
+bool cache_write(const char* path, const std::map<std::string, int>& m) {
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "w");
+    if (!f) return false;
+    bool ok = std::fputs("{\n", f) >= 0;
+    size_t i = 0;
+    for (const auto& kv : m) {
+        ok = ok && std::fprintf(f, "  \"%s\": {\"epoch_warps\": %d}%s\n", kv.first.c_str(), kv.second,
+                                ++i < m.size() ? "," : "") > 0;
+    }
+    ok = ok && std::fputs("}\n", f) >= 0;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok || std::rename(tmp.c_str(), path) != 0) {
+        std::remove(tmp.c_str());
+        return false;
+    }
+    return true;
+}
+
+std::string tuning_key(const Ctx* c, int64_t rows, int64_t instances, int k) {
+    auto lg = [](int64_t v) {
+        int e = 0;
+        while (v > 1) {
+            v >>= 1;
+            ++e;
+        }
+        return e;
+    };
+    char buf[384];
+    std::snprintf(buf, sizeof(buf), "%s|%d SMs|rows 2^%d|instances 2^%d|k %d", c->device_name.c_str(), c->num_sms,
+                  lg(rows), lg(instances), k);
+    std::string s = buf;
+    for (char& ch : s)
+        if (ch == '"' || ch == '\\' || static_cast<unsigned char>(ch) < 0x20 || static_cast<unsigned char>(ch) > 0x7e)
+            ch = '_';
+    return s;
+}
+
+
 }  // namespace drgb
 
 using namespace drgb;
@@ -171,6 +254,7 @@ int drgb_ctx_create(int device, drgb_ctx** out) {
     c->device = device;
     c->num_sms = prop.multiProcessorCount;
     c->l2_bytes = size_t(prop.l2CacheSize);
+    c->device_name = prop.name;
     if (cudaMalloc(&c->d_status, 256) != cudaSuccess) {
         delete c;
         cudaSetDevice(prev);
@@ -216,6 +300,29 @@ int drgb_set_tuning(drgb_ctx* c, int32_t param, int32_t value) {
         default:
             return set_error(c, DRGB_ERR_INVALID, "unknown tuning parameter %d", param);
     }
+}
+
+int drgb_tuning_cache_lookup(const char* path, const char* key, int32_t* epoch_warps) {
+    if (!path || !*path || !drgb::cache_key_ok(key) || !epoch_warps) return DRGB_ERR_INVALID;
+    const auto m = drgb::cache_read(path);
+    const auto it = m.find(key);
+    if (it == m.end() || !drgb::epoch_warps_supported(it->second)) return DRGB_ERR_INVALID;
+    *epoch_warps = it->second;
+    return DRGB_OK;
+}
+
+int drgb_tuning_cache_store(const char* path, const char* key, int32_t epoch_warps) {
+    if (!path || !*path || !drgb::cache_key_ok(key) || !drgb::epoch_warps_supported(epoch_warps))
+        return DRGB_ERR_INVALID;
+    auto m = drgb::cache_read(path);
+    m[key] = epoch_warps;
+    return drgb::cache_write(path, m) ? DRGB_OK : DRGB_ERR_INVALID;
+}
+
+int drgb_set_tuning_cache(drgb_ctx* c, const char* path) {
+    if (!c) return DRGB_ERR_INVALID;
+    c->tuning_cache = path ? path : "";
+    return DRGB_OK;
 }
 
 int drgb_get_tuning(const drgb_ctx* c, int32_t param, int32_t* value) {

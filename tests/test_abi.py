@@ -98,3 +98,51 @@ def test_product_path_does_not_import_the_oracle():
             text = open(path).read()
             assert "oracle" not in re.sub(r"#.*|//.*", "", text).replace("oracle.", ""), path
             assert "import oracle" not in text and "from oracle" not in text, path
+
+
+def test_tuning_cache_round_trip(lib, tmp_path):
+    import json
+    from paper_2603_04035_gb300 import _lib
+    path = str(tmp_path / "tune.json").encode()
+    v = C.c_int32(0)
+    key = b"NVIDIA GB300|152 SMs|rows 2^21|instances 2^8|k 15"
+    assert lib.drgb_tuning_cache_lookup(path, key, C.byref(v)) == _lib.ERR_INVALID   # no file yet
+    assert lib.drgb_tuning_cache_store(path, key, 8) == 0
+    assert lib.drgb_tuning_cache_store(path, b"other|1", 4) == 0
+    assert lib.drgb_tuning_cache_lookup(path, key, C.byref(v)) == 0 and v.value == 8
+    assert lib.drgb_tuning_cache_store(path, key, 4) == 0                              # replaced
+    assert lib.drgb_tuning_cache_lookup(path, key, C.byref(v)) == 0 and v.value == 4
+    with open(path) as f:
+        assert json.load(f) == {key.decode(): {"epoch_warps": 4}, "other|1": {"epoch_warps": 4}}
+    assert lib.drgb_tuning_cache_lookup(path, b"missing", C.byref(v)) == _lib.ERR_INVALID
+
+
+def test_tuning_cache_rejects_bad_keys_values_and_paths(lib, tmp_path):
+    from paper_2603_04035_gb300 import _lib
+    path = str(tmp_path / "tune.json").encode()
+    for bad in (b"", b'a"b', b"a\\b", b"tab\there", b"x" * 256):
+        assert lib.drgb_tuning_cache_store(path, bad, 8) == _lib.ERR_INVALID, bad
+    for warps in (0, 5, 16):
+        assert lib.drgb_tuning_cache_store(path, b"k", warps) == _lib.ERR_INVALID, warps
+    assert not os.path.exists(path)
+    assert lib.drgb_tuning_cache_store(str(tmp_path / "no" / "dir.json").encode(), b"k", 8) == _lib.ERR_INVALID
+    assert lib.drgb_set_tuning_cache(None, path) == _lib.ERR_INVALID
+
+
+def test_tuning_cache_reads_only_its_own_lines(lib, tmp_path):
+    from paper_2603_04035_gb300 import _lib
+    p = tmp_path / "tune.json"
+    p.write_text('{\n  garbage line\n  "a": {"epoch_warps": 6},\n  "b": {"epoch_warps": 4}\n}\n')
+    v = C.c_int32(0)
+    assert lib.drgb_tuning_cache_lookup(str(p).encode(), b"b", C.byref(v)) == 0 and v.value == 4
+    assert lib.drgb_tuning_cache_lookup(str(p).encode(), b"a", C.byref(v)) == _lib.ERR_INVALID  # unsupported
+
+
+def test_tuning_cache_python_wrappers(lib, tmp_path):
+    import paper_2603_04035_gb300 as drgb
+    path = str(tmp_path / "t.json")
+    assert drgb.tuning_cache_lookup(path, "k") is None
+    drgb.tuning_cache_store(path, "k", 8)
+    assert drgb.tuning_cache_lookup(path, "k") == 8
+    with pytest.raises(drgb.DrgbError):
+        drgb.tuning_cache_store(path, "k", 3)

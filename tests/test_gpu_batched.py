@@ -85,3 +85,29 @@ def test_fit_is_deterministic_from_a_fresh_context(drgb):
     Y2 = drgb.fit_transform(Xd, n_epochs=60)
     Y3 = drgb.fit_transform(Xd, n_epochs=60)
     assert torch.equal(Y1, Y2) and torch.equal(Y2, Y3)
+
+
+def test_autotune_uses_and_fills_the_tuning_cache(drgb, tmp_path):
+    import json
+    import torch
+    from paper_2603_04035_gb300 import _lib
+    sizes = [1500, 3000, 800, 2500]
+    X, off = _instances(sizes, seed=9)
+    Xd = torch.from_numpy(X).cuda()
+    path = str(tmp_path / "tune.json")
+    drgb.set_tuning_cache(path)
+    try:
+        Y0 = drgb.fit_transform_batched(Xd, off, autotune=True, n_epochs=60).cpu()   # times and records
+        with open(path) as f:
+            entries = json.load(f)
+        assert len(entries) == 1
+        key, val = next(iter(entries.items()))
+        assert key.endswith(f"|rows 2^{int(np.log2(sum(sizes)))}|instances 2^2|k 15")
+        assert val["epoch_warps"] == drgb.get_tuning(_lib.TUNE_EPOCH_WARPS)
+        other = 4 if val["epoch_warps"] == 8 else 8
+        drgb.tuning_cache_store(path, key, other)
+        Y1 = drgb.fit_transform_batched(Xd, off, autotune=True, n_epochs=60).cpu()   # takes the stored width
+        assert drgb.get_tuning(_lib.TUNE_EPOCH_WARPS) == other
+        assert torch.equal(Y0, Y1)
+    finally:
+        drgb.set_tuning_cache(None)
