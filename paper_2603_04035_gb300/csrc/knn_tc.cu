@@ -14,8 +14,10 @@
 // FP16 (S scales max |x - mean| to 2^10, C = 2^15), whose 11-bit significand
 // leaves an 8x smaller rounding residual at the same tensor-core rate.
 //
-// GEMM + select (A2): one CTA owns 128 query rows (TMEM lanes) and streams all
-// database tiles of 256 rows.  Warp 0 issues TMA loads into a 4-stage ring,
+// GEMM + select (A2): one CTA owns 128 query rows (TMEM lanes) and streams the
+// database tiles of 256 rows that its cell schedule admits (points are staged
+// in the spatial cell order of knn_order.cu; see knn_tc_kernel for the cell
+// bounds).  Warp 0 issues TMA loads into a 4-stage ring,
 // warp 1 issues 4 MMAs (M128 N256 K16) per tile into one of two TMEM
 // accumulators, and 8 epilogue warps (two per TMEM lane quarter, one per
 // column half) read the accumulator with tcgen05.ld, reject a 32-column chunk
@@ -26,9 +28,12 @@
 // of the 32 candidates (the same arithmetic as the FP32 scan), top-k by
 // (distance, index).  With delta_i = |x_i - x~_i| (BF16 rounding residual)
 // and eps_i bounding the FP32 accumulation error, every point outside the
-// list is at distance >= sqrt(n_i + s_thr - eps_i) - delta_i - delta_max.
-// If that bound exceeds the k-th exact distance the row is certified; other
-// rows are recomputed by the exact FP32 scan.
+// list is at distance >= sqrt(n_i + s_thr - eps_i) - delta_i - delta_max if
+// its tile was multiplied or its cell skipped (a skipped cell lies beyond the
+// row's upper bound, which is at least that), and beyond lbstop, the bound at
+// which the schedule stopped, otherwise.  If the smaller of the two exceeds
+// the k-th exact distance the row is certified; other rows are recomputed by
+// the exact FP32 scan.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
