@@ -234,6 +234,21 @@ def config(args, n):
 
 
 # ---------------------------------------------------------------- our arm
+def aggregate_over_ranks(total_ms, e2e_total_ms, units, device, world):
+    """Whole-job figures of a weak-scaling run: every rank embeds its own
+    instance, so the timed regions take the maximum over ranks and the units
+    (edge updates per fit) the sum.  Returns (total_ms, e2e_total_ms,
+    units of all ranks)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms, e2e_total_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), float(u[0])
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -315,12 +330,9 @@ def run_ours(args):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_total = float(sum(e2e_ms))
 
-    t = torch.tensor([total_ms, e2e_total], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms, e2e_total = float(t[0]), float(t[1])
-    value = world * updates * args.steps / (total_ms / 1e3)
-    e2e_value = world * updates * len(e2e_ms) / (e2e_total / 1e3)
+    total_ms, e2e_total, updates_all = aggregate_over_ranks(total_ms, e2e_total, updates, dev, world)
+    value = updates_all * args.steps / (total_ms / 1e3)
+    e2e_value = updates_all * len(e2e_ms) / (e2e_total / 1e3)
 
     if rank == 0:
         peaks, peak_src = load_peaks()
@@ -331,6 +343,7 @@ def run_ours(args):
                 "config": config(args, n),
                 "s_per_embed": total_ms / args.steps / 1e3,
                 "edge_updates_per_fit": updates,
+                "edge_updates_per_step_all_ranks": updates_all,
                 "stage_ms_per_step": {kk: v / args.steps for kk, v in stage_acc.items()},
                 "knn_tiles": {"multiplied": tiles_done, "full_scan": tiles_full,
                               "fraction": tiles_done / tiles_full if tiles_full else None},
