@@ -25,7 +25,6 @@ struct Ctx {
     int64_t knn_tiles_total = 0;              // tile products of a full scan (last tensor-core k-NN)
     int64_t launches = 0;         // kernels launched (host-side count)
     int epoch_warps = 8;          // warps per CTA of the epoch force kernel (tuning)
-    int knn_tile_n = 256;         // database tile width of the tensor-core k-NN (tuning)
     std::string device_name;      // for tuning-cache keys
     std::string tuning_cache;     // JSON file of tuned settings ("" = none)
     bool profiling = false;       // record stage events in fit_transform

@@ -233,11 +233,6 @@ __global__ void merge_partials_kernel(const int32_t* __restrict__ pidx, const fl
     }
 }
 
-size_t knn_rows_scratch_bytes(int64_t max_rows, int k, int num_sms) {
-    (void)num_sms;
-    return 2 * Carve::round(size_t(max_rows) * 64 * k * 4) + 1024;
-}
-
 int launch_knn_exact_rows(Ctx* c, const float* X, int64_t n, int d, int k, const int32_t* rows32,
                           const int32_t* n_rows_dev, int64_t max_rows, int32_t* idx_out,
                           float* dist_out, cudaStream_t st, void* part_scratch, size_t part_bytes) {

@@ -21,7 +21,6 @@ int launch_knn_exact(Ctx* c, const float* X, int64_t n, int d, int k, const int6
 int launch_knn_exact_rows(Ctx* c, const float* X, int64_t n, int d, int k, const int32_t* rows32,
                           const int32_t* n_rows_dev, int64_t max_rows, int32_t* idx_out,
                           float* dist_out, cudaStream_t st, void* part_scratch, size_t part_bytes);
-size_t knn_rows_scratch_bytes(int64_t max_rows, int k, int num_sms);
 // Exact FP32 k-NN of the nq rows of Q among the n rows of X (no self exclusion).
 int launch_knn_query(Ctx* c, const float* Q, int64_t nq, const float* X, int64_t n, int d, int k,
                      int32_t* idx_out, float* dist_out, cudaStream_t st);
