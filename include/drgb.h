@@ -4,7 +4,7 @@
  * The library computes the data-parallel hot path of the UMAP method as used
  * by mlx-vis (arXiv 2603.04035): the exact k-NN graph (Section 2.2), the
  * fuzzy simplicial-set graph and the a, b kernel fit (Section 2.3), and the
- * synchronous negative-sampling SGD epoch (Section 2.5, "UMAP's SGD step";
+ * synchronous negative-sampling SGD epoch (Section 2.5, the UMAP optimiser step;
  * Section 4.1, scatter-add updates on sampled edges), composed into
  * fit_transform(X) -> n x 2 (Section 2.1, public API).
  *
@@ -48,8 +48,8 @@ extern "C" {
 
 typedef struct drgb_ctx drgb_ctx;
 
-/* Hyper-parameters of fit_transform (Section 2.1: "instantiate with
- * hyperparameters"; defaults follow UMAP as used in Section 3). */
+/* Hyper-parameters of fit_transform (Section 2.1: a method object is created
+ * with its hyper-parameters; defaults follow UMAP as used in Section 3). */
 typedef struct drgb_params {
     int32_t k;            /* neighbours per point (default 15), 1..DRGB_MAX_K */
     int32_t n_epochs;     /* T, number of SGD epochs (Section 3: 500 for UMAP) */
@@ -136,9 +136,9 @@ int drgb_stage_times(drgb_ctx* ctx, float* ms, int max);
 
 /* ------------------------------------------------------------- k-NN graph */
 
-/* Exact k-nearest-neighbour graph (Section 2.2: "k-nearest neighbor search is
- * the first stage of every method"; the paper uses approximate NNDescent, this
- * library returns the exact graph).
+/* Exact k-nearest-neighbour graph (Section 2.2: every method starts from a
+ * k-NN search, approximate NNDescent in the paper; this library returns the
+ * exact graph).
  *   X        n x d FP32, row-major (4-byte aligned).
  *   idx_out  n x k int32: the k nearest OTHER points of each row (self
  *            excluded), ordered by FP32 squared distance sum_c (x_ic - x_jc)^2
@@ -169,8 +169,8 @@ int drgb_knn_tiles(drgb_ctx* ctx, int64_t* done, int64_t* total, void* stream);
 
 /* -------------------------------------------------------- fuzzy weights */
 
-/* Fuzzy simplicial-set graph of a k-NN graph (Section 3: UMAP's
- * "fuzzy-simplicial-set graph"; construction of UMAP, cited in Section 1):
+/* Fuzzy simplicial-set graph of a k-NN graph (Section 3, the graph UMAP
+ * builds; the construction is UMAP's, cited in Section 1):
  *   rho_i   = dist[i][0];
  *   sigma_i : sum_j exp(-max(0, dist[i][j] - rho_i) / sigma_i) = log2 k, by 64
  *             bisection steps (start 1, double until bracketed, then halve),
@@ -222,8 +222,8 @@ int drgb_fuzzy_weights_static(const int32_t* idx, const float* dist, int64_t n, 
 
 /* Host, synchronous.  Least-squares fit of Phi(x) = 1 / (1 + a x^(2b)) to
  * psi(x) = 1 (x < min_dist), exp(-(x - min_dist) / spread) otherwise, on 300
- * points in [0, 3 spread], by Gauss-Newton (Section 2.3: "UMAP fits its output
- * kernel parameters via Gauss-Newton optimization").  FP64 internally.
+ * points in [0, 3 spread], by Gauss-Newton (Section 2.3 fits UMAP's output
+ * kernel parameters this way).  FP64 internally.
  * Errors: DRGB_ERR_INVALID (NULL outputs, spread <= 0, min_dist < 0). */
 int drgb_find_ab(float spread, float min_dist, float* a, float* b);
 
@@ -237,8 +237,8 @@ int drgb_init_embedding(drgb_ctx* ctx, int64_t n, float init_range, uint64_t see
 
 /* ---------------------------------------------------------- SGD epoch */
 
-/* One synchronous SGD epoch t over a head-sorted CSR (Section 2.5, "UMAP's
- * SGD step"; Section 4.1, scatter-add on randomly sampled edges).  For every
+/* One synchronous SGD epoch t over a head-sorted CSR (Section 2.5, the UMAP
+ * optimiser step; Section 4.1, scatter-add on randomly sampled edges).  For every
  * row i and entry e = (i, j) active at t, i.e.
  *   floor((t+1) q_e / 2^24) > floor(t q_e / 2^24):
  *   d = |Y_i - Y_j|^2;  g_i += clip4(-2ab d^(b-1) / (1 + a d^b) (Y_i - Y_j)),
@@ -396,7 +396,7 @@ int drgb_default_params(drgb_params* p);
 
 /* -------------------------------------------------------- evaluation */
 
-/* k-NN preservation ("kNN-P", Section 3.2): mean over the query rows of
+/* k-NN preservation (kNN-P, Section 3.2): mean over the query rows of
  * |N_X(i) & N_Y(i)| / k, with exact neighbour sets in X (n x d, FP32 direct
  * distances) and in Y (n x 2).  Query rows: all rows if n_query <= 0 or
  * n_query >= n, else the evenly strided rows i_r = floor(r n / n_query),

@@ -22,7 +22,7 @@ below follows the published UMAP construction, in plain NumPy/SciPy, in FP64:
 * ``sgd``            uniform initialisation, the synchronous SGD epoch
                      (attraction along active edges, repulsion from negative
                      samples, clip to +-4) and the full fit (Section 3,
-                     "500 epochs"; Section 3.2 "UMAP optimization loop").
+                     500 epochs; Section 3.2, the optimisation loop).
 * ``metrics``        k-NN preservation and trustworthiness (Section 3.2).
 * ``mlp``            FP64 forward/backward of the learned 50-256-256-2 embedder
                      with BF16 rounding emulated where the CUDA path rounds.

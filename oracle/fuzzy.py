@@ -1,8 +1,8 @@
 """Fuzzy simplicial-set graph of the k-NN graph (oracle side).
 
-The paper times UMAP's "fuzzy-simplicial-set graph" (Section 3, the MLX vs
-PyTorch/MPS study) and cites UMAP (McInnes et al. 2018) for it without
-printing the construction.  The construction followed here, in FP64:
+The paper times the construction of UMAP's fuzzy simplicial-set graph
+(Section 3, the MLX vs PyTorch/MPS study) and cites UMAP (McInnes et al. 2018)
+for it without printing the construction.  The construction followed here, in FP64:
 
 1. rho_i = distance from i to its nearest neighbour.
 2. sigma_i solves  sum_{j in kNN(i)} exp(-max(0, d_ij - rho_i) / sigma) = log2 k

@@ -1,6 +1,6 @@
 """Initialisation, synchronous SGD epoch and full fit (oracle side, FP64).
 
-The paper's UMAP optimiser (Section 2.5 "UMAP's SGD step"; Section 3, 500
+The paper's UMAP optimiser (Section 2.5, its SGD step; Section 3, 500
 epochs, negative-sample rate, gradient expression; Section 4.1, scatter-add on
 sampled edges) follows UMAP.  Its per-epoch step, as restated here:
 
