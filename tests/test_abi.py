@@ -146,3 +146,14 @@ def test_tuning_cache_python_wrappers(lib, tmp_path):
     assert drgb.tuning_cache_lookup(path, "k") == 8
     with pytest.raises(drgb.DrgbError):
         drgb.tuning_cache_store(path, "k", 3)
+
+
+def test_params_aliases_and_umap_defaults(lib):
+    import paper_2603_04035_gb300 as drgb
+    p = drgb._params(n_neighbors=10, negative_sample_rate=7, learning_rate=0.5, n_epochs=300)
+    assert (p.k, p.neg, p.n_epochs) == (10, 7, 300) and abs(p.lr0 - 0.5) < 1e-7
+    with pytest.raises(TypeError):
+        drgb._params(no_such_parameter=1)
+    u = drgb.UMAP(n_neighbors=12, seed=4, min_dist=0.25)
+    assert u.params["k"] == 12 and u.params["min_dist"] == 0.25
+    assert (u.params["seed_init"], u.params["seed_neg"]) == (5, 6)   # data seed s: init s+1, negatives s+2
