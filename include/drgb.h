@@ -101,8 +101,13 @@ int64_t drgb_launch_count(const drgb_ctx* ctx);
 
 /* Tuning knobs (performance only; results do not depend on them):
  *   DRGB_TUNE_EPOCH_WARPS     warps per CTA of the epoch's force kernel: 4 or 8
+ *   DRGB_TUNE_EPOCH_PIPE      form of the epoch's force kernel: 1 (default)
+ *                             pipelined (a warp keeps two groups of gathers in
+ *                             flight, 24 warps per SM), 0 flat (one group, 40
+ *                             warps per SM)
  * Returns DRGB_ERR_INVALID for an unknown parameter or value. */
 #define DRGB_TUNE_EPOCH_WARPS 1
+#define DRGB_TUNE_EPOCH_PIPE 2
 int drgb_set_tuning(drgb_ctx* ctx, int32_t param, int32_t value);
 /* Current value of a tuning knob in *value.  DRGB_ERR_INVALID for an unknown
  * parameter or a NULL pointer. */

@@ -20,6 +20,7 @@ ERR_DEVICE = -6
 MAX_K = 32
 STATIC_SCRATCH_BYTES = 16 << 20
 TUNE_EPOCH_WARPS = 1
+TUNE_EPOCH_PIPE = 2
 FLAG_AUTOTUNE = 1
 
 ERROR_NAMES = {ERR_INVALID: "invalid argument", ERR_WORKSPACE: "workspace too small",

@@ -18,6 +18,7 @@ struct Ctx {
     int device = 0;
     int num_sms = 0;
     size_t l2_bytes = 0;
+    size_t smem_per_sm = 0;       // shared memory an SM can give CTAs (bytes)
     void* scratch = nullptr;      // grown on demand, 256-byte aligned carve-outs
     size_t scratch_bytes = 0;
     int* d_status = nullptr;      // device status word (0 = ok, else DRGB_ERR_*)
@@ -25,6 +26,7 @@ struct Ctx {
     int64_t knn_tiles_total = 0;              // tile products of a full scan (last tensor-core k-NN)
     int64_t launches = 0;         // kernels launched (host-side count)
     int epoch_warps = 8;          // warps per CTA of the epoch force kernel (tuning)
+    int epoch_pipe = 1;           // epoch force kernel form: 1 pipelined, 0 flat (tuning)
     std::string device_name;      // for tuning-cache keys
     std::string tuning_cache;     // JSON file of tuned settings ("" = none)
     bool profiling = false;       // record stage events in fit_transform

@@ -254,6 +254,7 @@ int drgb_ctx_create(int device, drgb_ctx** out) {
     c->device = device;
     c->num_sms = prop.multiProcessorCount;
     c->l2_bytes = size_t(prop.l2CacheSize);
+    c->smem_per_sm = size_t(prop.sharedMemPerMultiprocessor);
     c->device_name = prop.name;
     if (cudaMalloc(&c->d_status, 256) != cudaSuccess) {
         delete c;
@@ -297,6 +298,11 @@ int drgb_set_tuning(drgb_ctx* c, int32_t param, int32_t value) {
                 return set_error(c, DRGB_ERR_INVALID, "epoch force-kernel width must be 4 or 8 warps");
             c->epoch_warps = value;
             return DRGB_OK;
+        case DRGB_TUNE_EPOCH_PIPE:
+            if (value != 0 && value != 1)
+                return set_error(c, DRGB_ERR_INVALID, "epoch kernel form must be 0 (flat) or 1 (pipelined)");
+            c->epoch_pipe = value;
+            return DRGB_OK;
         default:
             return set_error(c, DRGB_ERR_INVALID, "unknown tuning parameter %d", param);
     }
@@ -329,6 +335,7 @@ int drgb_get_tuning(const drgb_ctx* c, int32_t param, int32_t* value) {
     if (!c || !value) return DRGB_ERR_INVALID;
     switch (param) {
         case DRGB_TUNE_EPOCH_WARPS: *value = c->epoch_warps; return DRGB_OK;
+        case DRGB_TUNE_EPOCH_PIPE: *value = c->epoch_pipe; return DRGB_OK;
         default: return DRGB_ERR_INVALID;
     }
 }

@@ -24,6 +24,8 @@
 //                adds the partial d lanes to the left)
 //   force      = 0 + (((group sum_0) + group sum_1) + ...) over the groups that
 //                hold the head, in order
+#include <type_traits>
+
 #include "common.cuh"
 #include "epoch.cuh"
 
@@ -74,6 +76,10 @@ __device__ __forceinline__ float hw_lg2(float x) {
 __device__ __forceinline__ float pow_pos(float d, float b) { return hw_ex2(b * hw_lg2(d)); }
 
 static constexpr unsigned FULL = 0xffffffffu;
+
+// Gather of one point of Y^(t).  (Read-only-path and L1 evict-last loads
+// were measured and made no difference.)
+__device__ __forceinline__ float2 load_y(const float2* p) { return *p; }
 
 // Instance-local view of a row: rows [off, off + n) with entries from eoff on,
 // negatives drawn under Philox key (k0, k1).  A single instance has off = 0,
@@ -131,8 +137,8 @@ __device__ __forceinline__ void fetch_entry(const EpochArgs& A, const RowInst& R
     in.e = e;
     in.i = ok ? i : -1 - lane;
     const int32_t ii = ok ? i : int32_t(h_lo);
-    in.yi = A.Y_in[ii];
-    in.yj = A.Y_in[ok ? j : ii];
+    in.yi = load_y(A.Y_in + ii);
+    in.yj = load_y(A.Y_in + (ok ? j : ii));
     const uint32_t n32 = R.n, i32 = uint32_t(ii - R.off), e32 = uint32_t(e - R.eoff);
     const float2* Yb = A.Y_in + R.off;
     U4 r0{0u, 0u, 0u, 0u}, r1{0u, 0u, 0u, 0u};
@@ -143,7 +149,7 @@ __device__ __forceinline__ void fetch_entry(const EpochArgs& A, const RowInst& R
     for (int w = 0; w < NP; ++w) {
         const uint32_t m = __umulhi(u[w], n32);  // floor(u n / 2^32)
         const bool take = ok && (NEG >= 0 || w < neg) && (m != i32);
-        in.ym[w] = Yb[take ? m : i32];           // a skipped negative reads Y_i
+        in.ym[w] = load_y(Yb + (take ? m : i32));  // a skipped negative reads Y_i
     }
 }
 
@@ -183,7 +189,7 @@ __device__ __forceinline__ float2 entry_math(const EpochArgs& A, const RowInst& 
             for (int w = 0; w < 4; ++w) {
                 const uint32_t m = __umulhi(v[w], n32);
                 const bool ok = (g * 4 + w < neg) && (m != i32);
-                yg[w] = ok ? Yb[m] : yi;
+                yg[w] = ok ? load_y(Yb + m) : yi;
             }
 #pragma unroll
             for (int w = 0; w < 4; ++w) repel(yg[w]);
@@ -310,23 +316,50 @@ int epoch_prepare(Ctx* c, const int32_t* rp, int64_t n, int64_t row_begin, int64
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// Active entries of one compaction piece waiting in shared memory: at most 31
-// left over from the previous piece plus one piece of EPOCH_WIN entries.
-static constexpr int EPOCH_QCAP = EPOCH_WIN + 32;
+// CSR chunks (of 32 entries) a warp loads at once before testing them.  The
+// window's CSR words are streamed in bursts so that several loads are in
+// flight per lane; the active entries of a burst wait in a per-warp queue of
+// at most 31 + 32 * EPOCH_BURST entries.  The queue is kept this small on
+// purpose: shared memory left unused goes to the L1 cache, and the random
+// 8-byte gathers of Y run at about 2.5x the rate with the largest L1 (the
+// misses in flight per SM are bounded by L1 capacity).
+static constexpr int EPOCH_BURST = 4;
+static constexpr int EPOCH_QCAP = 32 * EPOCH_BURST + 32;
+// Warps per SM each form's register budget is sized for: the pipelined form
+// holds two groups' gathered points (about 80 registers a thread), the flat
+// form one (about 48).
+static constexpr int epoch_warps_per_sm(bool pipe) { return pipe ? 24 : 40; }
 
 // One warp per window (grid-stride over windows).  No row crosses a window, so
 // the warp writes the final Y' of every row of its window.
-template <bool BATCHED, int NEG>
-__global__ void __launch_bounds__(256, 3) epoch_force_kernel(const __grid_constant__ EpochArgs A) {
-    // [warps][EPOCH_QCAP] (entry, tail) and [warps][EPOCH_QCAP] head of the waiting active entries
-    extern __shared__ int2 s_active[];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    int2* act_w = s_active + w * EPOCH_QCAP;
-    int32_t* head_w = reinterpret_cast<int32_t*>(s_active + nw * EPOCH_QCAP) + w * EPOCH_QCAP;
+//
+// The warp streams the window's CSR in bursts of EPOCH_BURST chunks of 32
+// entries (one entry per lane and chunk, coalesced) and appends each burst's
+// active entries to its queue, in entry order.  Every 32 waiting entries form
+// a group: one entry per lane, its negatives drawn and its points gathered
+// (fetch), then its force computed and the group's terms added by head
+// (segmented scan, carry between groups).  The window's last group may be
+// partial.
+//
+// PIPE: the gathers of a group are issued before the previous group's forces
+// are computed, so one warp keeps two groups' loads in flight (for grids with
+// few windows per SM); the next burst's CSR loads are issued before the held
+// group is finished.  Without PIPE each group is finished before the next is
+// fetched, and latency is hidden by more warps per SM (for grids with many
+// windows).  Both forms form the same groups and add in the same order, so
+// they give the same bits.
+template <bool BATCHED, int NEG, int NW, bool PIPE>
+__global__ void __launch_bounds__(NW * 32, epoch_warps_per_sm(PIPE) / NW)
+    epoch_force_kernel(const __grid_constant__ EpochArgs A) {
+    __shared__ int2 s_ej[NW][EPOCH_QCAP];     // (entry, tail) of the waiting active entries
+    __shared__ int32_t s_hd[NW][EPOCH_QCAP];  // their heads
     // carry of each warp: running sum of the previous group's last head and
     // that head's position; the head itself (-1 when none)
-    __shared__ float4 s_carry[8];
-    __shared__ int32_t s_chead[8];
+    __shared__ float4 s_carry[NW];
+    __shared__ int32_t s_chead[NW];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int2* act_w = s_ej[w];
+    int32_t* head_w = s_hd[w];
     const unsigned lt_mask = (1u << lane) - 1u;
     const float two_ab = 2.0f * A.a * A.b, two_b = 2.0f * A.b;
     grid_dep_launch();
@@ -352,7 +385,7 @@ __global__ void __launch_bounds__(256, 3) epoch_force_kernel(const __grid_consta
         return;
     }
     const RowInst R1{0, A.neg_n ? A.neg_n : uint32_t(A.n), 0, A.k0, A.k1};
-    for (int32_t W = int32_t(blockIdx.x) * nw + w; W < n_win; W += int32_t(gridDim.x) * nw) {
+    for (int32_t W = int32_t(blockIdx.x) * NW + w; W < n_win; W += int32_t(gridDim.x) * NW) {
         const int32_t rA = A.win_row[W], rB = A.win_row[W + 1];
         if (rA >= rB) continue;  // a long row started in an earlier window covers this one
         RowInst R = R1;
@@ -376,120 +409,119 @@ __global__ void __launch_bounds__(256, 3) epoch_force_kernel(const __grid_consta
             continue;
         }
         const int32_t es = A.row_ptr[rA - A.row_begin], ee = A.row_ptr[rB - A.row_begin];
-        // every row of the window first gets Y + lr * 0 (after the first
-        // piece is compacted); rows with active entries are rewritten with
-        // their force below
-        auto start_rows = [&]() {
-            grid_dep_wait();
-            for (int64_t r = rA + lane; r < rB; r += 32) {
-                const float2 y = A.Y_in[r];
-                A.Y_out[r] = make_float2(fmaf(A.lr, 0.f, y.x), fmaf(A.lr, 0.f, y.y));
+        // Negatives and gathers of `cnt` waiting entries from queue position p.
+        auto fetch_group = [&](int p, int cnt, EntryInputs<NEG>& in) {
+            const bool v = lane < cnt;
+            const int2 ej = v ? act_w[p + lane] : make_int2(es, 0);
+            fetch_entry<NEG, BATCHED>(A, R, v, ej.x, ej.y, v ? head_w[p + lane] : -1, h_lo, h_hi, lane, in);
+        };
+        // Forces of a fetched group of `cnt` entries, added by head.
+        auto finish_group = [&](const EntryInputs<NEG>& cur, int cnt) {
+            float fx = 0.f, fy = 0.f;
+            if (cur.ok) {
+                const float2 f = entry_math<NEG, BATCHED>(A, R, cur, two_ab, two_b);
+                fx = f.x;
+                fy = f.y;
             }
-            // s_carry / s_chead carry the running sum of the previous group's
-            // last head; a row is written when its last group has been added
-            if (lane == 0) s_chead[w] = -1;
+            const int32_t i = cur.i;
+            const int32_t chead = s_chead[w];
+            // the carried head ends unless this group starts with it
+            if (chead >= 0 && lane == 0 && i != chead) {
+                const float4 cv = s_carry[w];
+                A.Y_out[chead] = make_float2(fmaf(A.lr, 0.f + cv.x, cv.z), fmaf(A.lr, 0.f + cv.y, cv.w));
+            }
+            // segmented inclusive scan over runs of equal heads
+            const int32_t i_prev = __shfl_up_sync(FULL, i, 1);
+            const unsigned starts = __ballot_sync(FULL, lane == 0 || i_prev != i);
+            const int seg0 = 31 - __clz(starts & (FULL >> (31 - lane)));
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const float ox = __shfl_up_sync(FULL, fx, d), oy = __shfl_up_sync(FULL, fy, d);
+                if (lane - d >= seg0) {
+                    fx = ox + fx;
+                    fy = oy + fy;
+                }
+            }
+            if (seg0 == 0 && i == chead) {
+                const float4 cv = s_carry[w];
+                fx = cv.x + fx;
+                fy = cv.y + fy;
+            }
+            // a run that ends inside the group is the row's last: write it;
+            // the group's last run is carried
+            const int32_t i_next = __shfl_down_sync(FULL, i, 1);
+            if (cur.ok && lane < cnt - 1 && i_next != i)
+                A.Y_out[i] = make_float2(fmaf(A.lr, 0.f + fx, cur.yi.x), fmaf(A.lr, 0.f + fy, cur.yi.y));
+            __syncwarp();
+            if (lane == cnt - 1) {
+                s_carry[w] = make_float4(fx, fy, cur.yi.x, cur.yi.y);
+                s_chead[w] = cur.ok ? i : -1;
+            }
             __syncwarp();
         };
-        int qn = 0;  // active entries waiting at the front of the buffer
-        // (a window whose rows are all empty still takes one, empty, piece)
-        for (int32_t p0 = es; p0 == es || p0 < ee; p0 += EPOCH_WIN) {
-            const int32_t pe = min(p0 + EPOCH_WIN, ee);
-            // compaction, in entry order: the piece's q, col and heads are
-            // loaded LD chunks of 32 at a time (coalesced), then tested
-            constexpr int LD = 8;
+        EntryInputs<NEG> held;  // PIPE: the fetched group waiting for its forces
+        int held_cnt = 0;
+        int qn = 0;             // active entries waiting at the front of the queue
+        // (a window whose rows are all empty still takes one, empty, burst)
+        for (int32_t c0 = es; c0 == es || c0 < ee; c0 += 32 * EPOCH_BURST) {
+            // the burst's CSR words, all loads in flight before any test; q =
+            // 0 never fires.  The CSR streams through once per epoch:
+            // evict-first loads keep L2 for the gathered positions Y.
+            uint32_t qv[EPOCH_BURST];
+            int32_t jv[EPOCH_BURST], hv[EPOCH_BURST];
 #pragma unroll
-            for (int s0 = 0; s0 < EPOCH_WIN / 32; s0 += LD) {
-                uint32_t qv[LD];
-                int32_t jv[LD], hv[LD];
+            for (int b = 0; b < EPOCH_BURST; ++b) {
+                const int32_t e = c0 + 32 * b + lane;
+                const bool in = e < ee;
+                qv[b] = in ? __ldcs(A.q + e) : 0u;
+                jv[b] = in ? __ldcs(A.col + e) : 0;
+                hv[b] = in ? __ldcs(A.row_of + e) : -1;
+            }
+            if (PIPE && held_cnt) {  // the previous burst's last group, while the loads fly
+                finish_group(held, held_cnt);
+                held_cnt = 0;
+            }
 #pragma unroll
-                for (int s = 0; s < LD; ++s) {
-                    const int32_t e = p0 + 32 * (s0 + s) + lane;
-                    const bool in = e < pe;
-                    // the CSR streams through once per epoch: evict-first
-                    // loads keep L2 for the gathered positions Y
-                    qv[s] = in ? __ldcs(A.q + e) : 0u;  // q = 0 never fires
-                    jv[s] = in ? __ldcs(A.col + e) : 0;
-                    hv[s] = in ? __ldcs(A.row_of + e) : -1;
+            for (int b = 0; b < EPOCH_BURST; ++b) {
+                // floor((t+1) q / 2^24) > floor(t q / 2^24)  <=>  (t q mod 2^24) + q >= 2^24
+                const bool act = qv[b] >= 0x1000000u - ((A.t * qv[b]) & 0xFFFFFFu);
+                const unsigned m = __ballot_sync(FULL, act);
+                if (act) {
+                    const int pos = qn + __popc(m & lt_mask);
+                    act_w[pos] = make_int2(c0 + 32 * b + lane, jv[b]);
+                    head_w[pos] = hv[b];
                 }
-#pragma unroll
-                for (int s = 0; s < LD; ++s) {
-                    // floor((t+1) q / 2^24) > floor(t q / 2^24)  <=>  (t q mod 2^24) + q >= 2^24
-                    const bool act = qv[s] >= 0x1000000u - ((A.t * qv[s]) & 0xFFFFFFu);
-                    const unsigned m = __ballot_sync(FULL, act);
-                    if (act) {
-                        const int pos = qn + __popc(m & lt_mask);
-                        act_w[pos] = make_int2(p0 + 32 * (s0 + s) + lane, jv[s]);
-                        head_w[pos] = hv[s];
-                    }
-                    qn += __popc(m);
-                }
+                qn += __popc(m);
             }
             __syncwarp();
-            if (p0 == es) start_rows();
-            // groups of 32 active entries (the last, partial group waits for
-            // the next piece unless this is the window's last piece),
-            // software-pipelined: the next group's negatives are drawn and its
-            // points gathered before this group's forces are computed
-            const int ng = pe == ee ? (qn + 31) / 32 : qn / 32;
-            EntryInputs<NEG> cur, nxt;
-            if (ng > 0) {
-                const bool v = lane < qn;
-                const int2 ej = v ? act_w[lane] : make_int2(p0, 0);
-                fetch_entry<NEG, BATCHED>(A, R, v, ej.x, ej.y, v ? head_w[lane] : -1, h_lo, h_hi, lane, cur);
+            if (c0 == es) {
+                // every row of the window first gets Y + lr * 0; rows with
+                // active entries are rewritten with their force below.  The
+                // wait for the previous epoch comes here, after the first
+                // burst has been loaded and tested.
+                grid_dep_wait();
+                for (int64_t r = rA + lane; r < rB; r += 32) {
+                    const float2 y = A.Y_in[r];
+                    A.Y_out[r] = make_float2(fmaf(A.lr, 0.f, y.x), fmaf(A.lr, 0.f, y.y));
+                }
+                if (lane == 0) s_chead[w] = -1;
+                __syncwarp();
             }
+            const bool last = c0 + 32 * EPOCH_BURST >= ee;
+            const int ng = last ? (qn + 31) / 32 : qn / 32;
             for (int g = 0; g < ng; ++g) {
-                const int g0 = 32 * g;
-                const int cnt = qn - g0 < 32 ? qn - g0 : 32;
-                if (g + 1 < ng) {
-                    const bool v = g0 + 32 + lane < qn;
-                    const int2 ej = v ? act_w[g0 + 32 + lane] : make_int2(p0, 0);
-                    fetch_entry<NEG, BATCHED>(A, R, v, ej.x, ej.y, v ? head_w[g0 + 32 + lane] : -1, h_lo, h_hi,
-                                              lane, nxt);
+                const int cnt = qn - 32 * g < 32 ? qn - 32 * g : 32;
+                EntryInputs<NEG> in;
+                fetch_group(32 * g, cnt, in);
+                if (PIPE) {
+                    if (held_cnt) finish_group(held, held_cnt);
+                    held = in;
+                    held_cnt = cnt;
+                } else {
+                    finish_group(in, cnt);
                 }
-                float fx = 0.f, fy = 0.f;
-                if (cur.ok) {
-                    const float2 f = entry_math<NEG, BATCHED>(A, R, cur, two_ab, two_b);
-                    fx = f.x;
-                    fy = f.y;
-                }
-                const int32_t i = cur.i;
-                const int32_t chead = s_chead[w];
-                // the carried head ends unless this group starts with it
-                if (chead >= 0 && lane == 0 && i != chead) {
-                    const float4 cv = s_carry[w];
-                    A.Y_out[chead] = make_float2(fmaf(A.lr, 0.f + cv.x, cv.z), fmaf(A.lr, 0.f + cv.y, cv.w));
-                }
-                // segmented inclusive scan over runs of equal heads
-                const int32_t i_prev = __shfl_up_sync(FULL, i, 1);
-                const unsigned starts = __ballot_sync(FULL, lane == 0 || i_prev != i);
-                const int seg0 = 31 - __clz(starts & (FULL >> (31 - lane)));
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const float ox = __shfl_up_sync(FULL, fx, d), oy = __shfl_up_sync(FULL, fy, d);
-                    if (lane - d >= seg0) {
-                        fx = ox + fx;
-                        fy = oy + fy;
-                    }
-                }
-                if (seg0 == 0 && i == chead) {
-                    const float4 cv = s_carry[w];
-                    fx = cv.x + fx;
-                    fy = cv.y + fy;
-                }
-                // a run that ends inside the group is the row's last: write
-                // it; the group's last run is carried
-                const int32_t i_next = __shfl_down_sync(FULL, i, 1);
-                if (cur.ok && lane < cnt - 1 && i_next != i)
-                    A.Y_out[i] = make_float2(fmaf(A.lr, 0.f + fx, cur.yi.x), fmaf(A.lr, 0.f + fy, cur.yi.y));
-                __syncwarp();
-                if (lane == cnt - 1) {
-                    s_carry[w] = make_float4(fx, fy, cur.yi.x, cur.yi.y);
-                    s_chead[w] = cur.ok ? i : -1;
-                }
-                __syncwarp();
-                cur = nxt;
             }
-            // move the waiting partial group to the front of the buffer
+            // move the waiting partial group to the front
             const int left = qn - 32 * ng > 0 ? qn - 32 * ng : 0;
             int2 lv = make_int2(0, 0);
             int32_t lh = -1;
@@ -505,6 +537,7 @@ __global__ void __launch_bounds__(256, 3) epoch_force_kernel(const __grid_consta
             qn = left;
             __syncwarp();
         }
+        if (PIPE && held_cnt) finish_group(held, held_cnt);
         if (lane == 0 && s_chead[w] >= 0) {
             const float4 cv = s_carry[w];
             A.Y_out[s_chead[w]] = make_float2(fmaf(A.lr, 0.f + cv.x, cv.z), fmaf(A.lr, 0.f + cv.y, cv.w));
@@ -522,16 +555,24 @@ int launch_epoch(Ctx* c, const EpochArgs& A_in, int warps, cudaStream_t st, bool
     if (!A_in.row_of || !A_in.win_row) return set_error(c, DRGB_ERR_INVALID, "epoch: state not prepared");
     EpochArgs A = A_in;
     philox_round_keys(A.k0, A.k1, A.rk);
-    const int threads = warps * 32;
-    const size_t smem = size_t(warps) * EPOCH_QCAP * (sizeof(int2) + sizeof(int32_t));
-    const int fgrid = grid_for(A.win_cap, warps, c->num_sms * (24 / warps));
     const bool bat = A.count > 0, n5 = A.neg == 5;
+    const bool pipe = c->epoch_pipe != 0;
+    const int per_sm = epoch_warps_per_sm(pipe) / warps;
+    const int fgrid = grid_for(A.win_cap, warps, c->num_sms * per_sm);
     auto go = [&](auto kernel) -> int {
-        DRGB_CUDA(c, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        // Ask for no more shared memory than the resident CTAs hold (their
+        // queues plus the 1 KB the hardware reserves per CTA); the rest of the
+        // SM's 256 KB stays L1 cache for the gathers of Y.
+        cudaFuncAttributes fa;
+        DRGB_CUDA(c, cudaFuncGetAttributes(&fa, kernel));
+        const size_t need = size_t(per_sm) * (fa.sharedSizeBytes + 1024);
+        int pct = int((need * 100 + c->smem_per_sm - 1) / (c->smem_per_sm ? c->smem_per_sm : 1));
+        pct = pct < 1 ? 1 : (pct > 100 ? 100 : pct);
+        DRGB_CUDA(c, cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(fgrid);
-        cfg.blockDim = dim3(threads);
-        cfg.dynamicSmemBytes = smem;
+        cfg.blockDim = dim3(warps * 32);
+        cfg.dynamicSmemBytes = 0;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -541,8 +582,17 @@ int launch_epoch(Ctx* c, const EpochArgs& A_in, int warps, cudaStream_t st, bool
         DRGB_CUDA(c, cudaLaunchKernelEx(&cfg, kernel, A));
         return DRGB_OK;
     };
-    int rc = bat ? (n5 ? go(epoch_force_kernel<true, 5>) : go(epoch_force_kernel<true, -1>))
-                 : (n5 ? go(epoch_force_kernel<false, 5>) : go(epoch_force_kernel<false, -1>));
+    auto pick = [&](auto nw, auto pp) -> int {
+        constexpr int NW = decltype(nw)::value;
+        constexpr bool P = decltype(pp)::value;
+        return bat ? (n5 ? go(epoch_force_kernel<true, 5, NW, P>) : go(epoch_force_kernel<true, -1, NW, P>))
+                   : (n5 ? go(epoch_force_kernel<false, 5, NW, P>) : go(epoch_force_kernel<false, -1, NW, P>));
+    };
+    using I4 = std::integral_constant<int, 4>;
+    using I8 = std::integral_constant<int, 8>;
+    using PT = std::true_type;
+    using PF = std::false_type;
+    int rc = warps == 4 ? (pipe ? pick(I4{}, PT{}) : pick(I4{}, PF{})) : (pipe ? pick(I8{}, PT{}) : pick(I8{}, PF{}));
     if (rc) return rc;
     DRGB_CHECK_LAUNCH(c);
     return DRGB_OK;

@@ -254,20 +254,24 @@ def test_epoch_every_tuning_choice_is_bit_identical(drgb, graph):
     g = _graph_tensors(drgb, rp, col, q)
     Y = np.random.default_rng(5).uniform(-10, 10, size=(n, 2)).astype(np.float32)
     Yd = _t(Y)
-    saved = drgb.get_tuning(_lib.TUNE_EPOCH_WARPS)
+    saved = drgb.get_tuning(_lib.TUNE_EPOCH_WARPS), drgb.get_tuning(_lib.TUNE_EPOCH_PIPE)
     outs = {}
     try:
-        for warps in (4, 8):
-            drgb.set_tuning(_lib.TUNE_EPOCH_WARPS, warps)
-            for neg in (5, 6):   # the fixed-count and the generic force paths
-                outs[(warps, neg)] = drgb.embed_epoch(Yd, g, 1.577, 0.895, 0.7, neg, 13, 4).clone()
+        for pipe in (0, 1):   # flat and pipelined forms
+            drgb.set_tuning(_lib.TUNE_EPOCH_PIPE, pipe)
+            for warps in (4, 8):
+                drgb.set_tuning(_lib.TUNE_EPOCH_WARPS, warps)
+                for neg in (5, 6):   # the fixed-count and the generic force paths
+                    outs[(pipe, warps, neg)] = drgb.embed_epoch(Yd, g, 1.577, 0.895, 0.7, neg, 13, 4).clone()
         torch.cuda.synchronize()
     finally:
-        drgb.set_tuning(_lib.TUNE_EPOCH_WARPS, saved)
+        drgb.set_tuning(_lib.TUNE_EPOCH_WARPS, saved[0])
+        drgb.set_tuning(_lib.TUNE_EPOCH_PIPE, saved[1])
     for neg in (5, 6):
-        assert torch.equal(outs[(4, neg)], outs[(8, neg)]), neg
+        for key in ((0, 4, neg), (0, 8, neg), (1, 8, neg)):
+            assert torch.equal(outs[(1, 4, neg)], outs[key]), key
         ref = osgd.epoch(Y, rp, col, q.astype(np.uint64), 1.577, 0.895, 0.7, neg, 13, 4)
-        assert np.all(np.abs(_np(outs[(4, neg)]) - ref) <= epoch_tolerance(ref))
+        assert np.all(np.abs(_np(outs[(1, 4, neg)]) - ref) <= epoch_tolerance(ref))
 
 
 def test_set_tuning_rejects_unsupported_values(drgb):
@@ -275,5 +279,8 @@ def test_set_tuning_rejects_unsupported_values(drgb):
     for bad in (0, 2, 16, 32):
         with pytest.raises(drgb.DrgbError):
             drgb.set_tuning(_lib.TUNE_EPOCH_WARPS, bad)
+    for bad in (-1, 2):
+        with pytest.raises(drgb.DrgbError):
+            drgb.set_tuning(_lib.TUNE_EPOCH_PIPE, bad)
     with pytest.raises(drgb.DrgbError):
         drgb.set_tuning(99, 4)

@@ -24,20 +24,30 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
-def _static_graph(lib, idx, dist, n_epochs):
+def _outputs(n, k, dev):
+    import torch
+    cap = 2 * n * k
+    return (torch.empty(n + 1, dtype=torch.int32, device=dev), torch.empty(cap, dtype=torch.int32, device=dev),
+            torch.empty(cap, dtype=torch.float32, device=dev), torch.empty(cap, dtype=torch.int32, device=dev),
+            torch.empty(n, dtype=torch.float32, device=dev), torch.empty(n, dtype=torch.float32, device=dev))
+
+
+def _call_static(lib, idx, dist, n_epochs, outs):
     import torch
     n, k = idx.shape
-    cap = 2 * n * k
-    dev = idx.device
-    row_ptr = torch.empty(n + 1, dtype=torch.int32, device=dev)
-    col = torch.empty(cap, dtype=torch.int32, device=dev)
-    w = torch.empty(cap, dtype=torch.float32, device=dev)
-    q = torch.empty(cap, dtype=torch.int32, device=dev)
-    stream = C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
-    rc = lib.drgb_fuzzy_weights_static(_ptr(idx), _ptr(dist), n, k, n_epochs, _ptr(row_ptr), _ptr(col),
-                                       _ptr(w), _ptr(q), cap, None, None, stream)
+    row_ptr, col, w, q, rho, sigma = outs
+    stream = C.c_void_p(torch.cuda.current_stream(idx.device).cuda_stream)
+    return lib.drgb_fuzzy_weights_static(_ptr(idx), _ptr(dist), n, k, n_epochs, _ptr(row_ptr), _ptr(col),
+                                         _ptr(w), _ptr(q), col.numel(), _ptr(rho), _ptr(sigma), stream)
+
+
+def _static_graph(lib, idx, dist, n_epochs):
+    n, k = idx.shape
+    outs = _outputs(n, k, idx.device)
+    rc = _call_static(lib, idx, dist, n_epochs, outs)
+    row_ptr, col, w, q, rho, sigma = outs
     nnz = int(row_ptr[n].item()) if rc == 0 else 0
-    return rc, row_ptr, col[:nnz], w[:nnz], q[:nnz]
+    return rc, row_ptr, col[:nnz], w[:nnz], q[:nnz], rho, sigma
 
 
 def test_static_entry_point_matches_context_entry_point():
@@ -50,13 +60,38 @@ def test_static_entry_point_matches_context_entry_point():
     for n, seed, T in [(2000, 0, 200), (3500, 1, 500), (2000, 0, 200)]:
         X, _ = datagen.mixture(n, 50, 10, seed=seed)
         idx, dist = drgb.knn_graph(torch.from_numpy(X).cuda(), 15)
-        ref = drgb.fuzzy_weights(idx, dist, T)
-        rc, rp, col, w, q = _static_graph(lib, idx, dist, T)
+        ref = drgb.fuzzy_weights(idx, dist, T, with_rho_sigma=True)
+        rc, rp, col, w, q, rho, sigma = _static_graph(lib, idx, dist, T)
         assert rc == 0
+        # both entry points run the same kernels on the same inputs: the
+        # graph is the same bit for bit
         assert torch.equal(rp, ref.row_ptr)
         assert torch.equal(col, ref.col)
         assert torch.equal(q, ref.q)
-        np.testing.assert_allclose(w.cpu().numpy(), ref.w.cpu().numpy(), rtol=0, atol=1e-5)
+        assert torch.equal(w, ref.w)
+        assert torch.equal(rho, ref.rho)
+        assert torch.equal(sigma, ref.sigma)
+
+
+def test_static_entry_point_allocates_no_device_memory():
+    import torch
+    drgb = drgb_module()
+    from paper_2603_04035_gb300 import _lib
+    lib = _lib.load()
+    X, _ = datagen.mixture(25_000, 50, 10, seed=3)
+    idx, dist = drgb.knn_graph(torch.from_numpy(X).cuda(), 15)
+    X2, _ = datagen.mixture(2000, 50, 10, seed=4)
+    small = drgb.knn_graph(torch.from_numpy(X2).cuda(), 15)
+    assert _call_static(lib, *small, 200, _outputs(2000, 15, idx.device)) == 0   # set-up call
+    outs = _outputs(25_000, 15, idx.device)          # every output exists before the measurement
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    assert _call_static(lib, idx, dist, 200, outs) == 0
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    # its scratch (about 14 MB at this size) lives in the library's fixed array
+    assert free0 - free1 < (2 << 20), (free0, free1)
+    assert int(outs[0][25_000].item()) > 0
 
 
 def test_static_entry_point_refuses_oversized_input():
