@@ -115,20 +115,22 @@ int drgb_get_tuning(const drgb_ctx* ctx, int32_t param, int32_t* value);
 
 /* Tuning cache (host only; no counterpart in the paper, for repeated batched runs):
  * a JSON file mapping "device name|SM count|rows 2^a|instances 2^b|k c" keys
- * to tuned settings, one entry per line: {"<key>": {"epoch_warps": 8}, ...}.
+ * to tuned settings, one entry per line:
+ * {"<key>": {"epoch_warps": 8, "epoch_pipe": 1}, ...}.
  * drgb_set_tuning_cache makes drgb_fit_transform_batched with
  * DRGB_FLAG_AUTOTUNE use the file's setting for its key when there is one,
  * and otherwise time the choices and add the winner to the file (path NULL
  * or "": no cache).  drgb_tuning_cache_lookup writes the stored force-kernel
- * width of `key` to *epoch_warps (DRGB_ERR_INVALID if the file or key is
- * missing or the stored value unsupported); drgb_tuning_cache_store adds or
+ * width and form of `key` to *epoch_warps and *epoch_pipe (an entry without
+ * "epoch_pipe" reads as the default form 1; DRGB_ERR_INVALID if the file or
+ * key is missing or a stored value unsupported); drgb_tuning_cache_store adds or
  * replaces the entry, rewriting the file through a temporary file and a
  * rename (DRGB_ERR_INVALID for a bad key or value, or an I/O failure).  Keys
  * are printable ASCII without quotes or backslashes, shorter than 256 bytes.
  * Calls that update one file concurrently may lose each other's entries. */
 int drgb_set_tuning_cache(drgb_ctx* ctx, const char* path);
-int drgb_tuning_cache_lookup(const char* path, const char* key, int32_t* epoch_warps);
-int drgb_tuning_cache_store(const char* path, const char* key, int32_t epoch_warps);
+int drgb_tuning_cache_lookup(const char* path, const char* key, int32_t* epoch_warps, int32_t* epoch_pipe);
+int drgb_tuning_cache_store(const char* path, const char* key, int32_t epoch_warps, int32_t epoch_pipe);
 
 /* Stage timing of drgb_fit_transform.  When enabled (on != 0), each fit
  * records CUDA events on its stream between its stages; drgb_stage_times
@@ -309,12 +311,12 @@ int drgb_fit_transform_batched(drgb_ctx* ctx, const float* X_cat, const int64_t*
                                const uint64_t* seeds_init, const uint64_t* seeds_neg, float* Y_cat,
                                void* stream);
 
-/* Epoch autotuner: times every supported force-kernel width (warps per CTA)
- * for `trials` epochs of the given graph on a scratch copy of Y (n x 2,
- * device; not modified), keeps the fastest in the context (see
- * drgb_set_tuning) and returns it in choice[0] (choice[1], choice[2] are set
- * to 0) with its time per epoch.  Every choice gives bit-identical results.
- * Synchronous. */
+/* Epoch autotuner: times every supported force-kernel setting (width 4 or 8
+ * warps per CTA x form pipelined or flat, see drgb_set_tuning) for `trials`
+ * epochs of the given graph on a scratch copy of Y (n x 2, device; not
+ * modified), keeps the fastest in the context and returns it in choice[0]
+ * (width) and choice[1] (form; choice[2] is set to 0) with its time per
+ * epoch.  Every choice gives bit-identical results.  Synchronous. */
 int drgb_autotune_epoch(drgb_ctx* ctx, const float* Y, const int32_t* row_ptr, const int32_t* col,
                         const uint32_t* q, int64_t n, float a, float b, int32_t neg, int32_t n_epochs,
                         uint64_t seed, int32_t trials, int32_t* choice, float* us_per_epoch,
@@ -415,6 +417,23 @@ int drgb_eval_recall(drgb_ctx* ctx, const float* X, const float* Y, int64_t n, i
  * exact FP32 ranks.  Synchronous. */
 int drgb_eval_trust(drgb_ctx* ctx, const float* X, const float* Y, int64_t n, int32_t d,
                     int32_t k, int64_t n_query, double* out, void* stream);
+
+/* Held-out k-NN preservation, for embeddings of new points (the paper
+ * evaluates training points only; this carries its kNN-P measure of Section
+ * 3.2 over to points outside the training set): mean over the query new
+ * points p of |N_X(p) & N_Y(p)| / k, where N_X(p) are the k nearest of the n
+ * training points X_train (n x d) to X_new[p], and N_Y(p) the k nearest of
+ * the training embedding Y_train (n x 2) to Y_new[p] (n_new x 2): for the
+ * plain transform Y_train is the fitted embedding, for the learned embedder
+ * its own image of the training set.  Exact FP32 scans, ties by index.
+ * Query points: all if n_query <= 0 or n_query >= n_new, else the evenly
+ * strided p_r = floor(r n_new / n_query).  Device pointers, caller-owned;
+ * X rows 4-byte and Y rows 8-byte aligned.  Errors: DRGB_ERR_INVALID (NULL,
+ * misaligned, k outside [1, DRGB_MAX_K], n < k, n_new < 1, d < 1).
+ * Synchronous; *out receives the value. */
+int drgb_eval_recall_heldout(drgb_ctx* ctx, const float* X_train, const float* Y_train, int64_t n,
+                             const float* X_new, const float* Y_new, int64_t n_new, int32_t d,
+                             int32_t k, int64_t n_query, double* out, void* stream);
 
 #ifdef __cplusplus
 }

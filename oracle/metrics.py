@@ -10,13 +10,20 @@ trustworthiness (Venna & Kaski 2006), computed from exact distances.
   self excluded, ties by index) of j among i's neighbours in X, and m the
   number of rows summed (m = n for the full metric; a seeded row sample
   otherwise).
+* held-out recall (for embeddings of new points, which the paper does not
+  evaluate; the k-NN-preservation measure above carried over to points
+  outside the training set): for a new point p with 2-D position y_p,
+  |N_X(p) & N_Y(p)| / k, where N_X(p) are the k nearest training points to
+  x_p in the input space and N_Y(p) the k nearest training points to y_p in
+  the method's own 2-D embedding of the training set; averaged over the
+  evenly strided new points i_r = floor(r n_new / m).
 """
 from __future__ import annotations
 
 import numpy as np
 from scipy.spatial import cKDTree
 
-from .knn import knn_rows
+from .knn import knn_query, knn_rows
 
 
 def knn_2d(Y: np.ndarray, k: int, rows=None, brute_max: int = 4096):
@@ -85,3 +92,20 @@ def quality(X, Y, k: int = 15, rows=None, knn_x=None):
     nx = knn_rows(X, rows, k)[0] if knn_x is None else knn_x
     ny = knn_2d(Y, k, rows)
     return recall(nx, ny), trustworthiness(X, ny, rows)
+
+
+def strided_rows(n: int, m: int) -> np.ndarray:
+    """The m evenly strided rows floor(r n / m), r = 0 .. m-1 (all rows when
+    m <= 0 or m >= n)."""
+    if m <= 0 or m >= n:
+        return np.arange(n)
+    return (np.arange(m, dtype=np.int64) * n) // m
+
+
+def heldout_recall(X_train, Y_train, X_new, Y_new, k: int = 15, n_query: int = 0) -> float:
+    """Held-out k-NN preservation of new points against the training set
+    (module docstring): exact neighbour sets in both spaces, ties by index."""
+    rows = strided_rows(len(X_new), n_query)
+    nx = knn_query(np.asarray(X_new)[rows], X_train, k)[0]
+    ny = knn_query(np.asarray(Y_new)[rows], Y_train, k)[0]
+    return recall(nx, ny)

@@ -33,7 +33,7 @@ from ._lib import MAX_K, Params  # noqa: F401
 
 __all__ = ["DrgbError", "Graph", "UMAP", "knn_graph", "fuzzy_weights", "find_ab",
            "init_embedding", "embed_epoch", "embed_epochs", "fit_transform", "eval_recall",
-           "eval_trust", "default_params", "context", "knn_uncertified", "launch_count",
+           "eval_trust", "eval_recall_heldout", "default_params", "context", "knn_uncertified", "launch_count",
            "set_profiling", "stage_times", "set_tuning", "get_tuning", "set_tuning_cache",
            "tuning_cache_lookup", "tuning_cache_store", "knn_tiles", "fit_transform_batched",
            "autotune_epoch", "mlp_param_count", "mlp_init", "mlp_sample", "mlp_grad", "mlp_train",
@@ -150,18 +150,18 @@ def set_tuning_cache(path: str | None, device=None) -> None:
     _check(_lib.load().drgb_set_tuning_cache(ctx, None if path is None else os.fsencode(path)), ctx)
 
 
-def tuning_cache_lookup(path: str, key: str) -> int | None:
-    """Force-kernel width stored for `key` in the tuning cache, or None."""
-    v = C.c_int32(0)
-    rc = _lib.load().drgb_tuning_cache_lookup(os.fsencode(path), key.encode("ascii"), C.byref(v))
-    return int(v.value) if rc == 0 else None
+def tuning_cache_lookup(path: str, key: str) -> tuple[int, int] | None:
+    """(force-kernel width, form) stored for `key` in the tuning cache, or None."""
+    v, p = C.c_int32(0), C.c_int32(0)
+    rc = _lib.load().drgb_tuning_cache_lookup(os.fsencode(path), key.encode("ascii"), C.byref(v), C.byref(p))
+    return (int(v.value), int(p.value)) if rc == 0 else None
 
 
-def tuning_cache_store(path: str, key: str, epoch_warps: int) -> None:
+def tuning_cache_store(path: str, key: str, epoch_warps: int, epoch_pipe: int = 1) -> None:
     """Add or replace the entry of `key` in the tuning cache."""
-    rc = _lib.load().drgb_tuning_cache_store(os.fsencode(path), key.encode("ascii"), epoch_warps)
+    rc = _lib.load().drgb_tuning_cache_store(os.fsencode(path), key.encode("ascii"), epoch_warps, epoch_pipe)
     if rc != 0:
-        raise DrgbError(rc, f"tuning cache: cannot store {key!r} = {epoch_warps} in {path}")
+        raise DrgbError(rc, f"tuning cache: cannot store {key!r} = ({epoch_warps}, {epoch_pipe}) in {path}")
 
 
 def set_profiling(on: bool, device=None) -> None:
@@ -335,15 +335,15 @@ def fit_transform_batched(X_cat: torch.Tensor, offsets, seeds_init=None, seeds_n
 
 def autotune_epoch(Y: torch.Tensor, g: Graph, a: float, b: float, neg: int = 5, n_epochs: int = 200,
                    seed: int = 2, trials: int = 3):
-    """Time the epoch force-kernel widths on this graph; keeps and returns the
-    fastest (warps per CTA, microseconds per epoch)."""
+    """Time the epoch force-kernel settings on this graph; keeps and returns
+    the fastest ((warps per CTA, form), microseconds per epoch)."""
     Y = _cuda(Y, torch.float32, "Y", 2)
     choice = (C.c_int32 * 3)()
     us = C.c_float()
     ctx = context(Y.device.index)
     _check(_lib.load().drgb_autotune_epoch(ctx, _ptr(Y), *_graph_args(g), Y.shape[0], a, b, neg, n_epochs, seed,
                                            trials, choice, C.byref(us), _stream(Y.device)), ctx)
-    return int(choice[0]), us.value
+    return (int(choice[0]), int(choice[1])), us.value
 
 
 # ---------------------------------------------------------------- learned embedder
@@ -463,6 +463,24 @@ def eval_trust(X: torch.Tensor, Y: torch.Tensor, k: int = 15, n_query: int = 0) 
     ctx = context(X.device.index)
     _check(_lib.load().drgb_eval_trust(ctx, _ptr(X), _ptr(Y), X.shape[0], X.shape[1], k, n_query,
                                        C.byref(out), _stream(X.device)), ctx)
+    return out.value
+
+
+def eval_recall_heldout(X_train: torch.Tensor, Y_train: torch.Tensor, X_new: torch.Tensor, Y_new: torch.Tensor,
+                        k: int = 15, n_query: int = 0) -> float:
+    """Held-out k-NN preservation of new points against the training set."""
+    Xt = _cuda(X_train, torch.float32, "X_train", 2)
+    Yt = _cuda(Y_train, torch.float32, "Y_train", 2)
+    Xn = _cuda(X_new, torch.float32, "X_new", 2)
+    Yn = _cuda(Y_new, torch.float32, "Y_new", 2)
+    if Xt.shape[1] != Xn.shape[1] or Yt.shape[1] != 2 or Yn.shape[1] != 2 or Yt.shape[0] != Xt.shape[0] \
+            or Yn.shape[0] != Xn.shape[0]:
+        raise ValueError("eval_recall_heldout: shape mismatch")
+    out = C.c_double()
+    ctx = context(Xt.device.index)
+    _check(_lib.load().drgb_eval_recall_heldout(ctx, _ptr(Xt), _ptr(Yt), Xt.shape[0], _ptr(Xn), _ptr(Yn),
+                                                Xn.shape[0], Xt.shape[1], k, n_query, C.byref(out),
+                                                _stream(Xt.device)), ctx)
     return out.value
 
 

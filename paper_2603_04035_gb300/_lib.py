@@ -55,8 +55,8 @@ SIGNATURES = {
     "drgb_set_tuning": (C.c_int, [vp, i32, i32]),
     "drgb_get_tuning": (C.c_int, [vp, i32, C.POINTER(i32)]),
     "drgb_set_tuning_cache": (C.c_int, [vp, C.c_char_p]),
-    "drgb_tuning_cache_lookup": (C.c_int, [C.c_char_p, C.c_char_p, C.POINTER(i32)]),
-    "drgb_tuning_cache_store": (C.c_int, [C.c_char_p, C.c_char_p, i32]),
+    "drgb_tuning_cache_lookup": (C.c_int, [C.c_char_p, C.c_char_p, C.POINTER(i32), C.POINTER(i32)]),
+    "drgb_tuning_cache_store": (C.c_int, [C.c_char_p, C.c_char_p, i32, i32]),
     "drgb_set_profiling": (C.c_int, [vp, C.c_int]),
     "drgb_stage_times": (C.c_int, [vp, C.POINTER(C.c_float), C.c_int]),
     "drgb_knn_graph": (C.c_int, [vp, vp, i64, i32, i32, i32, vp, vp, vp]),
@@ -85,6 +85,8 @@ SIGNATURES = {
                                       C.POINTER(C.c_int32), C.POINTER(C.c_float), vp]),
     "drgb_eval_recall": (C.c_int, [vp, vp, vp, i64, i32, i32, i64, C.POINTER(C.c_double), vp]),
     "drgb_eval_trust": (C.c_int, [vp, vp, vp, i64, i32, i32, i64, C.POINTER(C.c_double), vp]),
+    "drgb_eval_recall_heldout": (C.c_int, [vp, vp, vp, i64, vp, vp, i64, i32, i32, i64, C.POINTER(C.c_double),
+                                           vp]),
 }
 
 _lib = None

@@ -9,9 +9,10 @@
 // to fitting it alone with the same seeds.  The epoch loop of all instances is
 // one captured CUDA graph.
 //
-// Also here: the epoch schedule autotuner, which times every supported
-// (rows per block, q prefetch, scheduling) choice on the actual graph; all of
-// them give bit-identical results, so it changes speed only.
+// Also here: the epoch autotuner's entry point, which times every supported
+// force-kernel setting (width 4 or 8 warps per CTA, pipelined or flat form)
+// on the actual graph; all of them give bit-identical results, so it changes
+// speed only.
 #include <vector>
 
 #include "common.cuh"
@@ -127,10 +128,11 @@ int drgb_fit_transform_batched(drgb_ctx* c, const float* X_cat, const int64_t* o
         // context has a tuning cache that holds one; else time the choices
         // (and record the winner there)
         const std::string key = tuning_key(c, N, count, k);
-        int32_t cached = 0;
+        int32_t cached_w = 0, cached_p = 1;
         if (!c->tuning_cache.empty() &&
-            drgb_tuning_cache_lookup(c->tuning_cache.c_str(), key.c_str(), &cached) == DRGB_OK) {
-            c->epoch_warps = cached;
+            drgb_tuning_cache_lookup(c->tuning_cache.c_str(), key.c_str(), &cached_w, &cached_p) == DRGB_OK) {
+            c->epoch_warps = cached_w;
+            c->epoch_pipe = cached_p;
         } else {
             float us = 0.f;
             EpochScratch es;
@@ -139,7 +141,8 @@ int drgb_fit_transform_batched(drgb_ctx* c, const float* X_cat, const int64_t* o
                                 count, d_off, d_seed_neg, &us);
             if (rc) return rc;
             if (!c->tuning_cache.empty() &&
-                drgb_tuning_cache_store(c->tuning_cache.c_str(), key.c_str(), c->epoch_warps) != DRGB_OK)
+                drgb_tuning_cache_store(c->tuning_cache.c_str(), key.c_str(), c->epoch_warps, c->epoch_pipe) !=
+                    DRGB_OK)
                 return set_error(c, DRGB_ERR_INVALID, "tuning cache %s could not be written", c->tuning_cache.c_str());
         }
     }
@@ -177,7 +180,7 @@ int drgb_autotune_epoch(drgb_ctx* c, const float* Y, const int32_t* row_ptr, con
     if (rc) return rc;
     if (choice) {
         choice[0] = c->epoch_warps;
-        choice[1] = 0;
+        choice[1] = c->epoch_pipe;
         choice[2] = 0;
     }
     return drgb_sync(c, stream);

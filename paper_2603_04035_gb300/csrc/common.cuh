@@ -33,6 +33,9 @@ struct Ctx {
     cudaEvent_t stage_ev[8] = {};
     int stage_marks = 0;
     bool gemm_marked = false;     // events 6, 7 bracket the tensor-core k-NN kernel
+    // The executable graph of the last epoch loop, refreshed in place
+    // (cudaGraphExecUpdate) when the next loop has the same shape.
+    cudaGraphExec_t epoch_exec = nullptr;
     std::string err;
 };
 

@@ -151,11 +151,17 @@ int exclusive_scan(Ctx* c, const int32_t* in, int32_t* out, int64_t n, int32_t* 
 // ------------------------------------------------------------------ tuning cache
 // The file is a JSON object with one entry per line, written by this library:
 //   {
-//     "<key>": {"epoch_warps": 8},
+//     "<key>": {"epoch_warps": 8, "epoch_pipe": 1},
 //     ...
 //   }
 // Keys are printable ASCII without quotes or backslashes.  Reading accepts
 // exactly the lines of that form and ignores every other line.
+
+// A tuned epoch setting: force-kernel width and form.
+struct TunedEpoch {
+    int warps;
+    int pipe;
+};
 
 bool cache_key_ok(const char* k) {
     if (!k || !*k) return false;
@@ -167,8 +173,8 @@ bool cache_key_ok(const char* k) {
     return n < 256;
 }
 
-std::map<std::string, int> cache_read(const char* path) {
-    std::map<std::string, int> m;
+std::map<std::string, TunedEpoch> cache_read(const char* path) {
+    std::map<std::string, TunedEpoch> m;
     FILE* f = std::fopen(path, "r");
     if (!f) return m;
     char line[1024];
@@ -183,21 +189,27 @@ std::map<std::string, int> cache_read(const char* path) {
         char* end = nullptr;
         const long w = std::strtol(v + std::strlen("\"epoch_warps\":"), &end, 10);
         if (end == v || w < 1 || w > 1024) continue;
-        m[key] = int(w);
+        long pp = 1;  // entries written before the form was tuned: the default form
+        if (const char* u = std::strstr(q + 1, "\"epoch_pipe\":")) {
+            char* e2 = nullptr;
+            pp = std::strtol(u + std::strlen("\"epoch_pipe\":"), &e2, 10);
+            if (e2 == u || pp < 0 || pp > 1) continue;
+        }
+        m[key] = TunedEpoch{int(w), int(pp)};
     }
     std::fclose(f);
     return m;
 }
 
-bool cache_write(const char* path, const std::map<std::string, int>& m) {
+bool cache_write(const char* path, const std::map<std::string, TunedEpoch>& m) {
     const std::string tmp = std::string(path) + ".tmp";
     FILE* f = std::fopen(tmp.c_str(), "w");
     if (!f) return false;
     bool ok = std::fputs("{\n", f) >= 0;
     size_t i = 0;
     for (const auto& kv : m) {
-        ok = ok && std::fprintf(f, "  \"%s\": {\"epoch_warps\": %d}%s\n", kv.first.c_str(), kv.second,
-                                ++i < m.size() ? "," : "") > 0;
+        ok = ok && std::fprintf(f, "  \"%s\": {\"epoch_warps\": %d, \"epoch_pipe\": %d}%s\n", kv.first.c_str(),
+                                kv.second.warps, kv.second.pipe, ++i < m.size() ? "," : "") > 0;
     }
     ok = ok && std::fputs("}\n", f) >= 0;
     ok = (std::fclose(f) == 0) && ok;
@@ -275,6 +287,7 @@ int drgb_ctx_destroy(drgb_ctx* c) {
     cudaGetDevice(&prev);
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
+    if (c->epoch_exec) cudaGraphExecDestroy(c->epoch_exec);
     if (c->scratch) cudaFree(c->scratch);
     if (c->d_status) cudaFree(c->d_status);
     for (auto& e : c->stage_ev)
@@ -308,20 +321,22 @@ int drgb_set_tuning(drgb_ctx* c, int32_t param, int32_t value) {
     }
 }
 
-int drgb_tuning_cache_lookup(const char* path, const char* key, int32_t* epoch_warps) {
-    if (!path || !*path || !drgb::cache_key_ok(key) || !epoch_warps) return DRGB_ERR_INVALID;
+int drgb_tuning_cache_lookup(const char* path, const char* key, int32_t* epoch_warps, int32_t* epoch_pipe) {
+    if (!path || !*path || !drgb::cache_key_ok(key) || !epoch_warps || !epoch_pipe) return DRGB_ERR_INVALID;
     const auto m = drgb::cache_read(path);
     const auto it = m.find(key);
-    if (it == m.end() || !drgb::epoch_warps_supported(it->second)) return DRGB_ERR_INVALID;
-    *epoch_warps = it->second;
+    if (it == m.end() || !drgb::epoch_warps_supported(it->second.warps)) return DRGB_ERR_INVALID;
+    *epoch_warps = it->second.warps;
+    *epoch_pipe = it->second.pipe;
     return DRGB_OK;
 }
 
-int drgb_tuning_cache_store(const char* path, const char* key, int32_t epoch_warps) {
-    if (!path || !*path || !drgb::cache_key_ok(key) || !drgb::epoch_warps_supported(epoch_warps))
+int drgb_tuning_cache_store(const char* path, const char* key, int32_t epoch_warps, int32_t epoch_pipe) {
+    if (!path || !*path || !drgb::cache_key_ok(key) || !drgb::epoch_warps_supported(epoch_warps) ||
+        (epoch_pipe != 0 && epoch_pipe != 1))
         return DRGB_ERR_INVALID;
     auto m = drgb::cache_read(path);
-    m[key] = epoch_warps;
+    m[key] = drgb::TunedEpoch{epoch_warps, epoch_pipe};
     return drgb::cache_write(path, m) ? DRGB_OK : DRGB_ERR_INVALID;
 }
 

@@ -640,8 +640,12 @@ static void fill_args(EpochArgs& A, const int32_t* rp, const int32_t* col, const
 }
 
 // Epochs [t_begin, t_end) of a T-epoch schedule, ping-ponging between Y and
-// Y_tmp; the result is left in Y.  The launches are captured once into a CUDA
-// graph (on a private stream) and the graph is launched on `st`.
+// Y_tmp; the result is left in Y.  The launches are captured into a CUDA
+// graph (on a private stream) and the graph is launched on `st`.  Building an
+// executable graph of hundreds of nodes costs milliseconds of host time, so
+// the context keeps the last one and refreshes it in place
+// (cudaGraphExecUpdate: same nodes, new parameters) whenever the new loop has
+// the same shape; a launch already enqueued keeps the parameters it had.
 int run_epochs(Ctx* c, float2* Y, float2* Y_tmp, const int32_t* rp, const int32_t* col, const uint32_t* q,
                int64_t n, float a, float b, float lr0, int neg, int t_begin, int t_end, int T, uint64_t seed,
                cudaStream_t st, int64_t nnz_cap, void* scratch, int count, const int64_t* inst_off,
@@ -653,7 +657,6 @@ int run_epochs(Ctx* c, float2* Y, float2* Y_tmp, const int32_t* rp, const int32_
     cudaStream_t cap;
     DRGB_CUDA(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
         cudaStreamDestroy(cap);
@@ -678,24 +681,33 @@ int run_epochs(Ctx* c, float2* Y, float2* Y_tmp, const int32_t* rp, const int32_
     e = cudaStreamEndCapture(cap, &graph);
     if (rc == DRGB_OK && e != cudaSuccess)
         rc = set_error(c, DRGB_ERR_CUDA, "end capture: %s", cudaGetErrorString(e));
-    if (rc == DRGB_OK) {
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        if (e != cudaSuccess) rc = set_error(c, DRGB_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
+    if (rc == DRGB_OK && c->epoch_exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(c->epoch_exec, graph, &info) != cudaSuccess) {
+            cudaGetLastError();  // a different shape: build a new executable graph
+            cudaGraphExecDestroy(c->epoch_exec);
+            c->epoch_exec = nullptr;
+        }
+    }
+    if (rc == DRGB_OK && !c->epoch_exec) {
+        e = cudaGraphInstantiate(&c->epoch_exec, graph, 0);
+        if (e != cudaSuccess) {
+            c->epoch_exec = nullptr;
+            rc = set_error(c, DRGB_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
+        }
     }
     if (rc == DRGB_OK) {
-        e = cudaGraphLaunch(exec, st);
+        e = cudaGraphLaunch(c->epoch_exec, st);
         if (e != cudaSuccess) rc = set_error(c, DRGB_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
     }
-    // The executable graph may be destroyed right after the launch is
-    // enqueued; the launch keeps what it needs.
-    if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     cudaStreamDestroy(cap);
     return rc;
 }
 
-// Force-kernel widths tried by the tuner.
+// Force-kernel widths and forms tried by the tuner.
 static const int kWarpChoices[] = {4, 8};
+static const int kPipeChoices[] = {1, 0};
 
 int autotune_epoch(Ctx* c, const float2* Y, float2* Ya, float2* Yb, const int32_t* rp, const int32_t* col,
                    const uint32_t* q, int64_t n, float a, float b, int neg, int T, uint64_t seed, int trials,
@@ -704,41 +716,49 @@ int autotune_epoch(Ctx* c, const float2* Y, float2* Ya, float2* Yb, const int32_
     cudaEvent_t e0, e1;
     DRGB_CUDA(c, cudaEventCreate(&e0));
     DRGB_CUDA(c, cudaEventCreate(&e1));
-    int best_w = c->epoch_warps, rc = DRGB_OK;
+    const int saved_pipe = c->epoch_pipe;
+    int best_w = c->epoch_warps, best_p = c->epoch_pipe, rc = DRGB_OK;
     float best = 1e30f;
     const int t0 = T / 4 < T - trials ? T / 4 : (T - trials > 0 ? T - trials : 0);
-    for (int warps : kWarpChoices) {
-        EpochArgs A;
-        fill_args(A, rp, col, q, n, a, b, neg, seed, c->d_status, es, count, inst_off, inst_seed, 0, 0);
-        if (cudaMemcpyAsync(Ya, Y, size_t(n) * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
-            rc = set_error(c, DRGB_ERR_CUDA, "autotune: copy failed");
-            break;
-        }
-        float ms = 0.f;
-        for (int pass = 0; pass < 2 && rc == DRGB_OK; ++pass) {  // pass 0 warms up
-            cudaEventRecord(e0, st);
-            for (int k = 0; k < trials && rc == DRGB_OK; ++k) {
-                A.Y_in = (k & 1) ? Yb : Ya;
-                A.Y_out = (k & 1) ? Ya : Yb;
-                A.t = uint32_t(t0 + k);
-                A.lr = 1.0f - float(t0 + k) / float(T);
-                rc = launch_epoch(c, A, warps, st, k > 0);
+    for (int pipe : kPipeChoices) {
+        c->epoch_pipe = pipe;
+        for (int warps : kWarpChoices) {
+            EpochArgs A;
+            fill_args(A, rp, col, q, n, a, b, neg, seed, c->d_status, es, count, inst_off, inst_seed, 0, 0);
+            if (cudaMemcpyAsync(Ya, Y, size_t(n) * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+                rc = set_error(c, DRGB_ERR_CUDA, "autotune: copy failed");
+                break;
             }
-            cudaEventRecord(e1, st);
-            if (cudaEventSynchronize(e1) != cudaSuccess) rc = set_error(c, DRGB_ERR_CUDA, "autotune: sync failed");
-            cudaEventElapsedTime(&ms, e0, e1);
+            float ms = 0.f;
+            for (int pass = 0; pass < 2 && rc == DRGB_OK; ++pass) {  // pass 0 warms up
+                cudaEventRecord(e0, st);
+                for (int k = 0; k < trials && rc == DRGB_OK; ++k) {
+                    A.Y_in = (k & 1) ? Yb : Ya;
+                    A.Y_out = (k & 1) ? Ya : Yb;
+                    A.t = uint32_t(t0 + k);
+                    A.lr = 1.0f - float(t0 + k) / float(T);
+                    rc = launch_epoch(c, A, warps, st, k > 0);
+                }
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = set_error(c, DRGB_ERR_CUDA, "autotune: sync failed");
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (rc) break;
+            const float us = ms * 1000.f / trials;
+            if (us < best) {
+                best = us;
+                best_w = warps;
+                best_p = pipe;
+            }
         }
         if (rc) break;
-        const float us = ms * 1000.f / trials;
-        if (us < best) {
-            best = us;
-            best_w = warps;
-        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    c->epoch_pipe = saved_pipe;
     if (rc) return rc;
     c->epoch_warps = best_w;
+    c->epoch_pipe = best_p;
     if (best_us) *best_us = best;
     return DRGB_OK;
 }

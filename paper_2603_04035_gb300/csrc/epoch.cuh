@@ -76,9 +76,10 @@ int run_epochs(Ctx* c, float2* Y, float2* Y_tmp, const int32_t* rp, const int32_
                cudaStream_t st, int64_t nnz_cap, void* scratch, int count = 0, const int64_t* inst_off = nullptr,
                const uint64_t* inst_seed = nullptr, int64_t row_begin = 0, uint32_t neg_n = 0);
 
-// Time every supported force-kernel width on this graph for `trials` epochs
-// (Ya, Yb: n-float2 scratch; Y is not modified) and keep the fastest in the
-// context; results do not depend on the choice.  `es` comes from epoch_prepare.
+// Time every supported force-kernel width and form on this graph for `trials`
+// epochs (Ya, Yb: n-float2 scratch; Y is not modified) and keep the fastest in
+// the context; results do not depend on the choice.  `es` comes from
+// epoch_prepare.
 int autotune_epoch(Ctx* c, const float2* Y, float2* Ya, float2* Yb, const int32_t* rp, const int32_t* col,
                    const uint32_t* q, int64_t n, float a, float b, int neg, int T, uint64_t seed, int trials,
                    cudaStream_t st, const EpochScratch& es, int count, const int64_t* inst_off,

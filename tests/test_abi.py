@@ -104,38 +104,45 @@ def test_tuning_cache_round_trip(lib, tmp_path):
     import json
     from paper_2603_04035_gb300 import _lib
     path = str(tmp_path / "tune.json").encode()
-    v = C.c_int32(0)
+    v, pp = C.c_int32(0), C.c_int32(0)
     key = b"NVIDIA GB300|152 SMs|rows 2^21|instances 2^8|k 15"
-    assert lib.drgb_tuning_cache_lookup(path, key, C.byref(v)) == _lib.ERR_INVALID   # no file yet
-    assert lib.drgb_tuning_cache_store(path, key, 8) == 0
-    assert lib.drgb_tuning_cache_store(path, b"other|1", 4) == 0
-    assert lib.drgb_tuning_cache_lookup(path, key, C.byref(v)) == 0 and v.value == 8
-    assert lib.drgb_tuning_cache_store(path, key, 4) == 0                              # replaced
-    assert lib.drgb_tuning_cache_lookup(path, key, C.byref(v)) == 0 and v.value == 4
+    assert lib.drgb_tuning_cache_lookup(path, key, C.byref(v), C.byref(pp)) == _lib.ERR_INVALID   # no file yet
+    assert lib.drgb_tuning_cache_store(path, key, 8, 1) == 0
+    assert lib.drgb_tuning_cache_store(path, b"other|1", 4, 0) == 0
+    assert lib.drgb_tuning_cache_lookup(path, key, C.byref(v), C.byref(pp)) == 0 and (v.value, pp.value) == (8, 1)
+    assert lib.drgb_tuning_cache_store(path, key, 4, 0) == 0                              # replaced
+    assert lib.drgb_tuning_cache_lookup(path, key, C.byref(v), C.byref(pp)) == 0 and (v.value, pp.value) == (4, 0)
     with open(path) as f:
-        assert json.load(f) == {key.decode(): {"epoch_warps": 4}, "other|1": {"epoch_warps": 4}}
-    assert lib.drgb_tuning_cache_lookup(path, b"missing", C.byref(v)) == _lib.ERR_INVALID
+        assert json.load(f) == {key.decode(): {"epoch_warps": 4, "epoch_pipe": 0},
+                                "other|1": {"epoch_warps": 4, "epoch_pipe": 0}}
+    assert lib.drgb_tuning_cache_lookup(path, b"missing", C.byref(v), C.byref(pp)) == _lib.ERR_INVALID
 
 
 def test_tuning_cache_rejects_bad_keys_values_and_paths(lib, tmp_path):
     from paper_2603_04035_gb300 import _lib
     path = str(tmp_path / "tune.json").encode()
     for bad in (b"", b'a"b', b"a\\b", b"tab\there", b"x" * 256):
-        assert lib.drgb_tuning_cache_store(path, bad, 8) == _lib.ERR_INVALID, bad
+        assert lib.drgb_tuning_cache_store(path, bad, 8, 1) == _lib.ERR_INVALID, bad
     for warps in (0, 5, 16):
-        assert lib.drgb_tuning_cache_store(path, b"k", warps) == _lib.ERR_INVALID, warps
+        assert lib.drgb_tuning_cache_store(path, b"k", warps, 1) == _lib.ERR_INVALID, warps
+    for pipe in (-1, 2):
+        assert lib.drgb_tuning_cache_store(path, b"k", 8, pipe) == _lib.ERR_INVALID, pipe
     assert not os.path.exists(path)
-    assert lib.drgb_tuning_cache_store(str(tmp_path / "no" / "dir.json").encode(), b"k", 8) == _lib.ERR_INVALID
+    assert lib.drgb_tuning_cache_store(str(tmp_path / "no" / "dir.json").encode(), b"k", 8, 1) == _lib.ERR_INVALID
     assert lib.drgb_set_tuning_cache(None, path) == _lib.ERR_INVALID
 
 
 def test_tuning_cache_reads_only_its_own_lines(lib, tmp_path):
     from paper_2603_04035_gb300 import _lib
     p = tmp_path / "tune.json"
-    p.write_text('{\n  garbage line\n  "a": {"epoch_warps": 6},\n  "b": {"epoch_warps": 4}\n}\n')
-    v = C.c_int32(0)
-    assert lib.drgb_tuning_cache_lookup(str(p).encode(), b"b", C.byref(v)) == 0 and v.value == 4
-    assert lib.drgb_tuning_cache_lookup(str(p).encode(), b"a", C.byref(v)) == _lib.ERR_INVALID  # unsupported
+    p.write_text('{\n  garbage line\n  "a": {"epoch_warps": 6},\n  "b": {"epoch_warps": 4},\n'
+                 '  "c": {"epoch_warps": 8, "epoch_pipe": 0},\n  "d": {"epoch_warps": 8, "epoch_pipe": 7}\n}\n')
+    v, pp = C.c_int32(0), C.c_int32(0)
+    f = str(p).encode()
+    assert lib.drgb_tuning_cache_lookup(f, b"b", C.byref(v), C.byref(pp)) == 0 and (v.value, pp.value) == (4, 1)
+    assert lib.drgb_tuning_cache_lookup(f, b"c", C.byref(v), C.byref(pp)) == 0 and (v.value, pp.value) == (8, 0)
+    assert lib.drgb_tuning_cache_lookup(f, b"a", C.byref(v), C.byref(pp)) == _lib.ERR_INVALID  # unsupported
+    assert lib.drgb_tuning_cache_lookup(f, b"d", C.byref(v), C.byref(pp)) == _lib.ERR_INVALID  # bad form
 
 
 def test_tuning_cache_python_wrappers(lib, tmp_path):
@@ -143,7 +150,9 @@ def test_tuning_cache_python_wrappers(lib, tmp_path):
     path = str(tmp_path / "t.json")
     assert drgb.tuning_cache_lookup(path, "k") is None
     drgb.tuning_cache_store(path, "k", 8)
-    assert drgb.tuning_cache_lookup(path, "k") == 8
+    assert drgb.tuning_cache_lookup(path, "k") == (8, 1)
+    drgb.tuning_cache_store(path, "k", 4, 0)
+    assert drgb.tuning_cache_lookup(path, "k") == (4, 0)
     with pytest.raises(drgb.DrgbError):
         drgb.tuning_cache_store(path, "k", 3)
 

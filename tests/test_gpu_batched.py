@@ -68,7 +68,7 @@ def test_autotune_returns_a_supported_choice(drgb):
     Y = drgb.init_embedding(5000, 10.0, 1)
     Y0 = Y.clone()
     choice, us = drgb.autotune_epoch(Y, g, 1.577, 0.895, trials=2)
-    assert choice in (4, 8)
+    assert choice[0] in (4, 8) and choice[1] in (0, 1)
     assert us > 0 and torch.equal(Y, Y0)   # the caller's embedding is untouched
 
 
@@ -104,10 +104,11 @@ def test_autotune_uses_and_fills_the_tuning_cache(drgb, tmp_path):
         key, val = next(iter(entries.items()))
         assert key.endswith(f"|rows 2^{int(np.log2(sum(sizes)))}|instances 2^2|k 15")
         assert val["epoch_warps"] == drgb.get_tuning(_lib.TUNE_EPOCH_WARPS)
-        other = 4 if val["epoch_warps"] == 8 else 8
-        drgb.tuning_cache_store(path, key, other)
-        Y1 = drgb.fit_transform_batched(Xd, off, autotune=True, n_epochs=60).cpu()   # takes the stored width
-        assert drgb.get_tuning(_lib.TUNE_EPOCH_WARPS) == other
+        assert val["epoch_pipe"] == drgb.get_tuning(_lib.TUNE_EPOCH_PIPE)
+        other = (4 if val["epoch_warps"] == 8 else 8, 1 - val["epoch_pipe"])
+        drgb.tuning_cache_store(path, key, *other)
+        Y1 = drgb.fit_transform_batched(Xd, off, autotune=True, n_epochs=60).cpu()   # takes the stored setting
+        assert (drgb.get_tuning(_lib.TUNE_EPOCH_WARPS), drgb.get_tuning(_lib.TUNE_EPOCH_PIPE)) == other
         assert torch.equal(Y0, Y1)
     finally:
         drgb.set_tuning_cache(None)

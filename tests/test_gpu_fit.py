@@ -67,6 +67,23 @@ def test_metrics_match_oracle(drgb):
         assert abs(r - ro) < 2e-3 and abs(t - to) < 1e-4, (r, ro, t, to)
 
 
+@pytest.mark.parametrize("n_query", [0, 333])
+def test_heldout_recall_matches_oracle(drgb, n_query):
+    import torch
+    X, _ = datagen.mixture(3500, 50, 10, seed=5)
+    Xt, Xn = X[:3000], X[3000:]
+    Yt = _gpu_fit(drgb, np.ascontiguousarray(Xt), n_epochs=100)
+    # new points placed near their first training neighbour's position, with noise
+    near = np.argmin(((Xn[:, None, :5] - Xt[None, :, :5]) ** 2).sum(-1), axis=1)
+    Yn = (Yt[near] + np.random.default_rng(1).normal(scale=0.5, size=(500, 2))).astype(np.float32)
+    d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (Xt, Yt, Xn, Yn)]
+    r = drgb.eval_recall_heldout(*d, 15, n_query)
+    ro = omet.heldout_recall(Xt, Yt, Xn, Yn, 15, n_query)
+    # exact neighbour sets on both sides; only FP32/FP64 distance ties may differ
+    assert abs(r - ro) < 2e-3, (r, ro)
+    assert 0.01 < ro < 0.99
+
+
 def test_epoch_callback_sees_every_epoch(drgb):
     import torch
     X, _ = datagen.mixture(500, 20, 5, seed=1)

@@ -146,19 +146,26 @@ def test_transform_matches_oracle(drgb, problem):
     assert np.all(err <= bound), (err.max(), (err / bound).max())
 
 
-def test_learned_embedder_gain_over_plain_transform(drgb, problem):
-    # what the trained network buys: new points embedded by one forward pass
-    # instead of a k-NN search and an optimisation per batch of new points
+def test_learned_embedder_gain_over_plain_transform(drgb):
+    """What the trained network buys: new points embedded by one forward pass
+    instead of a k-NN search and an optimisation, at the same held-out 15-NN
+    recall.  Held-out recall compares each new point's 15 nearest training
+    points in X with its 15 nearest training points in 2-D (the network's own
+    image of the training set for the MLP, the fitted embedding for the
+    transform); 15-NN recall among the new points themselves cannot separate
+    the two here, because within a Gaussian cluster the neighbours in 50-d
+    are set by noise that no 2-D map keeps."""
     import time
     import torch
-    X, g = problem
-    Xd = torch.from_numpy(X).cuda()
-    P = drgb.mlp_init(50, seed=1)
+    X, _ = datagen.mixture(12_000, 50, 10, seed=7)
+    Xd = torch.from_numpy(np.ascontiguousarray(X[:10_000])).cuda()
+    Xn = torch.from_numpy(np.ascontiguousarray(X[10_000:])).cuda()
+    idx, dist = drgb.knn_graph(Xd, 15)
+    g = drgb.fuzzy_weights(idx, dist, 200)
+    P = drgb.mlp_init(50, seed=0)
     m, v = torch.zeros_like(P), torch.zeros_like(P)
-    drgb.mlp_train(Xd, _graph(drgb, g), A_, B_, P, m, v, steps=600, batch_edges=1024, neg=5, seed=2)
+    drgb.mlp_train(Xd, g, A_, B_, P, m, v, steps=int(50 * g.nnz / 4096), batch_edges=4096, neg=5, seed=1)
     Yt = drgb.fit_transform(Xd, n_epochs=200)
-    Xn, _ = datagen.mixture(22000, 50, 10, seed=7)
-    Xn = torch.from_numpy(np.ascontiguousarray(Xn[2000:])).cuda()
     for _ in range(2):
         drgb.mlp_embed(P, Xn)
         drgb.transform(Xd, Yt, Xn, n_epochs=200)
@@ -171,8 +178,11 @@ def test_learned_embedder_gain_over_plain_transform(drgb, problem):
     Yp = drgb.transform(Xd, Yt, Xn, n_epochs=200)
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - t0
-    rm = drgb.eval_recall(Xn, Ym, 15, 4000)
-    rp = drgb.eval_recall(Xn, Yp, 15, 4000)
-    print(f"mlp {len(Xn) / t_mlp:.3g} pts/s recall {rm:.4f}; transform {len(Xn) / t_plain:.3g} pts/s recall {rp:.4f}")
+    rm = drgb.eval_recall_heldout(Xd, drgb.mlp_embed(P, Xd), Xn, Ym, 15)
+    rp = drgb.eval_recall_heldout(Xd, Yt, Xn, Yp, 15)
+    print(f"mlp {len(Xn) / t_mlp:.3g} pts/s held-out recall {rm:.4f}; "
+          f"transform {len(Xn) / t_plain:.3g} pts/s held-out recall {rp:.4f}")
+    chance = 15 / len(Xd)
+    assert rm > 10 * chance and rp > 10 * chance
+    assert abs(rm - rp) <= 0.01, (rm, rp)
     assert t_plain > 5 * t_mlp
-    assert rm > 10 * 15 / len(Xn) and rp > 10 * 15 / len(Xn)

@@ -47,3 +47,53 @@ def test_sampled_trust_equals_full_on_all_rows():
     full = metrics.trustworthiness(X, ny)
     part = metrics.trustworthiness(X, ny, rows=np.arange(300))
     assert full == part
+
+
+# ---------------------------------------------------------------- held-out recall
+def _brute_heldout(Xt, Yt, Xn, Yn, k, rows):
+    """Python loops over (squared distance, index) pairs in both spaces."""
+    hits = 0
+    for r in rows:
+        dx = sorted((float(((Xt[j] - Xn[r]) ** 2).sum()), j) for j in range(len(Xt)))
+        dy = sorted((float(((Yt[j] - Yn[r]) ** 2).sum()), j) for j in range(len(Yt)))
+        hits += len({j for _, j in dx[:k]} & {j for _, j in dy[:k]})
+    return hits / (k * len(rows))
+
+
+def test_heldout_recall_matches_brute_force():
+    g = np.random.default_rng(11)
+    Xt, Xn = g.normal(size=(120, 6)), g.normal(size=(40, 6))
+    # a lossy 2-D view: the first two coordinates plus noise
+    Yt = Xt[:, :2] + 0.3 * g.normal(size=(120, 2))
+    Yn = Xn[:, :2] + 0.3 * g.normal(size=(40, 2))
+    for k, nq in [(5, 0), (10, 13)]:
+        rows = metrics.strided_rows(40, nq)
+        want = _brute_heldout(Xt, Yt, Xn, Yn, k, rows)
+        assert metrics.heldout_recall(Xt, Yt, Xn, Yn, k, nq) == pytest.approx(want, abs=1e-12)
+        assert 0.0 < want < 1.0
+
+
+def test_heldout_recall_of_an_isometry_is_one():
+    g = np.random.default_rng(12)
+    Xt, Xn = g.normal(size=(500, 2)), g.normal(size=(100, 2))
+    c, s_ = np.cos(0.7), np.sin(0.7)
+    Rm = 3.0 * np.array([[c, -s_], [s_, c]])
+    shift = np.array([5.0, -2.0])
+    assert metrics.heldout_recall(Xt, Xt @ Rm + shift, Xn, Xn @ Rm + shift, 15) == 1.0
+
+
+def test_heldout_recall_uses_the_training_points_as_reference():
+    # the new points' neighbours are taken among the training points: a new
+    # embedding that is right but a training embedding that is shuffled
+    # scores near chance (k / n_train)
+    g = np.random.default_rng(13)
+    Xt, Xn = g.normal(size=(2000, 2)), g.normal(size=(300, 2))
+    Yt = Xt[g.permutation(2000)]
+    r = metrics.heldout_recall(Xt, Yt, Xn, Xn, 15)
+    assert r < 5 * 15 / 2000
+
+
+def test_strided_rows():
+    assert list(metrics.strided_rows(10, 4)) == [0, 2, 5, 7]
+    assert list(metrics.strided_rows(5, 0)) == [0, 1, 2, 3, 4]
+    assert list(metrics.strided_rows(5, 9)) == [0, 1, 2, 3, 4]
