@@ -1,7 +1,10 @@
 // Batched form: many independent instances of uneven size embedded together.
 // The concatenated instances form one block-diagonal problem: each instance's
 // k-NN graph is computed separately (rows of one instance only see that
-// instance), its indices are made global, the fuzzy graph of the whole
+// instance; the k-NN runs of all instances are enqueued back to back with no
+// host synchronisation between them: the uncertified rows of each run are
+// collected on the device and re-scanned after the last run, with one read of
+// their counts), its indices are made global, the fuzzy graph of the whole
 // concatenation is built at once (its rows never cross instances), and every
 // epoch runs as one launch over all rows with instance-local entry numbers,
 // negative ranges and Philox keys.  Every arithmetic step of a row is the one a
@@ -21,6 +24,9 @@
 #include "knn.cuh"
 
 namespace drgb {
+
+// Streams the batched k-NN runs spread over.
+static constexpr int BATCH_STREAMS = 8;
 
 __global__ void globalize_idx_kernel(int32_t* __restrict__ idx, int64_t n_total, int k, int count,
                                      const int64_t* __restrict__ inst_off) {
@@ -75,10 +81,15 @@ int drgb_fit_transform_batched(drgb_ctx* c, const float* X_cat, const int64_t* o
     }
     const size_t Nk = size_t(N) * k;
     const size_t main_bytes = Carve::round(Nk * 4) * 2 + Carve::round((N + 1) * 4) + Carve::round(2 * Nk * 4) * 3 +
+                              Carve::round(N * 4) + Carve::round(count * 4) +
                               Carve::round(N * 8) * 2 + Carve::round((count + 1) * 8) + 2 * Carve::round(count * 8) +
                               Carve::round(fuzzy_scratch_bytes(N, k)) +
                               Carve::round(epoch_scratch_bytes(N, int64_t(2 * Nk), count)) + 8192;
-    int rc = ensure_scratch(c, Carve::round(main_bytes) + knn_bytes, st);
+    // instances are small: their k-NN runs go round-robin to BATCH_STREAMS
+    // streams, each with its own k-NN scratch region, so that several run at once
+    const int n_str = count < BATCH_STREAMS ? count : BATCH_STREAMS;
+    const size_t knn_region = Carve::round(knn_bytes);
+    int rc = ensure_scratch(c, Carve::round(main_bytes) + size_t(n_str) * knn_region, st);
     if (rc) return rc;
     Carve cv(c->scratch);
     int32_t* idx = cv.take<int32_t>(Nk);
@@ -94,6 +105,8 @@ int drgb_fit_transform_batched(drgb_ctx* c, const float* X_cat, const int64_t* o
     uint64_t* d_seed_neg = cv.take<uint64_t>(count);
     void* fz = cv.take<char>(fuzzy_scratch_bytes(N, k));
     void* ep = cv.take<char>(epoch_scratch_bytes(N, int64_t(2 * Nk), count));
+    int32_t* fail_rows = cv.take<int32_t>(N);      // uncertified rows of instance b at [offsets[b], ...)
+    int32_t* fail_count = cv.take<int32_t>(count);
     void* knn_scratch = static_cast<char*>(c->scratch) + Carve::round(main_bytes);
 
     std::vector<uint64_t> si(count), sn(count);
@@ -110,10 +123,58 @@ int drgb_fit_transform_batched(drgb_ctx* c, const float* X_cat, const int64_t* o
     c->stage_marks = 0;
     if ((rc = launch_nonfinite_scan(c, X_cat, N * d, st))) return rc;
     if ((rc = stage_mark(c, 0, st))) return rc;
-    for (int b = 0; b < count; ++b) {
-        const int64_t off = offsets[b], nb = offsets[b + 1] - off;
-        rc = knn_run(c, X_cat + off * d, nb, d, k, p->knn_mode, idx + off * k, dist + off * k, st, knn_scratch);
+    DRGB_CUDA(c, cudaMemsetAsync(fail_count, 0, size_t(count) * 4, st));
+    {
+        // side streams start after the work already on `st` and `st` waits
+        // for all of them; they are created and destroyed per call
+        cudaStream_t ss[BATCH_STREAMS] = {};
+        cudaEvent_t ev[BATCH_STREAMS + 1] = {};
+        auto release = [&]() {
+            for (int i = 0; i < n_str; ++i)
+                if (ss[i]) cudaStreamDestroy(ss[i]);
+            for (int i = 0; i <= n_str; ++i)
+                if (ev[i]) cudaEventDestroy(ev[i]);
+        };
+        cudaError_t e = cudaEventCreateWithFlags(&ev[n_str], cudaEventDisableTiming);
+        for (int i = 0; i < n_str && e == cudaSuccess; ++i) {
+            e = cudaStreamCreateWithFlags(&ss[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev[n_str], st);
+        for (int i = 0; i < n_str && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(ss[i], ev[n_str], 0);
+        if (e != cudaSuccess) {
+            release();
+            return set_error(c, DRGB_ERR_CUDA, "fit_transform_batched: side streams: %s", cudaGetErrorString(e));
+        }
+        for (int b = 0; b < count && rc == DRGB_OK; ++b) {
+            const int64_t off = offsets[b], nb = offsets[b + 1] - off;
+            const int si_ = b % n_str;
+            rc = knn_run(c, X_cat + off * d, nb, d, k, p->knn_mode, idx + off * k, dist + off * k, ss[si_],
+                         static_cast<char*>(knn_scratch) + size_t(si_) * knn_region, fail_rows + off, fail_count + b);
+        }
+        for (int i = 0; i < n_str; ++i) {
+            if (cudaEventRecord(ev[i], ss[i]) != cudaSuccess || cudaStreamWaitEvent(st, ev[i], 0) != cudaSuccess) {
+                if (rc == DRGB_OK) rc = set_error(c, DRGB_ERR_CUDA, "fit_transform_batched: joining side streams");
+            }
+        }
+        release();
         if (rc) return rc;
+    }
+    // exact re-scan of every instance's uncertified rows (the k-NN scratch is
+    // free again: its partial lists go there)
+    {
+        std::vector<int32_t> h(count);
+        DRGB_CUDA(c, cudaMemcpyAsync(h.data(), fail_count, size_t(count) * 4, cudaMemcpyDeviceToHost, st));
+        DRGB_CUDA(c, cudaStreamSynchronize(st));
+        const size_t part = knn_bytes < knn_rescan_part_bytes() ? knn_bytes : knn_rescan_part_bytes();
+        for (int b = 0; b < count; ++b) {
+            const int64_t off = offsets[b], nb = offsets[b + 1] - off;
+            const int64_t cnt = h[b] < nb ? h[b] : nb;
+            if (cnt <= 0) continue;
+            rc = launch_knn_exact_rows_n(c, X_cat + off * d, nb, d, k, fail_rows + off, fail_count + b, cnt,
+                                         idx + off * k, dist + off * k, st, knn_scratch, part);
+            if (rc) return rc;
+        }
     }
     globalize_idx_kernel<<<grid_for(N, 256, c->num_sms * 8), 256, 0, st>>>(idx, N, k, count, d_off);
     DRGB_CHECK_LAUNCH(c);

@@ -241,7 +241,13 @@ int launch_knn_exact_rows(Ctx* c, const float* X, int64_t n, int d, int k, const
     int32_t cnt32 = 0;
     DRGB_CUDA(c, cudaMemcpyAsync(&cnt32, n_rows_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     DRGB_CUDA(c, cudaStreamSynchronize(st));
-    const int64_t cnt = cnt32 < max_rows ? cnt32 : max_rows;
+    return launch_knn_exact_rows_n(c, X, n, d, k, rows32, n_rows_dev, cnt32 < max_rows ? cnt32 : max_rows, idx_out,
+                                   dist_out, st, part_scratch, part_bytes);
+}
+
+int launch_knn_exact_rows_n(Ctx* c, const float* X, int64_t n, int d, int k, const int32_t* rows32,
+                            const int32_t* n_rows_dev, int64_t cnt, int32_t* idx_out, float* dist_out,
+                            cudaStream_t st, void* part_scratch, size_t part_bytes) {
     if (cnt <= 0) return DRGB_OK;
     const int row_blocks = int((cnt + KNN_THREADS - 1) / KNN_THREADS);
     int64_t C = (8 * int64_t(c->num_sms) + row_blocks - 1) / row_blocks;
@@ -415,9 +421,10 @@ size_t knn_scratch_bytes(int64_t n, int d, int k, int mode) {
 }
 
 int knn_run(Ctx* c, const float* X, int64_t n, int d, int k, int mode, int32_t* idx_out, float* dist_out,
-            cudaStream_t st, void* scratch) {
+            cudaStream_t st, void* scratch, int32_t* defer_rows, int32_t* defer_count) {
     const int m = knn_resolve_mode(n, d, k, mode);
-    if (m == 2 || m == 3) return knn_tc(c, X, n, d, k, m == 3, idx_out, dist_out, st, scratch);
+    if (m == 2 || m == 3)
+        return knn_tc(c, X, n, d, k, m == 3, idx_out, dist_out, st, scratch, defer_rows, defer_count);
     if (m != 1) return set_error(c, DRGB_ERR_INVALID, "knn_graph: bad mode %d", mode);
     return launch_knn_exact(c, X, n, d, k, nullptr, n, idx_out, dist_out, true, st);
 }

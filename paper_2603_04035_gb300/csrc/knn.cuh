@@ -21,6 +21,10 @@ int launch_knn_exact(Ctx* c, const float* X, int64_t n, int d, int k, const int6
 int launch_knn_exact_rows(Ctx* c, const float* X, int64_t n, int d, int k, const int32_t* rows32,
                           const int32_t* n_rows_dev, int64_t max_rows, int32_t* idx_out,
                           float* dist_out, cudaStream_t st, void* part_scratch, size_t part_bytes);
+// The same scan with the row count `cnt` known on the host (no synchronisation).
+int launch_knn_exact_rows_n(Ctx* c, const float* X, int64_t n, int d, int k, const int32_t* rows32,
+                            const int32_t* n_rows_dev, int64_t cnt, int32_t* idx_out, float* dist_out,
+                            cudaStream_t st, void* part_scratch, size_t part_bytes);
 // Exact FP32 k-NN of the nq rows of Q among the n rows of X (no self exclusion).
 int launch_knn_query(Ctx* c, const float* Q, int64_t nq, const float* X, int64_t n, int d, int k,
                      int32_t* idx_out, float* dist_out, cudaStream_t st);
@@ -33,8 +37,14 @@ int launch_nonfinite_scan(Ctx* c, const float* X, int64_t count, cudaStream_t st
 bool knn_tc_preferred(int64_t n, int d, int k);
 size_t knn_tc_scratch_bytes(int64_t n, int d);
 // `scratch` must hold knn_tc_scratch_bytes(n, d) bytes (256-byte aligned).
+// With defer_rows/defer_count (device; *defer_count zeroed by the caller) the
+// uncertified rows are appended there (row indices of X) and not re-scanned:
+// the caller re-scans them later (launch_knn_exact_rows_n), which lets many
+// k-NN runs be enqueued without a host synchronisation.
 int knn_tc(Ctx* c, const float* X, int64_t n, int d, int k, bool f16, int32_t* idx_out, float* dist_out,
-           cudaStream_t st, void* scratch);
+           cudaStream_t st, void* scratch, int32_t* defer_rows = nullptr, int32_t* defer_count = nullptr);
+// Bytes of scratch a deferred re-scan may use for its partial lists.
+size_t knn_rescan_part_bytes();
 
 // Spatial order for the tensor-core k-NN (knn_order.cu): K cells from
 // farthest-point pivots; perm[p] = point at position p (p < n), cell c holds
@@ -48,7 +58,9 @@ int knn_order(Ctx* c, const float* X, int64_t n, int d, int K, int32_t* perm, in
 // knn_scratch_bytes(n, d, k, mode) bytes (may be null when that is 0).
 int knn_resolve_mode(int64_t n, int d, int k, int mode);
 size_t knn_scratch_bytes(int64_t n, int d, int k, int mode);
+// defer_rows/defer_count: as for knn_tc (the exact-scan modes leave no
+// uncertified rows).
 int knn_run(Ctx* c, const float* X, int64_t n, int d, int k, int mode, int32_t* idx_out, float* dist_out,
-            cudaStream_t st, void* scratch);
+            cudaStream_t st, void* scratch, int32_t* defer_rows = nullptr, int32_t* defer_count = nullptr);
 
 }  // namespace drgb

@@ -957,9 +957,11 @@ size_t knn_tc_scratch_bytes(int64_t n, int d) {
     return tc_scratch_bytes(n, d, n_pad, TC_COLSUM_BLOCKS);
 }
 
+size_t knn_rescan_part_bytes() { return TC_PART_BYTES; }
+
 template <bool F16>
 static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t* idx_out, float* dist_out,
-                       cudaStream_t st, void* scratch) {
+                       cudaStream_t st, void* scratch, int32_t* defer_rows, int32_t* defer_count) {
     if (d + 3 > TC_K || k >= TC_KP)
         return set_error(c, DRGB_ERR_INVALID, "knn_graph: tensor-core mode needs d <= %d and k < %d", TC_K - 3,
                          TC_KP);
@@ -1038,9 +1040,10 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
     if ((rc = stage_mark(c, 7, st))) return rc;
 
     tc_rerank_kernel<F16><<<grid_for(n, RR_WARPS, c->num_sms * 8), RR_WARPS * 32, 0, st>>>(
-        Xp, perm, n, d, k, cand_idx, cand_s, norm, resid, maxbits, lbstop, idx_out, dist_out, fail_rows,
-        fail_count);
+        Xp, perm, n, d, k, cand_idx, cand_s, norm, resid, maxbits, lbstop, idx_out, dist_out,
+        defer_rows ? defer_rows : fail_rows, defer_count ? defer_count : fail_count);
     DRGB_CHECK_LAUNCH(c);
+    if (defer_rows) return DRGB_OK;  // the caller re-scans the uncertified rows
     // exact FP32 scan of the uncertified rows (row list and count on the device)
     DRGB_CUDA(c, cudaMemcpyAsync(c->d_counter, fail_count, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
     rc = launch_knn_exact_rows(c, X, n, d, k, fail_rows, fail_count, n, idx_out, dist_out, st, part,
@@ -1049,9 +1052,11 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
 }
 
 int knn_tc(Ctx* c, const float* X, int64_t n, int d, int k, bool f16, int32_t* idx_out, float* dist_out,
-           cudaStream_t st, void* scratch) {
-    return f16 ? knn_tc_impl<true>(c, X, n, d, k, idx_out, dist_out, st, scratch)
-               : knn_tc_impl<false>(c, X, n, d, k, idx_out, dist_out, st, scratch);
+           cudaStream_t st, void* scratch, int32_t* defer_rows, int32_t* defer_count) {
+    if ((defer_rows == nullptr) != (defer_count == nullptr))
+        return set_error(c, DRGB_ERR_INVALID, "knn: deferred re-scan needs both the row list and its count");
+    return f16 ? knn_tc_impl<true>(c, X, n, d, k, idx_out, dist_out, st, scratch, defer_rows, defer_count)
+               : knn_tc_impl<false>(c, X, n, d, k, idx_out, dist_out, st, scratch, defer_rows, defer_count);
 }
 
 }  // namespace drgb
