@@ -206,6 +206,17 @@ def batched(count: int = 256, d: int = 50, seed: int = 0, lo: float = 1e3, hi: f
     return np.ascontiguousarray(np.concatenate(parts, axis=0)), offsets
 
 
+def sheet(n: int, d: int = 50, seed: int = 0, aspect: float = 3.0, noise: float = 0.01):
+    """Points on a flat 2-D sheet [0, aspect] x [0, 1] placed in d dimensions
+    by a random orthonormal map, plus isotropic Gaussian noise: a connected
+    k-NN graph with a known low-dimensional structure.  Returns (X, uv)."""
+    g = _rng(seed, 7)
+    uv = g.uniform(0.0, 1.0, size=(n, 2)) * np.array([aspect, 1.0])
+    Q, _ = np.linalg.qr(g.normal(size=(d, 2)))
+    X = uv @ Q.T + noise * g.normal(size=(n, d))
+    return X.astype(np.float32), uv
+
+
 def config_small(seed: int = 0):
     """The 2,000-point, 50-d, 10-cluster workload."""
     return mixture(2000, 50, 10, seed)

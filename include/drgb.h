@@ -67,6 +67,10 @@ typedef struct drgb_params {
 /* drgb_params.flags: time the epoch schedules on the actual graph before the
  * loop and keep the fastest (results are identical for every schedule). */
 #define DRGB_FLAG_AUTOTUNE 1
+/* drgb_params.flags: start from the spectral layout of the fuzzy graph
+ * (drgb_spectral_init, with init_range and seed_init) instead of the uniform
+ * one; the fit then synchronises its stream during the initialisation. */
+#define DRGB_FLAG_INIT_SPECTRAL 2
 
 /* Called after each epoch by fit_transform (Section 2.1, epoch_callback).
  * Y_dev is the current device embedding (n x 2, valid during the call only);
@@ -241,6 +245,28 @@ int drgb_find_ab(float spread, float min_dist, float* a, float* b);
  * Y is n x 2 FP32 (8-byte aligned).  Errors: DRGB_ERR_INVALID. */
 int drgb_init_embedding(drgb_ctx* ctx, int64_t n, float init_range, uint64_t seed, float* Y,
                         void* stream);
+
+/* Spectral initial layout (the UMAP optimisation the paper times in Section 3
+ * starts from it): the two eigenvectors of the normalised adjacency
+ * M = D^-1/2 W D^-1/2 of the fuzzy graph (W = the CSR's weights w, d_i their
+ * row sums) with the largest eigenvalues after the trivial D^1/2 1
+ * (eigenvalue 1), i.e. the smallest non-trivial ones of the normalised graph
+ * Laplacian.  Each is signed so that its entry of largest magnitude (lowest
+ * index among equal magnitudes) is positive, both are scaled by one factor
+ * so that the largest |Y| is init_range, and each coordinate gets a jitter of
+ * init_range * 1e-5 * (2u - 1), u from words 2, 3 of the initialisation
+ * stream (Philox4x32-10, counter (i, 0, 0, 1), key = seed).
+ *   row_ptr, col, w  the symmetric CSR graph (device, n + 1 / nnz entries)
+ *   Y_out            n x 2 FP32 (device, 8-byte aligned)
+ *   eigvals          optional host array of 3: the leading eigenvalues of M
+ * Computed in FP32 by Chebyshev-filtered subspace iteration on 8 vectors
+ * until the residual |M v - lambda v| of the three leading pairs is below
+ * 1e-5, or for at most 400 subspace steps (then the current vectors are
+ * used); on a disconnected graph eigenvalue 1 repeats and the layout is some
+ * pair of vectors of its eigenspace.  Synchronous.  Errors: DRGB_ERR_INVALID
+ * (NULL, misaligned, n < 9, init_range <= 0), DRGB_ERR_CUDA. */
+int drgb_spectral_init(drgb_ctx* ctx, const int32_t* row_ptr, const int32_t* col, const float* w, int64_t n,
+                       float init_range, uint64_t seed, float* Y_out, double* eigvals, void* stream);
 
 /* ---------------------------------------------------------- SGD epoch */
 

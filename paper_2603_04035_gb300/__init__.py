@@ -33,7 +33,7 @@ from ._lib import MAX_K, Params  # noqa: F401
 
 __all__ = ["DrgbError", "Graph", "UMAP", "knn_graph", "fuzzy_weights", "find_ab",
            "init_embedding", "embed_epoch", "embed_epochs", "fit_transform", "eval_recall",
-           "eval_trust", "eval_recall_heldout", "default_params", "context", "knn_uncertified", "launch_count",
+           "eval_trust", "eval_recall_heldout", "spectral_init", "default_params", "context", "knn_uncertified", "launch_count",
            "set_profiling", "stage_times", "set_tuning", "get_tuning", "set_tuning_cache",
            "tuning_cache_lookup", "tuning_cache_store", "knn_tiles", "fit_transform_batched",
            "autotune_epoch", "mlp_param_count", "mlp_init", "mlp_sample", "mlp_grad", "mlp_train",
@@ -256,6 +256,18 @@ def _graph_args(g: Graph):
             _ptr(_cuda(g.q, torch.int32, "q")))
 
 
+def spectral_init(g: Graph, init_range: float = 10.0, seed: int = 1):
+    """Spectral initial layout of the graph (n x 2 FP32) and the three leading
+    eigenvalues of its normalised adjacency."""
+    n = g.n
+    Y = torch.empty((n, 2), dtype=torch.float32, device=g.row_ptr.device)
+    ev = (C.c_double * 3)()
+    ctx = context(Y.device.index)
+    _check(_lib.load().drgb_spectral_init(ctx, _ptr(g.row_ptr), _ptr(g.col), _ptr(g.w), n, init_range, seed,
+                                          _ptr(Y), ev, _stream(Y.device)), ctx)
+    return Y, [ev[0], ev[1], ev[2]]
+
+
 def embed_epoch(Y: torch.Tensor, g: Graph, a: float, b: float, lr: float, neg: int, epoch: int,
                 seed: int, out: torch.Tensor | None = None) -> torch.Tensor:
     Y = _cuda(Y, torch.float32, "Y", 2)
@@ -294,11 +306,17 @@ def _params(**kw) -> Params:
 
 
 def fit_transform(X: torch.Tensor, epoch_callback=None, out: torch.Tensor | None = None,
-                  **params) -> torch.Tensor:
-    """Embed the rows of X (n x d FP32, CUDA) into n x 2; synchronous."""
+                  init: str = "random", **params) -> torch.Tensor:
+    """Embed the rows of X (n x d FP32, CUDA) into n x 2; synchronous.
+    init: "random" (uniform in [-init_range, init_range]^2) or "spectral"
+    (the spectral layout of the fuzzy graph, see spectral_init)."""
     X = _cuda(X, torch.float32, "X", 2)
     n, d = X.shape
+    if init not in ("random", "spectral"):
+        raise ValueError(f"init must be 'random' or 'spectral', not {init!r}")
     p = _params(**params)
+    if init == "spectral":
+        p.flags |= _lib.FLAG_INIT_SPECTRAL
     Y = torch.empty((n, 2), dtype=torch.float32, device=X.device) if out is None else out
     ctx = context(X.device.index)
     if epoch_callback is None:

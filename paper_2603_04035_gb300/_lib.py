@@ -22,6 +22,7 @@ STATIC_SCRATCH_BYTES = 16 << 20
 TUNE_EPOCH_WARPS = 1
 TUNE_EPOCH_PIPE = 2
 FLAG_AUTOTUNE = 1
+FLAG_INIT_SPECTRAL = 2
 
 ERROR_NAMES = {ERR_INVALID: "invalid argument", ERR_WORKSPACE: "workspace too small",
                ERR_CUDA: "CUDA error", ERR_TIMEOUT: "device timeout",
@@ -85,6 +86,7 @@ SIGNATURES = {
                                       C.POINTER(C.c_int32), C.POINTER(C.c_float), vp]),
     "drgb_eval_recall": (C.c_int, [vp, vp, vp, i64, i32, i32, i64, C.POINTER(C.c_double), vp]),
     "drgb_eval_trust": (C.c_int, [vp, vp, vp, i64, i32, i32, i64, C.POINTER(C.c_double), vp]),
+    "drgb_spectral_init": (C.c_int, [vp, vp, vp, vp, i64, f32, u64, vp, C.POINTER(C.c_double), vp]),
     "drgb_eval_recall_heldout": (C.c_int, [vp, vp, vp, i64, vp, vp, i64, i32, i32, i64, C.POINTER(C.c_double),
                                            vp]),
 }

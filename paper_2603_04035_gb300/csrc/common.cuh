@@ -144,7 +144,7 @@ inline void philox_round_keys(uint32_t k0, uint32_t k1, uint32_t* rk) {
     }
 }
 
-enum : uint32_t { TAG_NEGATIVE = 0u, TAG_INIT = 1u, TAG_MLP = 2u };
+enum : uint32_t { TAG_NEGATIVE = 0u, TAG_INIT = 1u, TAG_MLP = 2u, TAG_SPECTRAL = 3u };
 
 // floor(u * n / 2^32): maps a uniform 32-bit word onto [0, n).
 __device__ __forceinline__ int64_t mulshift_index(uint32_t u, int64_t n) {

@@ -77,8 +77,8 @@ __device__ __forceinline__ float pow_pos(float d, float b) { return hw_ex2(b * h
 
 static constexpr unsigned FULL = 0xffffffffu;
 
-// Gather of one point of Y^(t).  (Read-only-path and L1 evict-last loads
-// were measured and made no difference.)
+// Read of one point of Y^(t).  (Read-only-path and L1 evict-last loads were
+// measured and made no difference.)
 __device__ __forceinline__ float2 load_y(const float2* p) { return *p; }
 
 // Instance-local view of a row: rows [off, off + n) with entries from eoff on,
@@ -91,13 +91,23 @@ struct RowInst {
     uint32_t k0, k1;
 };
 
+// What changes from one epoch to the next: the positions read and written,
+// the learning rate and the epoch number.
+struct EpochStep {
+    const float2* __restrict__ Y_in;
+    float2* __restrict__ Y_out;
+    float lr;
+    uint32_t t;
+};
+
 // Negative words of entry e32 at epoch t, group g (negatives 4g .. 4g+3):
 // Philox4x32-10 at counter (e, t, g, 0) under the row's key.  A single
 // instance takes the precomputed round keys from the kernel parameters.
 template <bool BATCHED>
-__device__ __forceinline__ U4 negative_words(const EpochArgs& A, const RowInst& R, uint32_t e32, uint32_t g) {
-    if (BATCHED) return philox4x32_10(U4{e32, A.t, g, TAG_NEGATIVE}, R.k0, R.k1);
-    return philox4x32_10_rk(U4{e32, A.t, g, TAG_NEGATIVE}, A.rk);
+__device__ __forceinline__ U4 negative_words(const EpochArgs& A, const EpochStep& S, const RowInst& R, uint32_t e32,
+                                             uint32_t g) {
+    if (BATCHED) return philox4x32_10(U4{e32, S.t, g, TAG_NEGATIVE}, R.k0, R.k1);
+    return philox4x32_10_rk(U4{e32, S.t, g, TAG_NEGATIVE}, A.rk);
 }
 
 // Force on head i from one active entry e = (i, j) and its negatives, summed in
@@ -126,7 +136,8 @@ struct EntryInputs {
 };
 
 template <int NEG, bool BATCHED>
-__device__ __forceinline__ void fetch_entry(const EpochArgs& A, const RowInst& R, bool valid, int32_t e, int32_t j,
+__device__ __forceinline__ void fetch_entry(const EpochArgs& A, const EpochStep& S, const RowInst& R, bool valid,
+                                            int32_t e, int32_t j,
                                             int32_t i, int64_t h_lo, int64_t h_hi, int lane,
                                             EntryInputs<NEG>& in) {
     constexpr int NP = EntryInputs<NEG>::NP;
@@ -137,13 +148,13 @@ __device__ __forceinline__ void fetch_entry(const EpochArgs& A, const RowInst& R
     in.e = e;
     in.i = ok ? i : -1 - lane;
     const int32_t ii = ok ? i : int32_t(h_lo);
-    in.yi = load_y(A.Y_in + ii);
-    in.yj = load_y(A.Y_in + (ok ? j : ii));
+    in.yi = load_y(S.Y_in + ii);
+    in.yj = load_y(S.Y_in + (ok ? j : ii));
     const uint32_t n32 = R.n, i32 = uint32_t(ii - R.off), e32 = uint32_t(e - R.eoff);
-    const float2* Yb = A.Y_in + R.off;
+    const float2* Yb = S.Y_in + R.off;
     U4 r0{0u, 0u, 0u, 0u}, r1{0u, 0u, 0u, 0u};
-    if (NP > 0 && neg > 0) r0 = negative_words<BATCHED>(A, R, e32, 0u);
-    if (NP > 4 && neg > 4) r1 = negative_words<BATCHED>(A, R, e32, 1u);
+    if (NP > 0 && neg > 0) r0 = negative_words<BATCHED>(A, S, R, e32, 0u);
+    if (NP > 4 && neg > 4) r1 = negative_words<BATCHED>(A, S, R, e32, 1u);
     const uint32_t u[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
 #pragma unroll
     for (int w = 0; w < NP; ++w) {
@@ -154,8 +165,8 @@ __device__ __forceinline__ void fetch_entry(const EpochArgs& A, const RowInst& R
 }
 
 template <int NEG, bool BATCHED>
-__device__ __forceinline__ float2 entry_math(const EpochArgs& A, const RowInst& R, const EntryInputs<NEG>& in,
-                                             float two_ab, float two_b) {
+__device__ __forceinline__ float2 entry_math(const EpochArgs& A, const EpochStep& S, const RowInst& R,
+                                             const EntryInputs<NEG>& in, float two_ab, float two_b) {
     constexpr int NP = EntryInputs<NEG>::NP;
     const float2 yi = in.yi;
     float gx = 0.f, gy = 0.f;
@@ -180,9 +191,9 @@ __device__ __forceinline__ float2 entry_math(const EpochArgs& A, const RowInst& 
     if (NEG < 0 || NEG > 8) {
         const int neg = NEG >= 0 ? NEG : A.neg;
         const uint32_t n32 = R.n, i32 = uint32_t(in.i - R.off), e32 = uint32_t(in.e - R.eoff);
-        const float2* Yb = A.Y_in + R.off;
+        const float2* Yb = S.Y_in + R.off;
         for (int g = 2; g * 4 < neg; ++g) {
-            const U4 r = negative_words<BATCHED>(A, R, e32, uint32_t(g));
+            const U4 r = negative_words<BATCHED>(A, S, R, e32, uint32_t(g));
             const uint32_t v[4] = {r.x, r.y, r.z, r.w};
             float2 yg[4];
 #pragma unroll
@@ -319,24 +330,37 @@ __device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol
 // CSR chunks (of 32 entries) a warp loads at once before testing them.  The
 // window's CSR words are streamed in bursts so that several loads are in
 // flight per lane; the active entries of a burst wait in a per-warp queue of
-// at most 31 + 32 * EPOCH_BURST entries.  The queue is kept this small on
+// at most 31 + 32 * burst entries.  The queue is kept this small on
 // purpose: shared memory left unused goes to the L1 cache, and the random
 // 8-byte gathers of Y run at about 2.5x the rate with the largest L1 (the
 // misses in flight per SM are bounded by L1 capacity).
 static constexpr int EPOCH_BURST = 4;
-static constexpr int EPOCH_QCAP = 32 * EPOCH_BURST + 32;
+constexpr int epoch_qcap(int burst) { return 32 * burst + 32; }
 // Warps per SM each form's register budget is sized for: the pipelined form
 // holds two groups' gathered points (about 80 registers a thread), the flat
 // form one (about 48).
 static constexpr int epoch_warps_per_sm(bool pipe) { return pipe ? 24 : 40; }
 
-// One warp per window (grid-stride over windows).  No row crosses a window, so
-// the warp writes the final Y' of every row of its window.
+// Where a window's CSR words come from: global memory, streamed with
+// evict-first loads (they are read once per epoch, so L2 keeps the gathered
+// positions Y instead).
+struct CsrGlobal {
+    const uint32_t* __restrict__ q;
+    const int32_t* __restrict__ col;
+    const int32_t* __restrict__ row_of;
+    __device__ __forceinline__ void load(int32_t e, bool in, uint32_t& qv, int32_t& jv, int32_t& hv) const {
+        qv = in ? __ldcs(q + e) : 0u;  // q = 0 never fires
+        jv = in ? __ldcs(col + e) : 0;
+        hv = in ? __ldcs(row_of + e) : -1;
+    }
+};
+// One window W of epoch S, by one warp.  No row crosses a window, so the warp
+// writes the final Y' of every row of the window.
 //
-// The warp streams the window's CSR in bursts of EPOCH_BURST chunks of 32
-// entries (one entry per lane and chunk, coalesced) and appends each burst's
-// active entries to its queue, in entry order.  Every 32 waiting entries form
-// a group: one entry per lane, its negatives drawn and its points gathered
+// The warp streams the window's CSR in bursts of BURST chunks of 32 entries
+// (one entry per lane and chunk, coalesced) and appends each burst's active
+// entries to its queue, in entry order.  Every 32 waiting entries form a
+// group: one entry per lane, its negatives drawn and its points gathered
 // (fetch), then its force computed and the group's terms added by head
 // (segmented scan, carry between groups).  The window's last group may be
 // partial.
@@ -348,30 +372,194 @@ static constexpr int epoch_warps_per_sm(bool pipe) { return pipe ? 24 : 40; }
 // fetched, and latency is hidden by more warps per SM (for grids with many
 // windows).  Both forms form the same groups and add in the same order, so
 // they give the same bits.
-template <bool BATCHED, int NEG, int NW, bool PIPE>
-__global__ void __launch_bounds__(NW * 32, epoch_warps_per_sm(PIPE) / NW)
-    epoch_force_kernel(const __grid_constant__ EpochArgs A) {
-    __shared__ int2 s_ej[NW][EPOCH_QCAP];     // (entry, tail) of the waiting active entries
-    __shared__ int32_t s_hd[NW][EPOCH_QCAP];  // their heads
-    // carry of each warp: running sum of the previous group's last head and
-    // that head's position; the head itself (-1 when none)
-    __shared__ float4 s_carry[NW];
-    __shared__ int32_t s_chead[NW];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int2* act_w = s_ej[w];
-    int32_t* head_w = s_hd[w];
+template <bool BATCHED, int NEG, bool PIPE, int BURST, class Csr>
+__device__ __forceinline__ void epoch_window(const EpochArgs& A, const EpochStep& S, const Csr& csr, int32_t W,
+                                             int lane, int2* act_w, int32_t* head_w, float4* carry_w,
+                                             int32_t* chead_w, float two_ab, float two_b) {
     const unsigned lt_mask = (1u << lane) - 1u;
-    const float two_ab = 2.0f * A.a * A.b, two_b = 2.0f * A.b;
-    grid_dep_launch();
-    int32_t nnz = 0, n_win = 0;
+    const int32_t rA = A.win_row[W], rB = A.win_row[W + 1];
+    if (rA >= rB) return;  // a long row started in an earlier window covers this one
+    RowInst R{0, A.neg_n ? A.neg_n : uint32_t(A.n), 0, A.k0, A.k1};
+    int64_t h_lo = A.row_begin, h_hi = A.n;  // rows a head may take (the instance's rows)
     if (BATCHED) {
+        int lo = 0, hi = A.count - 1;  // the instance whose windows hold W
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (A.win_base[mid] <= W) lo = mid; else hi = mid - 1;
+        }
+        R.off = A.inst_off[lo];
+        R.n = uint32_t(A.inst_off[lo + 1] - R.off);
+        R.eoff = A.inst_eoff[lo];
+        R.k0 = uint32_t(A.inst_seed[lo]);
+        R.k1 = uint32_t(A.inst_seed[lo] >> 32);
+        h_lo = R.off;
+        h_hi = R.off + R.n;
+    }
+    if (rA < h_lo || rB > h_hi) {
+        if (lane == 0) report_status(A.status, DRGB_ERR_INVALID);
+        return;
+    }
+    const int32_t es = A.row_ptr[rA - A.row_begin], ee = A.row_ptr[rB - A.row_begin];
+    // Negatives and gathers of `cnt` waiting entries from queue position p.
+    auto fetch_group = [&](int p, int cnt, EntryInputs<NEG>& in) {
+        const bool v = lane < cnt;
+        const int2 ej = v ? act_w[p + lane] : make_int2(es, 0);
+        fetch_entry<NEG, BATCHED>(A, S, R, v, ej.x, ej.y, v ? head_w[p + lane] : -1, h_lo, h_hi, lane, in);
+    };
+    // Forces of a fetched group of `cnt` entries, added by head.
+    auto finish_group = [&](const EntryInputs<NEG>& cur, int cnt) {
+        float fx = 0.f, fy = 0.f;
+        if (cur.ok) {
+            const float2 f = entry_math<NEG, BATCHED>(A, S, R, cur, two_ab, two_b);
+            fx = f.x;
+            fy = f.y;
+        }
+        const int32_t i = cur.i;
+        const int32_t chead = *chead_w;
+        // the carried head ends unless this group starts with it
+        if (chead >= 0 && lane == 0 && i != chead) {
+            const float4 cv = *carry_w;
+            S.Y_out[chead] = make_float2(fmaf(S.lr, 0.f + cv.x, cv.z), fmaf(S.lr, 0.f + cv.y, cv.w));
+        }
+        // segmented inclusive scan over runs of equal heads
+        const int32_t i_prev = __shfl_up_sync(FULL, i, 1);
+        const unsigned starts = __ballot_sync(FULL, lane == 0 || i_prev != i);
+        const int seg0 = 31 - __clz(starts & (FULL >> (31 - lane)));
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const float ox = __shfl_up_sync(FULL, fx, d), oy = __shfl_up_sync(FULL, fy, d);
+            if (lane - d >= seg0) {
+                fx = ox + fx;
+                fy = oy + fy;
+            }
+        }
+        if (seg0 == 0 && i == chead) {
+            const float4 cv = *carry_w;
+            fx = cv.x + fx;
+            fy = cv.y + fy;
+        }
+        // a run that ends inside the group is the row's last: write it; the
+        // group's last run is carried
+        const int32_t i_next = __shfl_down_sync(FULL, i, 1);
+        if (cur.ok && lane < cnt - 1 && i_next != i)
+            S.Y_out[i] = make_float2(fmaf(S.lr, 0.f + fx, cur.yi.x), fmaf(S.lr, 0.f + fy, cur.yi.y));
+        __syncwarp();
+        if (lane == cnt - 1) {
+            *carry_w = make_float4(fx, fy, cur.yi.x, cur.yi.y);
+            *chead_w = cur.ok ? i : -1;
+        }
+        __syncwarp();
+    };
+    EntryInputs<NEG> held;  // PIPE: the fetched group waiting for its forces
+    int held_cnt = 0;
+    int qn = 0;             // active entries waiting at the front of the queue
+    // (a window whose rows are all empty still takes one, empty, burst)
+    for (int32_t c0 = es; c0 == es || c0 < ee; c0 += 32 * BURST) {
+        // the burst's CSR words, all loads in flight before any test
+        uint32_t qv[BURST];
+        int32_t jv[BURST], hv[BURST];
+#pragma unroll
+        for (int b = 0; b < BURST; ++b) {
+            const int32_t e = c0 + 32 * b + lane;
+            csr.load(e, e < ee, qv[b], jv[b], hv[b]);
+        }
+        if (PIPE && held_cnt) {  // the previous burst's last group, while the loads fly
+            finish_group(held, held_cnt);
+            held_cnt = 0;
+        }
+#pragma unroll
+        for (int b = 0; b < BURST; ++b) {
+            // floor((t+1) q / 2^24) > floor(t q / 2^24)  <=>  (t q mod 2^24) + q >= 2^24
+            const bool act = qv[b] >= 0x1000000u - ((S.t * qv[b]) & 0xFFFFFFu);
+            const unsigned m = __ballot_sync(FULL, act);
+            if (act) {
+                const int pos = qn + __popc(m & lt_mask);
+                act_w[pos] = make_int2(c0 + 32 * b + lane, jv[b]);
+                head_w[pos] = hv[b];
+            }
+            qn += __popc(m);
+        }
+        __syncwarp();
+        if (c0 == es) {
+            // every row of the window first gets Y + lr * 0; rows with active
+            // entries are rewritten with their force below.  The wait for the
+            // previous epoch comes here, after the first burst has been loaded
+            // and tested.
+            grid_dep_wait();
+            for (int64_t r = rA + lane; r < rB; r += 32) {
+                const float2 y = load_y(S.Y_in + r);
+                S.Y_out[r] = make_float2(fmaf(S.lr, 0.f, y.x), fmaf(S.lr, 0.f, y.y));
+            }
+            if (lane == 0) *chead_w = -1;
+            __syncwarp();
+        }
+        const bool last = c0 + 32 * BURST >= ee;
+        const int ng = last ? (qn + 31) / 32 : qn / 32;
+        for (int g = 0; g < ng; ++g) {
+            const int cnt = qn - 32 * g < 32 ? qn - 32 * g : 32;
+            EntryInputs<NEG> in;
+            fetch_group(32 * g, cnt, in);
+            if (PIPE) {
+                if (held_cnt) finish_group(held, held_cnt);
+                held = in;
+                held_cnt = cnt;
+            } else {
+                finish_group(in, cnt);
+            }
+        }
+        // move the waiting partial group to the front
+        const int left = qn - 32 * ng > 0 ? qn - 32 * ng : 0;
+        int2 lv = make_int2(0, 0);
+        int32_t lh = -1;
+        if (lane < left) {
+            lv = act_w[32 * ng + lane];
+            lh = head_w[32 * ng + lane];
+        }
+        __syncwarp();
+        if (lane < left) {
+            act_w[lane] = lv;
+            head_w[lane] = lh;
+        }
+        qn = left;
+        __syncwarp();
+    }
+    if (PIPE && held_cnt) finish_group(held, held_cnt);
+    if (lane == 0 && *chead_w >= 0) {
+        const float4 cv = *carry_w;
+        S.Y_out[*chead_w] = make_float2(fmaf(S.lr, 0.f + cv.x, cv.z), fmaf(S.lr, 0.f + cv.y, cv.w));
+    }
+    __syncwarp();
+}
+
+// Entries and windows of the call, checked against the prepared tables.
+__device__ __forceinline__ bool epoch_extent(const EpochArgs& A, int32_t& nnz, int32_t& n_win) {
+    if (A.count > 0) {
         nnz = A.inst_eoff[A.count];
         n_win = A.win_base[A.count];
     } else {
         nnz = A.row_ptr[A.n - A.row_begin];
         n_win = (nnz + EPOCH_WIN - 1) / EPOCH_WIN;
     }
-    if (nnz < 0 || nnz > A.nnz_cap || n_win > A.win_cap) {
+    return nnz >= 0 && nnz <= A.nnz_cap && n_win <= A.win_cap;
+}
+
+// One epoch: one warp per window (grid-stride over windows).
+template <bool BATCHED, int NEG, int NW, bool PIPE>
+__global__ void __launch_bounds__(NW * 32, epoch_warps_per_sm(PIPE) / NW)
+    epoch_force_kernel(const __grid_constant__ EpochArgs A) {
+    constexpr int QCAP = epoch_qcap(EPOCH_BURST);
+    __shared__ int2 s_ej[NW][QCAP];     // (entry, tail) of the waiting active entries
+    __shared__ int32_t s_hd[NW][QCAP];  // their heads
+    // carry of each warp: running sum of the previous group's last head and
+    // that head's position; the head itself (-1 when none)
+    __shared__ float4 s_carry[NW];
+    __shared__ int32_t s_chead[NW];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float two_ab = 2.0f * A.a * A.b, two_b = 2.0f * A.b;
+    const EpochStep S{A.Y_in, A.Y_out, A.lr, A.t};
+    grid_dep_launch();
+    int32_t nnz = 0, n_win = 0;
+    if (!epoch_extent(A, nnz, n_win)) {
         if (threadIdx.x == 0 && blockIdx.x == 0) report_status(A.status, DRGB_ERR_INVALID);
         return;
     }
@@ -384,166 +572,10 @@ __global__ void __launch_bounds__(NW * 32, epoch_warps_per_sm(PIPE) / NW)
         }
         return;
     }
-    const RowInst R1{0, A.neg_n ? A.neg_n : uint32_t(A.n), 0, A.k0, A.k1};
-    for (int32_t W = int32_t(blockIdx.x) * NW + w; W < n_win; W += int32_t(gridDim.x) * NW) {
-        const int32_t rA = A.win_row[W], rB = A.win_row[W + 1];
-        if (rA >= rB) continue;  // a long row started in an earlier window covers this one
-        RowInst R = R1;
-        int64_t h_lo = A.row_begin, h_hi = A.n;  // rows a head may take (the instance's rows)
-        if (BATCHED) {
-            int lo = 0, hi = A.count - 1;  // the instance whose windows hold W
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (A.win_base[mid] <= W) lo = mid; else hi = mid - 1;
-            }
-            R.off = A.inst_off[lo];
-            R.n = uint32_t(A.inst_off[lo + 1] - R.off);
-            R.eoff = A.inst_eoff[lo];
-            R.k0 = uint32_t(A.inst_seed[lo]);
-            R.k1 = uint32_t(A.inst_seed[lo] >> 32);
-            h_lo = R.off;
-            h_hi = R.off + R.n;
-        }
-        if (rA < h_lo || rB > h_hi) {
-            if (lane == 0) report_status(A.status, DRGB_ERR_INVALID);
-            continue;
-        }
-        const int32_t es = A.row_ptr[rA - A.row_begin], ee = A.row_ptr[rB - A.row_begin];
-        // Negatives and gathers of `cnt` waiting entries from queue position p.
-        auto fetch_group = [&](int p, int cnt, EntryInputs<NEG>& in) {
-            const bool v = lane < cnt;
-            const int2 ej = v ? act_w[p + lane] : make_int2(es, 0);
-            fetch_entry<NEG, BATCHED>(A, R, v, ej.x, ej.y, v ? head_w[p + lane] : -1, h_lo, h_hi, lane, in);
-        };
-        // Forces of a fetched group of `cnt` entries, added by head.
-        auto finish_group = [&](const EntryInputs<NEG>& cur, int cnt) {
-            float fx = 0.f, fy = 0.f;
-            if (cur.ok) {
-                const float2 f = entry_math<NEG, BATCHED>(A, R, cur, two_ab, two_b);
-                fx = f.x;
-                fy = f.y;
-            }
-            const int32_t i = cur.i;
-            const int32_t chead = s_chead[w];
-            // the carried head ends unless this group starts with it
-            if (chead >= 0 && lane == 0 && i != chead) {
-                const float4 cv = s_carry[w];
-                A.Y_out[chead] = make_float2(fmaf(A.lr, 0.f + cv.x, cv.z), fmaf(A.lr, 0.f + cv.y, cv.w));
-            }
-            // segmented inclusive scan over runs of equal heads
-            const int32_t i_prev = __shfl_up_sync(FULL, i, 1);
-            const unsigned starts = __ballot_sync(FULL, lane == 0 || i_prev != i);
-            const int seg0 = 31 - __clz(starts & (FULL >> (31 - lane)));
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const float ox = __shfl_up_sync(FULL, fx, d), oy = __shfl_up_sync(FULL, fy, d);
-                if (lane - d >= seg0) {
-                    fx = ox + fx;
-                    fy = oy + fy;
-                }
-            }
-            if (seg0 == 0 && i == chead) {
-                const float4 cv = s_carry[w];
-                fx = cv.x + fx;
-                fy = cv.y + fy;
-            }
-            // a run that ends inside the group is the row's last: write it;
-            // the group's last run is carried
-            const int32_t i_next = __shfl_down_sync(FULL, i, 1);
-            if (cur.ok && lane < cnt - 1 && i_next != i)
-                A.Y_out[i] = make_float2(fmaf(A.lr, 0.f + fx, cur.yi.x), fmaf(A.lr, 0.f + fy, cur.yi.y));
-            __syncwarp();
-            if (lane == cnt - 1) {
-                s_carry[w] = make_float4(fx, fy, cur.yi.x, cur.yi.y);
-                s_chead[w] = cur.ok ? i : -1;
-            }
-            __syncwarp();
-        };
-        EntryInputs<NEG> held;  // PIPE: the fetched group waiting for its forces
-        int held_cnt = 0;
-        int qn = 0;             // active entries waiting at the front of the queue
-        // (a window whose rows are all empty still takes one, empty, burst)
-        for (int32_t c0 = es; c0 == es || c0 < ee; c0 += 32 * EPOCH_BURST) {
-            // the burst's CSR words, all loads in flight before any test; q =
-            // 0 never fires.  The CSR streams through once per epoch:
-            // evict-first loads keep L2 for the gathered positions Y.
-            uint32_t qv[EPOCH_BURST];
-            int32_t jv[EPOCH_BURST], hv[EPOCH_BURST];
-#pragma unroll
-            for (int b = 0; b < EPOCH_BURST; ++b) {
-                const int32_t e = c0 + 32 * b + lane;
-                const bool in = e < ee;
-                qv[b] = in ? __ldcs(A.q + e) : 0u;
-                jv[b] = in ? __ldcs(A.col + e) : 0;
-                hv[b] = in ? __ldcs(A.row_of + e) : -1;
-            }
-            if (PIPE && held_cnt) {  // the previous burst's last group, while the loads fly
-                finish_group(held, held_cnt);
-                held_cnt = 0;
-            }
-#pragma unroll
-            for (int b = 0; b < EPOCH_BURST; ++b) {
-                // floor((t+1) q / 2^24) > floor(t q / 2^24)  <=>  (t q mod 2^24) + q >= 2^24
-                const bool act = qv[b] >= 0x1000000u - ((A.t * qv[b]) & 0xFFFFFFu);
-                const unsigned m = __ballot_sync(FULL, act);
-                if (act) {
-                    const int pos = qn + __popc(m & lt_mask);
-                    act_w[pos] = make_int2(c0 + 32 * b + lane, jv[b]);
-                    head_w[pos] = hv[b];
-                }
-                qn += __popc(m);
-            }
-            __syncwarp();
-            if (c0 == es) {
-                // every row of the window first gets Y + lr * 0; rows with
-                // active entries are rewritten with their force below.  The
-                // wait for the previous epoch comes here, after the first
-                // burst has been loaded and tested.
-                grid_dep_wait();
-                for (int64_t r = rA + lane; r < rB; r += 32) {
-                    const float2 y = A.Y_in[r];
-                    A.Y_out[r] = make_float2(fmaf(A.lr, 0.f, y.x), fmaf(A.lr, 0.f, y.y));
-                }
-                if (lane == 0) s_chead[w] = -1;
-                __syncwarp();
-            }
-            const bool last = c0 + 32 * EPOCH_BURST >= ee;
-            const int ng = last ? (qn + 31) / 32 : qn / 32;
-            for (int g = 0; g < ng; ++g) {
-                const int cnt = qn - 32 * g < 32 ? qn - 32 * g : 32;
-                EntryInputs<NEG> in;
-                fetch_group(32 * g, cnt, in);
-                if (PIPE) {
-                    if (held_cnt) finish_group(held, held_cnt);
-                    held = in;
-                    held_cnt = cnt;
-                } else {
-                    finish_group(in, cnt);
-                }
-            }
-            // move the waiting partial group to the front
-            const int left = qn - 32 * ng > 0 ? qn - 32 * ng : 0;
-            int2 lv = make_int2(0, 0);
-            int32_t lh = -1;
-            if (lane < left) {
-                lv = act_w[32 * ng + lane];
-                lh = head_w[32 * ng + lane];
-            }
-            __syncwarp();
-            if (lane < left) {
-                act_w[lane] = lv;
-                head_w[lane] = lh;
-            }
-            qn = left;
-            __syncwarp();
-        }
-        if (PIPE && held_cnt) finish_group(held, held_cnt);
-        if (lane == 0 && s_chead[w] >= 0) {
-            const float4 cv = s_carry[w];
-            A.Y_out[s_chead[w]] = make_float2(fmaf(A.lr, 0.f + cv.x, cv.z), fmaf(A.lr, 0.f + cv.y, cv.w));
-        }
-        __syncwarp();
-    }
+    const CsrGlobal csr{A.q, A.col, A.row_of};
+    for (int32_t W = int32_t(blockIdx.x) * NW + w; W < n_win; W += int32_t(gridDim.x) * NW)
+        epoch_window<BATCHED, NEG, PIPE, EPOCH_BURST>(A, S, csr, W, lane, s_ej[w], s_hd[w], &s_carry[w], &s_chead[w],
+                                                      two_ab, two_b);
 }
 
 bool epoch_warps_supported(int warps) { return warps == 4 || warps == 8; }

@@ -6,6 +6,7 @@
 #include "epoch.cuh"
 #include "graph.cuh"
 #include "knn.cuh"
+#include "spectral.cuh"
 
 namespace drgb {
 
@@ -65,7 +66,11 @@ extern "C" int drgb_fit_transform(drgb_ctx* c, const float* X, int64_t n, int32_
     const int k = p->k;
     if (p->knn_mode < 0 || p->knn_mode > 3) return set_error(c, DRGB_ERR_INVALID, "fit_transform: bad knn_mode");
     const size_t fb = Carve::round(fit_bytes(n, k));
-    rc = ensure_scratch(c, fb + knn_scratch_bytes(n, d, k, p->knn_mode), st);
+    const bool spectral = (p->flags & DRGB_FLAG_INIT_SPECTRAL) != 0;
+    const size_t kb = knn_scratch_bytes(n, d, k, p->knn_mode);
+    // the spectral layout's scratch reuses the k-NN region (free by then)
+    const size_t sb = spectral ? spectral_scratch_bytes(n, int64_t(2) * n * k, c->num_sms) : 0;
+    rc = ensure_scratch(c, fb + (kb > sb ? kb : sb), st);
     if (rc) return rc;
     FitBuffers b = carve_fit(c->scratch, n, k);
     void* knn_scratch = static_cast<char*>(c->scratch) + fb;
@@ -87,7 +92,11 @@ extern "C" int drgb_fit_transform(drgb_ctx* c, const float* X, int64_t n, int32_
     if (rc) return rc;
     if ((rc = stage_mark(c, 2, st))) return rc;
     float2* Y = reinterpret_cast<float2*>(Y_out);
-    rc = launch_init(c, Y, n, p->init_range, p->seed_init, st);
+    if (spectral)
+        rc = spectral_layout(c, b.row_ptr, b.col, b.w, n, int64_t(2) * n * k, p->init_range, p->seed_init, Y,
+                             nullptr, knn_scratch, st);
+    else
+        rc = launch_init(c, Y, n, p->init_range, p->seed_init, st);
     if (rc) return rc;
     const int64_t nnz_cap = int64_t(2) * n * k;
     if (p->flags & DRGB_FLAG_AUTOTUNE) {

@@ -284,3 +284,4 @@ def test_set_tuning_rejects_unsupported_values(drgb):
             drgb.set_tuning(_lib.TUNE_EPOCH_PIPE, bad)
     with pytest.raises(drgb.DrgbError):
         drgb.set_tuning(99, 4)
+
