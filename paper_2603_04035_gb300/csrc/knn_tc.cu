@@ -48,7 +48,7 @@ namespace drgb {
 static constexpr int TC_BM = 128;
 static constexpr int TC_BN = 256;
 static constexpr int TC_K = 64;
-static constexpr int TC_STAGES = 4;
+static constexpr int TC_STAGES = 3;
 static constexpr int TC_KP = 32;                 // candidates kept per row
 static constexpr int TC_EPI_WARPS = 8;
 static constexpr int TC_THREADS = 64 + TC_EPI_WARPS * 32;
@@ -57,7 +57,8 @@ static constexpr int TC_B_BYTES = TC_BN * TC_K * 2;   // 32 KiB
 static constexpr int TC_TMEM_COLS = 512;               // two 256-column accumulators
 static constexpr int TC_QCAP = 32;                     // per-thread candidate queue slots (one chunk)
 static constexpr size_t TC_QUEUE_BYTES = size_t(TC_EPI_WARPS) * 32 * TC_QCAP * 8;
-static constexpr size_t TC_THR_BYTES = size_t(2) * TC_BM * 4;   // per (column half, row) threshold
+static constexpr int TC_NQ = 4;                       // list quantiles a column half publishes
+static constexpr size_t TC_THR_BYTES = size_t(2) * TC_BM * TC_NQ * 4;   // per (column half, row) quantiles
 static constexpr int TC_CELLS = 128;                   // most cells a schedule may hold
 static constexpr int TC_GROUPS = 4;                    // row groups (runs of one cell) bounded separately
 static constexpr int TC_RING = 16;                     // tile-index ring (slots in flight < 16)
@@ -392,11 +393,12 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     // per epilogue thread: a queue of candidates (value bits, column) that
     // passed the threshold
     int2* q = reinterpret_cast<int2*>(reinterpret_cast<uint8_t*>(bars) + 256);
-    // per (column half, row): the 32nd-best value that half holds so far
+    // per (column half, row): the 8th, 16th, 24th and 32nd best values that
+    // half's list holds so far
     float* s_thr = reinterpret_cast<float*>(q + TC_EPI_WARPS * 32 * TC_QCAP);
     // schedule: sorted cell bounds and cells, per-row distance bounds, the
     // tile ring (slot number and tile), misc words, visited-tile bitmap
-    float* s_lb = s_thr + 2 * TC_BM;
+    float* s_lb = s_thr + 2 * TC_BM * TC_NQ;
     int32_t* s_cl = reinterpret_cast<int32_t*>(s_lb + TC_CELLS);
     float* s_glb = reinterpret_cast<float*>(s_cl + TC_CELLS);                // [TC_GROUPS][TC_CELLS]
     int32_t* s_gb = reinterpret_cast<int32_t*>(s_glb + TC_GROUPS * TC_CELLS);  // [TC_GROUPS + 1] (+pad)
@@ -679,20 +681,34 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         }
         // Candidates below the row's threshold are appended to this thread's
         // queue (slot s at q[s * 256 + tid], conflict-free).  The threshold
-        // is the smaller of the two column halves' 32nd-best values: a value at
-        // or above either cannot be among the row's 32 best, whichever half
-        // holds it (each half's 32nd-best bounds the row's from above, and a
-        // stale, larger, value is still a valid bound).  When a chunk would
-        // overflow any lane's queue, all lanes merge their queues into their
-        // lists in lockstep: the queue (padded with +inf) is sorted by a
-        // bitonic network, the 32 smallest of list and queue are selected by
-        // pairing the list's upper half with the reversed queue, and a bitonic
-        // merge restores the order.
+        // is a bound on the row's 32nd-best value over both column halves:
+        // each half publishes the 8th, 16th, 24th and 32nd values of its
+        // sorted list, and for b in {0, 8, 16, 24, 32} the 32 - b smallest of
+        // this half's list together with the b smallest of the other's are 32
+        // distinct columns, so max(own[31 - b], other's b-th) bounds the
+        // row's 32nd-best; the threshold is the smallest of the five.  A value
+        // at or above it cannot be among the row's 32 best.  A stale (larger)
+        // published value still bounds correctly, since a list only improves.
+        // When a chunk would overflow any lane's queue, all lanes merge their
+        // queues into their lists in lockstep: the queue (padded with +inf)
+        // is sorted by a bitonic network, the 32 smallest of list and queue
+        // are selected by pairing the list's upper half with the reversed
+        // queue, and a bitonic merge restores the order.
         const int qb = e * 32 + lane;
-        volatile float* thr_mine = s_thr + half * TC_BM + row;
-        volatile float* thr_other = s_thr + (1 - half) * TC_BM + row;
-        *thr_mine = INFINITY;
+        volatile float* q_mine = s_thr + (half * TC_BM + row) * TC_NQ;
+        volatile float* q_other = s_thr + ((1 - half) * TC_BM + row) * TC_NQ;
+#pragma unroll
+        for (int j = 0; j < TC_NQ; ++j) q_mine[j] = INFINITY;
         asm volatile("bar.sync 1, %0;" ::"r"(TC_EPI_WARPS * 32) : "memory");
+        // the row's threshold from this half's list and the other's quantiles
+        auto row_bound = [&]() {
+            const float o8 = q_other[0], o16 = q_other[1], o24 = q_other[2], o32 = q_other[3];
+            float t = fminf(L[TC_KP - 1], o32);
+            t = fminf(t, fmaxf(L[23], o8));
+            t = fminf(t, fmaxf(L[15], o16));
+            t = fminf(t, fmaxf(L[7], o24));
+            return t;
+        };
         int qn = 0;
         auto flush = [&]() {
             float qv[TC_QCAP];
@@ -713,8 +729,11 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             }
             bitonic_merge_asc<TC_KP>(L, I);
             qn = 0;
-            *thr_mine = L[TC_KP - 1];
-            const float thr = fminf(L[TC_KP - 1], *thr_other);
+            q_mine[0] = L[7];
+            q_mine[1] = L[15];
+            q_mine[2] = L[23];
+            q_mine[3] = L[TC_KP - 1];
+            const float thr = row_bound();
             if (g_row >= 0 && thr < INFINITY)
                 s_U[row] = (sqrtf(fmaxf(s_ua[row] + thr * s_misc[2], 0.f)) + s_uc[row]) * (1.0f + 1e-5f);
         };
@@ -735,15 +754,15 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             if (tile < 0) break;
             const uint32_t tbase = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(buf * TC_BN + half * 128);
             const int32_t j0 = tile * TC_BN + half * 128;
-            // the other half's threshold, read once per tile (a stale, larger,
-            // value is still a valid bound)
-            const float thr_o = *thr_other;
+            // the row's threshold, with the other half's quantiles read once
+            // per tile (stale, larger, values still bound correctly)
+            float thr_t = row_bound();
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 float v[32];
                 __syncwarp();
                 tmem_ld32(tbase + c * 32, v);
-                float thr = fminf(L[TC_KP - 1], thr_o);
+                float thr = thr_t;
                 float gm[4];
 #pragma unroll
                 for (int g = 0; g < 4; ++g)
@@ -764,7 +783,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                             flush();
                             __syncwarp();
                             tmem_ld32(tbase + c * 32, v);
-                            thr = fminf(L[TC_KP - 1], *thr_other);
+                            thr = thr_t = row_bound();
                         }
                     }
 #pragma unroll
