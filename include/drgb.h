@@ -96,6 +96,19 @@ const char* drgb_last_error(const drgb_ctx* ctx);
  * Returns DRGB_OK or the first device-side error since the last sync. */
 int drgb_sync(drgb_ctx* ctx, void* stream);
 
+/* Self-test of the bounded device-side waits (no counterpart in the paper):
+ * every tensor-core kernel of the library waits on its mbarriers for at most
+ * 2 s, then reports DRGB_ERR_TIMEOUT through the context's status word,
+ * drains what it has issued and returns instead of hanging the GPU.  This
+ * call runs that same wait in a one-thread kernel on a barrier nothing
+ * arrives at (arrive = 0; with arrive != 0 the thread arrives first and the
+ * wait succeeds), with a limit of limit_us microseconds (1 .. 10,000,000).
+ * Synchronous: returns DRGB_ERR_TIMEOUT (arrive = 0) or DRGB_OK (arrive != 0)
+ * as read back by drgb_sync, which clears the status word, so later calls on
+ * the context start clean.  DRGB_ERR_INVALID for a NULL context or a limit
+ * out of range. */
+int drgb_wait_selftest(drgb_ctx* ctx, int64_t limit_us, int32_t arrive, void* stream);
+
 /* Bytes of scratch the context currently holds (for memory accounting). */
 int64_t drgb_ctx_scratch_bytes(const drgb_ctx* ctx);
 

@@ -49,18 +49,19 @@ __device__ __forceinline__ bool mbar_try_sleep(uint64_t* bar, uint32_t parity, u
         : "memory");
     return ok != 0;
 }
-// Bounded wait: gives up after TC_TIMEOUT_NS or when another role aborted.
-// Between checks the thread sleeps in the barrier (at most 20 us a time)
-// instead of spinning, so a waiting role takes no issue slots from the
-// roles that work.
+// Bounded wait: gives up after limit_ns (TC_TIMEOUT_NS unless given) or when
+// another role aborted; giving up raises the abort flag and reports
+// DRGB_ERR_TIMEOUT in the status word.  Between checks the thread sleeps in
+// the barrier (at most 20 us a time) instead of spinning, so a waiting role
+// takes no issue slots from the roles that work.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          int* status) {
+                                          int* status, unsigned long long limit_ns = TC_TIMEOUT_NS) {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = global_timer();
     while (true) {
         if (mbar_try_sleep(bar, parity, 20000u)) return true;
         if (*abort_flag) return false;
-        if (global_timer() - t0 > TC_TIMEOUT_NS) {
+        if (global_timer() - t0 > limit_ns) {
             *abort_flag = 1;
             report_status(status, DRGB_ERR_TIMEOUT);
             return false;

@@ -100,6 +100,11 @@ def test_product_path_does_not_import_the_oracle():
             assert "import oracle" not in text and "from oracle" not in text, path
 
 
+def test_wait_selftest_needs_a_context(lib):
+    from paper_2603_04035_gb300 import _lib
+    assert lib.drgb_wait_selftest(None, 1000, 0, None) == _lib.ERR_INVALID
+
+
 def test_tuning_cache_round_trip(lib, tmp_path):
     import json
     from paper_2603_04035_gb300 import _lib
