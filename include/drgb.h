@@ -274,9 +274,10 @@ int drgb_init_embedding(drgb_ctx* ctx, int64_t n, float init_range, uint64_t see
  *   eigvals          optional host array of 3: the leading eigenvalues of M
  * Computed in FP32 by Chebyshev-filtered subspace iteration on 8 vectors
  * until the residual |M v - lambda v| of the three leading pairs is below
- * 1e-5, or for at most 400 subspace steps (then the current vectors are
- * used); on a disconnected graph eigenvalue 1 repeats and the layout is some
- * pair of vectors of its eigenspace.  Synchronous.  Errors: DRGB_ERR_INVALID
+ * 1e-5, for at most 400 subspace steps, or until the worst residual has not
+ * halved in 40 steps (then the current vectors are used: the leading
+ * eigenvalues are too close to separate); on a disconnected graph eigenvalue
+ * 1 repeats and the layout is some pair of vectors of its eigenspace.  Synchronous.  Errors: DRGB_ERR_INVALID
  * (NULL, misaligned, n < 9, init_range <= 0), DRGB_ERR_CUDA. */
 int drgb_spectral_init(drgb_ctx* ctx, const int32_t* row_ptr, const int32_t* col, const float* w, int64_t n,
                        float init_range, uint64_t seed, float* Y_out, double* eigvals, void* stream);

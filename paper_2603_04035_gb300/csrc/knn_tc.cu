@@ -600,6 +600,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         if (lane == 0) {
             s_misc[1] = lbstop;
             atomicAdd(P.tiles_done, static_cast<unsigned long long>(t));
+            // loads issued: slots 0 .. issued - 1 (an aborted slot issued none)
+            int issued = stop_ok ? t : t - 1;
             if (stop_ok) {
                 // end of the stream: slot t carries tile -1 (no data)
                 const int s = t % TC_STAGES;
@@ -608,16 +610,25 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     __threadfence_block();
                     ring_t[t % TC_RING] = t;
                     mbar_arrive(&full[s]);
+                } else {
+                    stop_ok = false;
                 }
-            } else {
-                // aborted: let the loads already issued land before the CTA exits
-                for (int u = (t > TC_STAGES ? t - TC_STAGES : 0); u < t - 1; ++u) {
+            }
+            if (!stop_ok) {
+                // aborted: let every load already issued land before the CTA
+                // exits (each wait bounded by 100 ms).  Slots before
+                // issued - TC_STAGES were consumed by the MMA warp, whose
+                // wait on them completed; their buffers were reused only
+                // after that.  The A tile's load was issued first of all.
+                for (int u = (issued > TC_STAGES ? issued - TC_STAGES : 0); u < issued; ++u) {
                     const unsigned long long t0 = global_timer();
                     while (!mbar_try(&full[u % TC_STAGES], (u / TC_STAGES) & 1) &&
                            global_timer() - t0 < 100000000ull) {
                     }
                 }
-                mbar_try(a_full, 0);
+                const unsigned long long t0 = global_timer();
+                while (!mbar_try(a_full, 0) && global_timer() - t0 < 100000000ull) {
+                }
             }
         }
     } else if (warp == 1) {

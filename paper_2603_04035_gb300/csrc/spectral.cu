@@ -13,8 +13,9 @@
 //   X  = Y R^-1          Cholesky QR, twice (Y^T Y = R^T R)
 //   H  = X^T M X         Rayleigh-Ritz: H = V diag(theta) V^T, X <- X V
 // until the residuals |M x_k - theta_k x_k| of the three leading Ritz pairs
-// fall below SPEC_TOL (at most SPEC_MAXIT steps); cut is the smallest Ritz
-// value of the block.  A vector's angle to its eigenvector is then about
+// fall below SPEC_TOL, for at most SPEC_MAXIT steps, or until the worst of
+// them has not halved in SPEC_STALL steps; cut is the smallest Ritz value of
+// the block.  A vector's angle to its eigenvector is then about
 // SPEC_TOL / (gap to the neighbouring eigenvalues).
 // The layout takes Ritz vectors 1 and 2 (vector 0 is D^1/2 1, eigenvalue 1),
 // each with the sign that makes its largest-magnitude entry positive.
@@ -32,6 +33,7 @@ namespace drgb {
 static constexpr int SP = 8;          // block size
 static constexpr int SPEC_DEG = 12;   // Chebyshev degree per iteration
 static constexpr int SPEC_MAXIT = 400;
+static constexpr int SPEC_STALL = 40;
 static constexpr double SPEC_TOL = 1e-5;
 static constexpr float SPEC_JITTER = 1e-5f;
 static constexpr int GRAM_BLOCKS_PER_SM = 2;
@@ -368,7 +370,14 @@ int spectral_layout(Ctx* c, const int32_t* rp, const int32_t* col, const float* 
     };
     if ((rc = rayleigh_ritz())) return rc;
     int it = 0;
+    double best_res = std::fmax(resid[0], std::fmax(resid[1], resid[2]));
+    int best_it = 0;
     for (; it < SPEC_MAXIT && std::fmax(resid[0], std::fmax(resid[1], resid[2])) > SPEC_TOL; ++it) {
+        // stagnation: the worst residual has not halved in SPEC_STALL steps,
+        // so the leading eigenvalues are too close to separate in FP32 (a
+        // nearly disconnected graph); any combination of their eigenvectors
+        // serves as the layout
+        if (it - best_it >= SPEC_STALL) break;
         // Chebyshev filter damping [a, b] = [-1, cut], scaled at a0 = 1 (the
         // top eigenvalue of M)
         double cut = theta[SP - 1];
@@ -399,6 +408,11 @@ int spectral_layout(Ctx* c, const int32_t* rp, const int32_t* col, const float* 
         Zb = nxt;
         if ((rc = orthonormalise(X, Yb))) return rc;
         if ((rc = rayleigh_ritz())) return rc;
+        const double worst = std::fmax(resid[0], std::fmax(resid[1], resid[2]));
+        if (worst < 0.5 * best_res) {
+            best_res = worst;
+            best_it = it + 1;
+        }
     }
     // (after SPEC_MAXIT steps the current Ritz vectors are taken as they are:
     // a slow finish means nearly equal eigenvalues, whose eigenvectors any

@@ -71,4 +71,10 @@ def test_fit_quality_at_scale(drgb, big):
     Y = drgb.fit_transform(X, n_epochs=200)
     r = drgb.eval_recall(X, Y, 15, 10_000)
     t = drgb.eval_trust(X, Y, 15, 10_000)
-    assert r > 100 * 15 / N and t > 0.8, (r, t)
+    # Measured on GB300 (seeds 0 and 1 of this workload, 10K sampled rows):
+    # recall 1.7e-4 and 2.5e-4 (110-170x chance: inside a 100,000-point
+    # Gaussian cluster a point's 15 nearest neighbours are set by noise that
+    # no 2-D map keeps), trustworthiness 0.9950 both.  The floors sit below
+    # half the measured recall and 0.005 below the measured trust, and at
+    # least at the 0.9 trust floor of the smaller fits.
+    assert r > 50 * 15 / N and t > 0.99, (r, t)
