@@ -441,6 +441,36 @@ int drgb_transform(drgb_ctx* ctx, const float* X_train, const float* Y_train, in
  * spread 1, init_range 10, seeds 1 and 2, knn_mode auto). */
 int drgb_default_params(drgb_params* p);
 
+/* -------------------------------------------------------- rendering */
+
+/* Circle-splatting renderer (Section 2.4, the GPU rendering pipeline): every
+ * point i adds, at each pixel whose centre lies at distance r < radius (in
+ * pixels) from it, alpha * w and alpha * w * rgb_i with w = 1 - r / radius to
+ * the pixel's alpha and colour accumulators (atomic scatter-add); the
+ * resolve pass writes, where the accumulated alpha A > 0, the colour C / A
+ * composited over the background with coverage min(1, A), and the background
+ * elsewhere, each channel stored as round(255 * clamp(v, 0, 1)).
+ *   Y          n x 2 FP32 embedding (device, 8-byte aligned)
+ *   rgb        n x 3 FP32 colours in [0, 1] (device)
+ *   width, height  frame size (at most 2^28 pixels); radius in (0, 64]
+ *   alpha      opacity of one splat's centre (>= 0)
+ *   background 3 floats (host)
+ *   view_in    host (x0, y0, s): pixel px = (x - x0) s, py = (y - y0) s,
+ *              pixel (u, v) centred at (u + 1/2, v + 1/2), row v growing with
+ *              y; or NULL: fitted to the points' bounding box with a 5%
+ *              margin on each side, the larger extent filling the frame,
+ *              centred
+ *   view_out   NULL, or host 3 floats receiving the view used (synchronises
+ *              the stream)
+ *   frame      height x width x 3 uint8, row-major (device, caller-owned)
+ * The accumulator (16 bytes per pixel) lives in the context's scratch; the
+ * order of the scatter-add is not fixed, so sums may differ between runs by
+ * FP32 rounding.  Asynchronous unless view_out is given.  Errors:
+ * DRGB_ERR_INVALID (NULL, sizes, radius, alpha, alignment, view scale <= 0). */
+int drgb_render(drgb_ctx* ctx, const float* Y, const float* rgb, int64_t n, int32_t width, int32_t height,
+                float radius, float alpha, const float* background, const float* view_in, float* view_out,
+                uint8_t* frame, void* stream);
+
 /* -------------------------------------------------------- evaluation */
 
 /* k-NN preservation (kNN-P, Section 3.2): mean over the query rows of

@@ -33,7 +33,7 @@ from ._lib import MAX_K, Params  # noqa: F401
 
 __all__ = ["DrgbError", "Graph", "UMAP", "knn_graph", "fuzzy_weights", "find_ab",
            "init_embedding", "embed_epoch", "embed_epochs", "fit_transform", "eval_recall",
-           "eval_trust", "eval_recall_heldout", "spectral_init", "default_params", "context", "knn_uncertified", "launch_count",
+           "eval_trust", "eval_recall_heldout", "spectral_init", "render", "default_params", "context", "knn_uncertified", "launch_count",
            "set_profiling", "stage_times", "set_tuning", "get_tuning", "set_tuning_cache",
            "tuning_cache_lookup", "tuning_cache_store", "knn_tiles", "fit_transform_batched",
            "autotune_epoch", "mlp_param_count", "mlp_init", "mlp_sample", "mlp_grad", "mlp_train",
@@ -500,6 +500,28 @@ def eval_recall_heldout(X_train: torch.Tensor, Y_train: torch.Tensor, X_new: tor
                                                 Xn.shape[0], Xt.shape[1], k, n_query, C.byref(out),
                                                 _stream(Xt.device)), ctx)
     return out.value
+
+
+def render(Y: torch.Tensor, rgb: torch.Tensor, width: int = 1000, height: int = 1000, radius: float = 2.0,
+           alpha: float = 1.0, background=(1.0, 1.0, 1.0), view=None, out: torch.Tensor | None = None,
+           return_view: bool = False):
+    """Circle-splatting render of the embedding Y (n x 2) with per-point
+    colours rgb (n x 3 in [0, 1]) into a height x width x 3 uint8 frame on the
+    device.  view = (x0, y0, scale) or None (fitted to the points)."""
+    Y = _cuda(Y, torch.float32, "Y", 2)
+    rgb = _cuda(rgb, torch.float32, "rgb", 2)
+    if Y.shape[1] != 2 or rgb.shape != (Y.shape[0], 3):
+        raise ValueError("render: Y must be n x 2 and rgb n x 3")
+    frame = torch.empty((height, width, 3), dtype=torch.uint8, device=Y.device) if out is None else out
+    bg = (C.c_float * 3)(*background)
+    vin = (C.c_float * 3)(*view) if view is not None else None
+    vout = (C.c_float * 3)()
+    ctx = context(Y.device.index)
+    _check(_lib.load().drgb_render(ctx, _ptr(Y), _ptr(rgb), Y.shape[0], width, height, radius, alpha, bg, vin,
+                                   vout if return_view else None, _ptr(frame), _stream(Y.device)), ctx)
+    if return_view:
+        return frame, (vout[0], vout[1], vout[2])
+    return frame
 
 
 class UMAP:

@@ -86,6 +86,8 @@ SIGNATURES = {
                                       C.POINTER(C.c_int32), C.POINTER(C.c_float), vp]),
     "drgb_eval_recall": (C.c_int, [vp, vp, vp, i64, i32, i32, i64, C.POINTER(C.c_double), vp]),
     "drgb_eval_trust": (C.c_int, [vp, vp, vp, i64, i32, i32, i64, C.POINTER(C.c_double), vp]),
+    "drgb_render": (C.c_int, [vp, vp, vp, i64, i32, i32, f32, f32, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                              C.POINTER(C.c_float), vp, vp]),
     "drgb_wait_selftest": (C.c_int, [vp, i64, i32, vp]),
     "drgb_spectral_init": (C.c_int, [vp, vp, vp, vp, i64, f32, u64, vp, C.POINTER(C.c_double), vp]),
     "drgb_eval_recall_heldout": (C.c_int, [vp, vp, vp, i64, vp, vp, i64, i32, i32, i64, C.POINTER(C.c_double),

@@ -232,8 +232,11 @@ __global__ void epoch_instances_kernel(const int32_t* __restrict__ rp, const int
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b <= count; b += gridDim.x * blockDim.x) {
         inst_eoff[b] = rp[inst_off[b]];
         if (b < count) {
+            // an instance without entries still takes one (empty) window, so
+            // that its rows are written (Y + lr * 0) and no other instance's
+            // window reaches into them
             const int32_t ne = rp[inst_off[b + 1]] - rp[inst_off[b]];
-            win_cnt[b] = ne > 0 ? (ne + EPOCH_WIN - 1) / EPOCH_WIN : 0;
+            win_cnt[b] = ne > 0 ? (ne + EPOCH_WIN - 1) / EPOCH_WIN : 1;
         }
     }
 }
