@@ -28,6 +28,8 @@ below follows the published UMAP construction, in plain NumPy/SciPy, in FP64:
                      eigenvectors of the normalised fuzzy-graph adjacency.
 * ``render``         the circle-splatting renderer (Section 2.4): linear
                      falloff splats, premultiplied accumulation, resolve.
+* ``pca``            PCA preprocessing to pca_dim (Section 3): covariance,
+                     leading eigenvectors, projection.
 * ``mlp``            FP64 forward/backward of the learned 50-256-256-2 embedder
                      with BF16 rounding emulated where the CUDA path rounds.
 
@@ -36,4 +38,4 @@ something other than itself (library routines, closed forms, finite
 differences, invariants or published constants).  ``sgd.fit`` is a chaotic
 iteration and is pinned only through its parts and through statistics.
 """
-from . import knn, fuzzy, curve, philox, sgd, metrics, mlp, spectral, render  # noqa: F401
+from . import knn, fuzzy, curve, philox, sgd, metrics, mlp, spectral, render, pca  # noqa: F401
