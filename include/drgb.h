@@ -282,6 +282,34 @@ int drgb_init_embedding(drgb_ctx* ctx, int64_t n, float init_range, uint64_t see
 int drgb_spectral_init(drgb_ctx* ctx, const int32_t* row_ptr, const int32_t* col, const float* w, int64_t n,
                        float init_range, uint64_t seed, float* Y_out, double* eigvals, void* stream);
 
+/* PCA preprocessing to dim components (the paper's pipeline reduces the raw
+ * features by PCA before the k-NN graph, Section 3, pca_dim = 50 for UMAP):
+ * mu = the column means of X, C = (X - mu)^T (X - mu) / (n - 1), V = the
+ * eigenvectors of C for its dim largest eigenvalues in decreasing order, each
+ * signed so that its entry of largest magnitude (lowest index among equal
+ * magnitudes) is positive, and Z = (X - mu) V.
+ *   X           n x D FP32 row-major (device), 1 <= D <= 1024, n >= 2
+ *   dim         1 <= dim <= min(D, 56)
+ *   Z           n x dim FP32 (device, caller-owned)
+ *   components  NULL, or dim x D FP32 (device): V^T, one component per row
+ *   mean        NULL, or D FP32 (device): mu
+ *   eigvals     NULL, or host array of dim: the eigenvalues of C
+ * C is formed on the tensor cores from a two-term BF16 split of X - mu (hi +
+ * lo, about 16 significant bits): sym(hi hi^T) + hi lo^T + lo hi^T with FP32
+ * accumulation over at most 2048 points per split, the splits summed in
+ * float-float.  The eigenvectors come from Chebyshev-filtered subspace
+ * iteration on 64 vectors, all on the device (FP32 products, float-float
+ * Gram matrices, Cholesky QR with an FP64 factor, Rayleigh-Ritz by FP32
+ * Jacobi); leading pairs whose residual |C v - theta v| is below
+ * 1e-5 theta_1 are locked and deflated, until the dim leading pairs are
+ * (at most 300 steps, or until the worst residual has not halved in 40: then
+ * the current vectors, which span the leading eigenspace to that accuracy,
+ * are used); Z is an FP32 product.  Scratch, in the context's: about
+ * 4 n D' + n D'^2 / 256 bytes, D' = D rounded up to 128.  Synchronous.
+ * Errors: DRGB_ERR_INVALID (NULL, misaligned, sizes), DRGB_ERR_CUDA. */
+int drgb_pca(drgb_ctx* ctx, const float* X, int64_t n, int32_t D, int32_t dim, float* Z, float* components,
+             float* mean, double* eigvals, void* stream);
+
 /* ---------------------------------------------------------- SGD epoch */
 
 /* One synchronous SGD epoch t over a head-sorted CSR (Section 2.5, the UMAP

@@ -33,7 +33,7 @@ from ._lib import MAX_K, Params  # noqa: F401
 
 __all__ = ["DrgbError", "Graph", "UMAP", "knn_graph", "fuzzy_weights", "find_ab",
            "init_embedding", "embed_epoch", "embed_epochs", "fit_transform", "eval_recall",
-           "eval_trust", "eval_recall_heldout", "spectral_init", "render", "default_params", "context", "knn_uncertified", "launch_count",
+           "eval_trust", "eval_recall_heldout", "spectral_init", "pca", "render", "default_params", "context", "knn_uncertified", "launch_count",
            "set_profiling", "stage_times", "set_tuning", "get_tuning", "set_tuning_cache",
            "tuning_cache_lookup", "tuning_cache_store", "knn_tiles", "fit_transform_batched",
            "autotune_epoch", "mlp_param_count", "mlp_init", "mlp_sample", "mlp_grad", "mlp_train",
@@ -266,6 +266,21 @@ def spectral_init(g: Graph, init_range: float = 10.0, seed: int = 1):
     _check(_lib.load().drgb_spectral_init(ctx, _ptr(g.row_ptr), _ptr(g.col), _ptr(g.w), n, init_range, seed,
                                           _ptr(Y), ev, _stream(Y.device)), ctx)
     return Y, [ev[0], ev[1], ev[2]]
+
+
+def pca(X: torch.Tensor, dim: int = 50):
+    """PCA of the rows of X (n x D, FP32 on the GPU) to `dim` components:
+    (Z n x dim, components dim x D, mean D, eigenvalues of the covariance)."""
+    X = _cuda(X, torch.float32, "X", 2)
+    n, D = X.shape
+    Z = torch.empty((n, dim), dtype=torch.float32, device=X.device)
+    comps = torch.empty((dim, D), dtype=torch.float32, device=X.device)
+    mu = torch.empty((D,), dtype=torch.float32, device=X.device)
+    ev = (C.c_double * max(dim, 1))()
+    ctx = context(X.device.index)
+    _check(_lib.load().drgb_pca(ctx, _ptr(X), n, D, dim, _ptr(Z), _ptr(comps), _ptr(mu), ev,
+                                _stream(X.device)), ctx)
+    return Z, comps, mu, [ev[k] for k in range(dim)]
 
 
 def embed_epoch(Y: torch.Tensor, g: Graph, a: float, b: float, lr: float, neg: int, epoch: int,

@@ -90,6 +90,7 @@ SIGNATURES = {
                               C.POINTER(C.c_float), vp, vp]),
     "drgb_wait_selftest": (C.c_int, [vp, i64, i32, vp]),
     "drgb_spectral_init": (C.c_int, [vp, vp, vp, vp, i64, f32, u64, vp, C.POINTER(C.c_double), vp]),
+    "drgb_pca": (C.c_int, [vp, vp, i64, i32, i32, vp, vp, vp, C.POINTER(C.c_double), vp]),
     "drgb_eval_recall_heldout": (C.c_int, [vp, vp, vp, i64, vp, vp, i64, i32, i32, i64, C.POINTER(C.c_double),
                                            vp]),
 }

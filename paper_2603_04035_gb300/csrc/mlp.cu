@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "gemm.cuh"
 #include "tc_ptx.cuh"
 
 namespace drgb {
@@ -292,6 +293,20 @@ static int gemm_launch(Ctx* c, const Gemm& G, cudaStream_t st) {
     if (G.bn == 256 && G.epi == EPI_F32) return gemm_launch_t<256, EPI_F32>(c, G, st);
     if (G.bn == 64 && G.epi == EPI_F32) return gemm_launch_t<64, EPI_F32>(c, G, st);
     return set_error(c, DRGB_ERR_INVALID, "mlp gemm: unsupported tile");
+}
+
+// The plain product for other users of the library (the PCA covariance):
+// partials[z][M][N] = A[M x K] B[N x K]^T over the z-th share of K.
+int tc_gemm_nt_f32(Ctx* c, const void* A, const void* B, int M, int N, int K, int splits, float* partials,
+                   int* splits_used, cudaStream_t st) {
+    Gemm G;
+    const int bn = (N % 256 == 0) ? 256 : 64;
+    int rc = gemm_setup(c, G, static_cast<const bf16*>(A), static_cast<const bf16*>(B), M, N, K, bn, EPI_F32, splits);
+    if (rc) return rc;
+    G.g.out_f32 = partials;
+    if ((rc = bn == 256 ? gemm_attr<256, EPI_F32>(c) : gemm_attr<64, EPI_F32>(c))) return rc;
+    if (splits_used) *splits_used = int(G.grid.z);
+    return gemm_launch(c, G, st);
 }
 
 // ------------------------------------------------------------------ SIMT kernels
