@@ -62,6 +62,9 @@ typedef struct drgb_params {
     uint64_t seed_neg;    /* Philox key of the negative samples */
     int32_t knn_mode;     /* 0 auto, 1 exact FP32 scan, 2 BF16 / 3 FP16 tensor-core + FP32 re-rank */
     int32_t flags;        /* DRGB_FLAG_* bits */
+    int32_t pca_dim;      /* 0 (default): none; 1..56: fit_transform first projects X on its pca_dim
+                             leading principal components (drgb_pca) when d > pca_dim (Section 3:
+                             the timed pipeline includes PCA preprocessing; 50 there) */
 } drgb_params;
 
 /* drgb_params.flags: time the epoch schedules on the actual graph before the
@@ -351,12 +354,15 @@ int drgb_embed_epochs(drgb_ctx* ctx, float* Y, float* Y_tmp, const int32_t* row_
 
 /* ----------------------------------------------------------- full fit */
 
-/* fit_transform(X) -> Y (Section 2.1): k-NN graph, fuzzy graph, a, b fit,
- * initialisation and p->n_epochs epochs.  X is n x d FP32 on the device,
- * Y_out n x 2 FP32 on the device.  Synchronous (returns after Y_out is
- * written and the device status has been checked).  `cb` may be NULL; when
- * set it is called after every epoch (this costs one host sync per epoch).
- * Errors: as the steps above; DRGB_ERR_NONFINITE if X holds NaN/Inf. */
+/* fit_transform(X) -> Y (Section 2.1): with p->pca_dim > 0 and d > pca_dim,
+ * PCA of X to pca_dim (as drgb_pca; d <= 1024) first; then k-NN graph, fuzzy
+ * graph, a, b fit, initialisation and p->n_epochs epochs.  X is n x d FP32 on
+ * the device, Y_out n x 2 FP32 on the device.  Synchronous (returns after
+ * Y_out is written and the device status has been checked).  `cb` may be
+ * NULL; when set it is called after every epoch (this costs one host sync per
+ * epoch).  Errors: as the steps above; DRGB_ERR_NONFINITE if X holds NaN/Inf;
+ * DRGB_ERR_INVALID for pca_dim outside 0..56.  drgb_fit_transform_batched and
+ * drgb_transform take pca_dim = 0 only. */
 int drgb_fit_transform(drgb_ctx* ctx, const float* X, int64_t n, int32_t d,
                        const drgb_params* p, float* Y_out, drgb_epoch_cb cb, void* user,
                        void* stream);

@@ -33,7 +33,7 @@ class Params(C.Structure):
     _fields_ = [("k", C.c_int32), ("n_epochs", C.c_int32), ("neg", C.c_int32),
                 ("lr0", C.c_float), ("min_dist", C.c_float), ("spread", C.c_float),
                 ("init_range", C.c_float), ("seed_init", C.c_uint64), ("seed_neg", C.c_uint64),
-                ("knn_mode", C.c_int32), ("flags", C.c_int32)]
+                ("knn_mode", C.c_int32), ("flags", C.c_int32), ("pca_dim", C.c_int32)]
 
 
 class MlpParams(C.Structure):

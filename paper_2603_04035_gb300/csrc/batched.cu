@@ -60,6 +60,7 @@ int drgb_fit_transform_batched(drgb_ctx* c, const float* X_cat, const int64_t* o
         !aligned(X_cat, 4))
         return set_error(c, DRGB_ERR_INVALID, "fit_transform_batched: bad parameters");
     if (offsets[0] != 0) return set_error(c, DRGB_ERR_INVALID, "fit_transform_batched: offsets[0] != 0");
+    if (p->pca_dim != 0) return set_error(c, DRGB_ERR_INVALID, "fit_transform_batched: pca_dim is not supported");
     int64_t max_n = 0;
     for (int b = 0; b < count; ++b) {
         const int64_t nb = offsets[b + 1] - offsets[b];

@@ -1,11 +1,13 @@
 // fit_transform(X) -> Y: the whole hot path on one stream (Section 2.1, the
-// public API; Section 3, the timed fit_transform).  k-NN graph -> fuzzy graph
-// -> a, b -> initialisation -> T epochs (one captured graph), all enqueued
-// before the single synchronisation at the end.
+// public API; Section 3, the timed fit_transform).  [PCA to pca_dim ->] k-NN
+// graph -> fuzzy graph -> a, b -> initialisation -> T epochs (one captured
+// graph), all enqueued before the single synchronisation at the end (the
+// optional PCA synchronises on its own first).
 #include "common.cuh"
 #include "epoch.cuh"
 #include "graph.cuh"
 #include "knn.cuh"
+#include "pca.cuh"
 #include "spectral.cuh"
 
 namespace drgb {
@@ -65,15 +67,27 @@ extern "C" int drgb_fit_transform(drgb_ctx* c, const float* X, int64_t n, int32_
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int k = p->k;
     if (p->knn_mode < 0 || p->knn_mode > 3) return set_error(c, DRGB_ERR_INVALID, "fit_transform: bad knn_mode");
+    if (p->pca_dim < 0 || p->pca_dim > PCA_MAX_DIM)
+        return set_error(c, DRGB_ERR_INVALID, "fit_transform: pca_dim must be 0..%d", PCA_MAX_DIM);
+    const bool do_pca = p->pca_dim > 0 && p->pca_dim < d;
+    if (do_pca && d > PCA_MAX_FEATURES)
+        return set_error(c, DRGB_ERR_INVALID, "fit_transform: PCA takes at most %d features", PCA_MAX_FEATURES);
+    const int dk = do_pca ? p->pca_dim : d;  // the k-NN graph's dimension
     const size_t fb = Carve::round(fit_bytes(n, k));
+    const size_t zb = do_pca ? Carve::round(size_t(n) * dk * 4) : 0;
     const bool spectral = (p->flags & DRGB_FLAG_INIT_SPECTRAL) != 0;
-    const size_t kb = knn_scratch_bytes(n, d, k, p->knn_mode);
-    // the spectral layout's scratch reuses the k-NN region (free by then)
+    const size_t kb = knn_scratch_bytes(n, dk, k, p->knn_mode);
+    // the PCA's, then the k-NN's, then the spectral layout's scratch share one
+    // region (each is free by the time the next starts)
     const size_t sb = spectral ? spectral_scratch_bytes(n, int64_t(2) * n * k, c->num_sms) : 0;
-    rc = ensure_scratch(c, fb + (kb > sb ? kb : sb), st);
+    const size_t pb = do_pca ? pca_scratch_bytes(n, d) : 0;
+    size_t rb = kb > sb ? kb : sb;
+    rb = rb > pb ? rb : pb;
+    rc = ensure_scratch(c, fb + zb + rb, st);
     if (rc) return rc;
     FitBuffers b = carve_fit(c->scratch, n, k);
-    void* knn_scratch = static_cast<char*>(c->scratch) + fb;
+    float* Z = do_pca ? reinterpret_cast<float*>(static_cast<char*>(c->scratch) + fb) : nullptr;
+    void* knn_scratch = static_cast<char*>(c->scratch) + fb + zb;
 
     float a = 0.f, bb = 0.f;
     rc = drgb_find_ab(p->spread, p->min_dist, &a, &bb);
@@ -83,8 +97,14 @@ extern "C" int drgb_fit_transform(drgb_ctx* c, const float* X, int64_t n, int32_
     c->gemm_marked = false;
     rc = launch_nonfinite_scan(c, X, n * d, st);
     if (rc) return rc;
+    const float* Xk = X;
+    if (do_pca) {  // synchronises the stream (its Rayleigh-Ritz steps read back a few values)
+        rc = pca_run(c, X, n, d, dk, Z, nullptr, nullptr, nullptr, knn_scratch, st);
+        if (rc) return rc;
+        Xk = Z;
+    }
     if ((rc = stage_mark(c, 0, st))) return rc;
-    rc = knn_run(c, X, n, d, k, p->knn_mode, b.idx, b.dist, st, knn_scratch);
+    rc = knn_run(c, Xk, n, dk, k, p->knn_mode, b.idx, b.dist, st, knn_scratch);
     if (rc) return rc;
     if ((rc = stage_mark(c, 1, st))) return rc;
     rc = build_fuzzy_graph(c, b.idx, b.dist, n, k, p->n_epochs, b.row_ptr, b.col, b.w, b.q, nullptr,

@@ -28,11 +28,12 @@
 
 #include "common.cuh"
 #include "gemm.cuh"
+#include "pca.cuh"
 
 namespace drgb {
 
 static constexpr int PCA_P = 64;        // subspace block
-static constexpr int PCA_MAX_D = 1024;
+static constexpr int PCA_MAX_D = PCA_MAX_FEATURES;
 static constexpr int PCA_DEG = 10;      // Chebyshev degree per step
 static constexpr int PCA_MAXIT = 300;
 static constexpr int PCA_STALL = 40;
@@ -981,9 +982,9 @@ extern "C" int drgb_pca(drgb_ctx* c, const float* X, int64_t n, int32_t D, int32
     if (!X || !Z) return set_error(c, DRGB_ERR_INVALID, "pca: NULL pointer");
     if (!aligned(X, 4) || !aligned(Z, 4) || (components && !aligned(components, 4)) || (mean && !aligned(mean, 4)))
         return set_error(c, DRGB_ERR_INVALID, "pca: misaligned");
-    if (D < 1 || D > PCA_MAX_D || dim < 1 || dim > PCA_P - 8 || dim > D || n < 2 || round_up(n, 64) > INT32_MAX)
+    if (D < 1 || D > PCA_MAX_D || dim < 1 || dim > PCA_MAX_DIM || dim > D || n < 2 || round_up(n, 64) > INT32_MAX)
         return set_error(c, DRGB_ERR_INVALID, "pca: need 1 <= dim <= min(D, %d), D <= %d, 2 <= n < 2^31",
-                         PCA_P - 8, PCA_MAX_D);
+                         PCA_MAX_DIM, PCA_MAX_D);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = ensure_scratch(c, pca_scratch_bytes(n, D), st);
     if (rc) return rc;

@@ -56,6 +56,8 @@ extern "C" int drgb_transform(drgb_ctx* c, const float* X_train, const float* Y_
     if (k < 1 || k > DRGB_MAX_K || n_train < k + 1 || n_train + n_new > INT32_MAX / 2 || p->n_epochs < 1 ||
         p->neg < 0 || p->neg > 64)
         return set_error(c, DRGB_ERR_INVALID, "transform: bad parameters");
+    if (p->pca_dim != 0)
+        return set_error(c, DRGB_ERR_INVALID, "transform: pca_dim is not supported (project X_new first)");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t N = n_train + n_new;
     const size_t nk = size_t(n_new) * k;

@@ -46,6 +46,8 @@ def test_version_and_defaults(lib):
     p = _lib.Params()
     assert lib.drgb_default_params(C.byref(p)) == 0
     assert (p.k, p.n_epochs, p.neg, p.lr0, p.init_range) == (15, 200, 5, 1.0, 10.0)
+    assert p.pca_dim == 0                      # no PCA unless asked for
+    assert C.sizeof(p) == 64                   # the C struct: 56 bytes of fields, pca_dim, padding
     assert lib.drgb_default_params(None) == _lib.ERR_INVALID
 
 
@@ -77,6 +79,7 @@ def test_null_context_is_rejected_without_touching_a_gpu(lib):
                                  0, None) == E
     assert lib.drgb_init_embedding(None, 10, 10.0, 0, None, None) == E
     assert lib.drgb_fit_transform(None, None, 10, 2, None, None, _lib.EPOCH_CB(), None, None) == E
+    assert lib.drgb_pca(None, None, 10, 4, 2, None, None, None, None, None) == E
     assert lib.drgb_sync(None, None) == E
     assert lib.drgb_ctx_create(0, None) == E
     assert lib.drgb_ctx_destroy(None) == 0

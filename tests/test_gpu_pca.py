@@ -135,3 +135,21 @@ def test_rejects_bad_sizes(drgb):
         drgb.pca(torch.zeros((1, 80), dtype=torch.float32, device="cuda"), 2)
     with pytest.raises(drgb.DrgbError):
         drgb.pca(torch.zeros((10, 1025), dtype=torch.float32, device="cuda"), 2)
+
+
+def test_fit_with_pca_dim_equals_fit_on_the_projection(drgb):
+    # fit_transform(X, pca_dim=50) is PCA then the fit on the projection; both
+    # paths run the same fixed-order kernels, so the embeddings are identical
+    import torch
+    imgs, _ = datagen.blob_images(6_000, 1)
+    X = torch.from_numpy(imgs.astype(np.float32)).cuda()
+    Y_raw = drgb.fit_transform(X, n_epochs=60, pca_dim=50)
+    Z = drgb.pca(X, 50)[0]
+    Y_z = drgb.fit_transform(Z, n_epochs=60)
+    assert torch.equal(Y_raw, Y_z)
+    # pca_dim >= d is no PCA
+    assert torch.equal(drgb.fit_transform(Z, n_epochs=60, pca_dim=50), Y_z)
+    with pytest.raises(drgb.DrgbError):
+        drgb.fit_transform(X, n_epochs=5, pca_dim=57)
+    with pytest.raises(drgb.DrgbError):
+        drgb.fit_transform_batched(X, [0, 3000, 6000], n_epochs=5, pca_dim=50)
