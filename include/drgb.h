@@ -64,7 +64,8 @@ typedef struct drgb_params {
     int32_t flags;        /* DRGB_FLAG_* bits */
     int32_t pca_dim;      /* 0 (default): none; 1..56: fit_transform first projects X on its pca_dim
                              leading principal components (drgb_pca) when d > pca_dim (Section 3:
-                             the timed pipeline includes PCA preprocessing; 50 there) */
+                             the timed pipeline includes PCA preprocessing; Section 3.3 names
+                             the pca_dim knob) */
 } drgb_params;
 
 /* drgb_params.flags: time the epoch schedules on the actual graph before the
@@ -286,7 +287,7 @@ int drgb_spectral_init(drgb_ctx* ctx, const int32_t* row_ptr, const int32_t* col
                        float init_range, uint64_t seed, float* Y_out, double* eigvals, void* stream);
 
 /* PCA preprocessing to dim components (the paper's pipeline reduces the raw
- * features by PCA before the k-NN graph, Section 3, pca_dim = 50 for UMAP):
+ * features by PCA before the k-NN graph, Section 3; Section 3.3 names pca_dim):
  * mu = the column means of X, C = (X - mu)^T (X - mu) / (n - 1), V = the
  * eigenvectors of C for its dim largest eigenvalues in decreasing order, each
  * signed so that its entry of largest magnitude (lowest index among equal

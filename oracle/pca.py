@@ -1,8 +1,9 @@
 """PCA preprocessing (oracle side, FP64).
 
 The paper's timed pipeline starts with PCA of the raw features (Section 3,
-the per-method timings include it) and names its target width (pca_dim,
-50 for UMAP).  Restated here:
+the per-method timings include it) and exposes its target width as the
+pca_dim knob (Section 3.3); it does not state the decomposition, so it is
+restated here:
 
 * mu = the column means of X (n x D); Xc = X - mu.
 * C = Xc^T Xc / (n - 1), the sample covariance (D x D).

@@ -46,3 +46,23 @@ def test_components_are_orthonormal_eigenvectors_with_signs():
         i = int(np.argmax(np.abs(V[:, k])))
         assert V[i, k] > 0
     assert np.allclose(Z, (X - mu) @ V)
+
+
+def test_matches_the_svd_of_the_centred_data():
+    # an independent route: Xc = U S W^T gives eigenvalues S^2 / (n - 1) and
+    # components W, each up to its sign
+    g = np.random.default_rng(4)
+    X = g.normal(size=(400, 9)) @ g.normal(size=(9, 9)) + 3.0
+    Z, V, mu, vals = pca.pca(X, 4)
+    U, S, Wt = np.linalg.svd(X - X.mean(axis=0), full_matrices=False)
+    assert np.allclose(vals, S[:4] ** 2 / (len(X) - 1), rtol=1e-10)
+    for k in range(4):
+        assert abs(abs(V[:, k] @ Wt[k]) - 1.0) < 1e-10
+        assert np.allclose(np.abs(Z[:, k]), np.abs(U[:, k] * S[k]), atol=1e-9 * S[0])
+
+
+def test_sign_rule_takes_the_lowest_index_among_equal_magnitudes():
+    V = np.array([[-0.5, 0.6], [0.5, -0.6], [0.5, 0.2], [0.5, 0.1]])
+    F = pca.fix_signs(V)
+    assert np.array_equal(F[:, 0], -V[:, 0])   # |v| ties at 0.5: row 0 decides, and it is negative
+    assert np.array_equal(F[:, 1], V[:, 1])    # |v| ties at 0.6: row 0 decides, and it is positive
