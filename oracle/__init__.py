@@ -30,6 +30,9 @@ below follows the published UMAP construction, in plain NumPy/SciPy, in FP64:
                      falloff splats, premultiplied accumulation, resolve.
 * ``pca``            PCA preprocessing to pca_dim (Section 3): covariance,
                      leading eigenvectors, projection.
+* ``nndescent``      the approximate k-NN graph by NNDescent (Section 2.2):
+                     random start, neighbours-of-neighbours refinement,
+                     early stop at update rate 0.015.
 * ``mlp``            FP64 forward/backward of the learned 50-256-256-2 embedder
                      with BF16 rounding emulated where the CUDA path rounds.
 
@@ -38,4 +41,4 @@ something other than itself (library routines, closed forms, finite
 differences, invariants or published constants).  ``sgd.fit`` is a chaotic
 iteration and is pinned only through its parts and through statistics.
 """
-from . import knn, fuzzy, curve, philox, sgd, metrics, mlp, spectral, render, pca  # noqa: F401
+from . import knn, fuzzy, curve, philox, sgd, metrics, mlp, spectral, render, pca, nndescent  # noqa: F401

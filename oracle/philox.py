@@ -15,6 +15,8 @@ How the method consumes it:
   = (e, t, j' // 4, 0), word j' % 4 -> u; the sampled point is (u * n) >> 32.
 * initial coordinates of point i: key = (seed lo, seed hi), counter =
   (i, 0, 0, 1); words 0 and 1 give x and y.
+* the random start of NNDescent: counters (i, r, 0, 5), r = 0..15
+  (``nndescent.init_graph``).
 """
 from __future__ import annotations
 
