@@ -60,7 +60,9 @@ typedef struct drgb_params {
     float init_range;     /* Y0 ~ U[-init_range, init_range]^2 (default 10) */
     uint64_t seed_init;   /* Philox key of the initialisation */
     uint64_t seed_neg;    /* Philox key of the negative samples */
-    int32_t knn_mode;     /* 0 auto, 1 exact FP32 scan, 2 BF16 / 3 FP16 tensor-core + FP32 re-rank */
+    int32_t knn_mode;     /* 0 auto, 1 exact FP32 scan, 2 BF16 / 3 FP16 tensor-core + FP32 re-rank,
+                             4 approximate NNDescent (drgb_knn_nndescent with seed_init, delta 0.015,
+                             at most 30 iterations; fit_transform only) */
     int32_t flags;        /* DRGB_FLAG_* bits */
     int32_t pca_dim;      /* 0 (default): none; 1..56: fit_transform first projects X on its pca_dim
                              leading principal components (drgb_pca) when d > pca_dim (Section 3:
@@ -194,6 +196,34 @@ int drgb_knn_uncertified(drgb_ctx* ctx, int64_t* count, void* stream);
  * the number a full scan would compute; blocks skip the tiles of cells that
  * their distance bound rules out (synchronous). */
 int drgb_knn_tiles(drgb_ctx* ctx, int64_t* done, int64_t* total, void* stream);
+
+/* Approximate k-NN graph by NNDescent (Section 2.2: k random neighbours per
+ * point, refined by exploring neighbours of neighbours with a top-k
+ * selection, stopped once the update rate falls below delta = 0.015).  The
+ * iteration is synchronous, so the graph is a pure function of X, k, seed,
+ * delta and max_iter:
+ *   start      point i takes the words of Philox4x32-10 (key = seed, counter
+ *              (i, r, 0, 5), r = 0..15, words in order); a word u proposes
+ *              floor(u n / 2^32), accepted when it is not i and not yet in the
+ *              list, until k are accepted (then the smallest unused indices);
+ *   iteration  the candidates of i are its list and the lists of its
+ *              members, without i; its new list is the k candidates of
+ *              smallest (squared FP32 distance sum_j (x_cj - x_ij)^2, index);
+ *   stop       after the first iteration in which (new neighbours entering
+ *              the lists) / (n k) < delta, or after max_iter iterations.
+ *   X          n x d FP32 row-major (device), 1 <= d <= 1024
+ *   idx_out    n x k int32, dist_out n x k FP32 Euclidean (device,
+ *              caller-owned), each row in (distance, index) order
+ *   iterations NULL, or host int: the iterations run
+ *   rates      NULL, or host array of max_iter doubles: each iteration's
+ *              update rate
+ * Scratch: 12 n k bytes in the context's.  Synchronous (one synchronisation
+ * per iteration to read its update count).  Errors: as drgb_knn_graph, plus
+ * DRGB_ERR_INVALID for delta outside [0, 1], max_iter outside 1..1000 or
+ * d > 1024; DRGB_ERR_NONFINITE if X holds NaN/Inf. */
+int drgb_knn_nndescent(drgb_ctx* ctx, const float* X, int64_t n, int32_t d, int32_t k, uint64_t seed,
+                       double delta, int32_t max_iter, int32_t* idx_out, float* dist_out, int32_t* iterations,
+                       double* rates, void* stream);
 
 /* -------------------------------------------------------- fuzzy weights */
 

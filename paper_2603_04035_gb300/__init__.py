@@ -33,7 +33,7 @@ from ._lib import MAX_K, Params  # noqa: F401
 
 __all__ = ["DrgbError", "Graph", "UMAP", "knn_graph", "fuzzy_weights", "find_ab",
            "init_embedding", "embed_epoch", "embed_epochs", "fit_transform", "eval_recall",
-           "eval_trust", "eval_recall_heldout", "spectral_init", "pca", "render", "default_params", "context", "knn_uncertified", "launch_count",
+           "eval_trust", "eval_recall_heldout", "spectral_init", "pca", "knn_nndescent", "render", "default_params", "context", "knn_uncertified", "launch_count",
            "set_profiling", "stage_times", "set_tuning", "get_tuning", "set_tuning_cache",
            "tuning_cache_lookup", "tuning_cache_store", "knn_tiles", "fit_transform_batched",
            "autotune_epoch", "mlp_param_count", "mlp_init", "mlp_sample", "mlp_grad", "mlp_train",
@@ -192,6 +192,21 @@ def knn_graph(X: torch.Tensor, k: int = 15, mode: int = 0):
     _check(_lib.load().drgb_knn_graph(ctx, _ptr(X), n, d, k, mode, _ptr(idx), _ptr(dist),
                                       _stream(X.device)), ctx)
     return idx, dist
+
+
+def knn_nndescent(X: torch.Tensor, k: int = 15, seed: int = 1, delta: float = 0.015, max_iter: int = 30):
+    """Approximate k-NN graph by NNDescent: (idx int32, dist float32, update
+    rate of each iteration run)."""
+    X = _cuda(X, torch.float32, "X", 2)
+    n, d = X.shape
+    idx = torch.empty((n, k), dtype=torch.int32, device=X.device)
+    dist = torch.empty((n, k), dtype=torch.float32, device=X.device)
+    it = C.c_int32(0)
+    rates = (C.c_double * max(1, max_iter))()
+    ctx = context(X.device.index)
+    _check(_lib.load().drgb_knn_nndescent(ctx, _ptr(X), n, d, k, seed, delta, max_iter, _ptr(idx), _ptr(dist),
+                                          C.byref(it), rates, _stream(X.device)), ctx)
+    return idx, dist, [rates[t] for t in range(it.value)]
 
 
 def knn_uncertified(device=None) -> int:

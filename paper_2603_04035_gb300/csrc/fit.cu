@@ -7,6 +7,7 @@
 #include "epoch.cuh"
 #include "graph.cuh"
 #include "knn.cuh"
+#include "nndescent.cuh"
 #include "pca.cuh"
 #include "spectral.cuh"
 
@@ -66,17 +67,20 @@ extern "C" int drgb_fit_transform(drgb_ctx* c, const float* X, int64_t n, int32_
         return set_error(c, DRGB_ERR_INVALID, "fit_transform: bad parameters");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int k = p->k;
-    if (p->knn_mode < 0 || p->knn_mode > 3) return set_error(c, DRGB_ERR_INVALID, "fit_transform: bad knn_mode");
+    if (p->knn_mode < 0 || p->knn_mode > 4) return set_error(c, DRGB_ERR_INVALID, "fit_transform: bad knn_mode");
     if (p->pca_dim < 0 || p->pca_dim > PCA_MAX_DIM)
         return set_error(c, DRGB_ERR_INVALID, "fit_transform: pca_dim must be 0..%d", PCA_MAX_DIM);
     const bool do_pca = p->pca_dim > 0 && p->pca_dim < d;
     if (do_pca && d > PCA_MAX_FEATURES)
         return set_error(c, DRGB_ERR_INVALID, "fit_transform: PCA takes at most %d features", PCA_MAX_FEATURES);
     const int dk = do_pca ? p->pca_dim : d;  // the k-NN graph's dimension
+    const bool nnd = p->knn_mode == 4;
+    if (nnd && dk > NND_MAX_D)
+        return set_error(c, DRGB_ERR_INVALID, "fit_transform: NNDescent takes at most %d dimensions", NND_MAX_D);
     const size_t fb = Carve::round(fit_bytes(n, k));
     const size_t zb = do_pca ? Carve::round(size_t(n) * dk * 4) : 0;
     const bool spectral = (p->flags & DRGB_FLAG_INIT_SPECTRAL) != 0;
-    const size_t kb = knn_scratch_bytes(n, dk, k, p->knn_mode);
+    const size_t kb = nnd ? nnd_scratch_bytes(n, k) : knn_scratch_bytes(n, dk, k, p->knn_mode);
     // the PCA's, then the k-NN's, then the spectral layout's scratch share one
     // region (each is free by the time the next starts)
     const size_t sb = spectral ? spectral_scratch_bytes(n, int64_t(2) * n * k, c->num_sms) : 0;
@@ -104,7 +108,11 @@ extern "C" int drgb_fit_transform(drgb_ctx* c, const float* X, int64_t n, int32_
         Xk = Z;
     }
     if ((rc = stage_mark(c, 0, st))) return rc;
-    rc = knn_run(c, Xk, n, dk, k, p->knn_mode, b.idx, b.dist, st, knn_scratch);
+    if (nnd)  // synchronises the stream once per iteration
+        rc = nnd_run(c, Xk, n, dk, k, p->seed_init, NND_DELTA, NND_ITER_DEFAULT, b.idx, b.dist, nullptr, nullptr,
+                     knn_scratch, st);
+    else
+        rc = knn_run(c, Xk, n, dk, k, p->knn_mode, b.idx, b.dist, st, knn_scratch);
     if (rc) return rc;
     if ((rc = stage_mark(c, 1, st))) return rc;
     rc = build_fuzzy_graph(c, b.idx, b.dist, n, k, p->n_epochs, b.row_ptr, b.col, b.w, b.q, nullptr,
