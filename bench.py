@@ -406,7 +406,7 @@ def run_ours(args):
             torch.cuda.empty_cache()
             legs = {}
             for name, fn in (("10m", leg_10m), ("batched", leg_batched), ("mlp", leg_mlp), ("render", leg_render),
-                             ("raw", leg_raw)):
+                             ("raw", leg_raw), ("nndescent", leg_nndescent)):
                 try:
                     legs[name] = fn(args, drgb, dev, peaks, peak_src)
                 except Exception as e:  # a failed leg is reported, not hidden
@@ -431,7 +431,9 @@ def leg_10m(args, drgb, dev, peaks, peak_src):
     updates, nnz = graph_counts(drgb, X, T, args.knn_mode)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     m = time_fits(drgb, X, X_host, params, 1, 1, dev, flush, e2e_steps=1)
-    del X, flush
+    del flush
+    nnd = nndescent_record(drgb, X, args.knn_mode)
+    del X
     rec = fit_record("10m", X_host, T, m, updates, nnz, 1, peaks, peak_src)
     total_ms = float(sum(m["step_ms"]))
     out = {"workload": config(types.SimpleNamespace(workload="10m", knn_mode=args.knn_mode, gpus=1),
@@ -439,11 +441,50 @@ def leg_10m(args, drgb, dev, peaks, peak_src):
            "value": updates / (total_ms / 1e3), "unit": UNIT, "steps": 1, "warmup": 1,
            "ms_per_step": total_ms}
     out.update(rec)
+    out["nndescent"] = nnd
     if not args.no_cpu_baseline:
         sec, sample = oracle_fit_estimate(X_host, 16, 10_000, 3, T=T)
         out["cpu_baseline"] = {"value": updates / sec, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                "sample": "extrapolated: " + sample, "s_per_embed": sec}
     return out
+
+
+def nndescent_record(drgb, X, knn_mode):
+    """The paper's approximate k-NN (NNDescent, delta 0.015) on X against the
+    exact graph of the same rows: both timed once after a warm-up call on a
+    slice, recall = the share of the exact 15 neighbours NNDescent finds, on
+    up to 20,000 evenly strided rows."""
+    import torch
+    n = X.shape[0]
+    drgb.knn_nndescent(X[: min(n, 20_000)].contiguous(), K_NN)
+    drgb.knn_graph(X[: min(n, 20_000)].contiguous(), K_NN, mode=knn_mode)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    gi, gd, rates = drgb.knn_nndescent(X, K_NN, seed=1)
+    e1.record()
+    e1.synchronize()
+    nnd_ms = e0.elapsed_time(e1)
+    e0.record()
+    ei, ed = drgb.knn_graph(X, K_NN, mode=knn_mode)
+    e1.record()
+    e1.synchronize()
+    exact_ms = e0.elapsed_time(e1)
+    rows = torch.from_numpy(np.linspace(0, n - 1, min(n, 20_000)).astype(np.int64)).to(X.device)
+    recall = (gi[rows].unsqueeze(2) == ei[rows].unsqueeze(1)).any(2).float().mean().item()
+    return {"ms": nnd_ms, "iterations": len(rates), "update_rates": [round(r, 4) for r in rates],
+            "ms_per_iteration": nnd_ms / max(1, len(rates)), "exact_knn_ms": exact_ms,
+            "recall15_vs_exact": recall, "speed_vs_exact": exact_ms / nnd_ms}
+
+
+def leg_nndescent(args, drgb, dev, peaks=None, peak_src=None):
+    """NNDescent (the paper's k-NN, Section 2.2) against the exact k-NN graph
+    on the 70K workload; the 10M comparison is in the 10m leg."""
+    import torch
+    X = torch.from_numpy(workload(0, "70k")).to(dev)
+    rec = nndescent_record(drgb, X, args.knn_mode)
+    rec.update({"workload": f"NNDescent (delta 0.015, k = {K_NN}) on the 70K workload against the exact graph",
+                "value": rec["ms"], "unit": "ms"})
+    return rec
 
 
 def roofline_epoch(workload, n, nnz, updates, ep_ms, peaks, peak_src, T):
