@@ -163,14 +163,31 @@ __global__ void __launch_bounds__(256) pca_cmul_part_kernel(const float* __restr
     __shared__ float Cs[PCA_CROWS][PCA_KCHUNK + 1];
     const int a0 = blockIdx.x * PCA_CROWS, b0 = blockIdx.y * PCA_KCHUNK;
     const int kb = D - b0 < PCA_KCHUNK ? D - b0 : PCA_KCHUNK;
-    for (int t = threadIdx.x; t < kb * (PCA_P / 4); t += blockDim.x) {
-        const int k = t / (PCA_P / 4), c4 = t - k * (PCA_P / 4);
-        *reinterpret_cast<float4*>(&Xs[k][4 * c4]) =
-            *reinterpret_cast<const float4*>(X + int64_t(b0 + k) * PCA_P + 4 * c4);
+    // all of a thread's loads are issued before any is stored, so the block
+    // waits for one round trip instead of one per element
+    constexpr int NX = PCA_KCHUNK * (PCA_P / 4) / 256, NC = PCA_CROWS * PCA_KCHUNK / 256;
+    float4 xv[NX];
+    float cv_[NC];
+#pragma unroll
+    for (int u = 0; u < NX; ++u) {
+        const int t = threadIdx.x + u * 256, k = t / (PCA_P / 4), c4 = t % (PCA_P / 4);
+        xv[u] = k < kb ? *reinterpret_cast<const float4*>(X + int64_t(b0 + k) * PCA_P + 4 * c4)
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    for (int t = threadIdx.x; t < PCA_CROWS * kb; t += blockDim.x) {
-        const int r = t / kb, k = t - r * kb;
-        Cs[r][k] = (a0 + r < D) ? C[int64_t(a0 + r) * D + b0 + k] : 0.f;
+#pragma unroll
+    for (int u = 0; u < NC; ++u) {
+        const int t = threadIdx.x + u * 256, r = t / PCA_KCHUNK, k = t % PCA_KCHUNK;
+        cv_[u] = (k < kb && a0 + r < D) ? C[int64_t(a0 + r) * D + b0 + k] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < NX; ++u) {
+        const int t = threadIdx.x + u * 256;
+        *reinterpret_cast<float4*>(&Xs[t / (PCA_P / 4)][4 * (t % (PCA_P / 4))]) = xv[u];
+    }
+#pragma unroll
+    for (int u = 0; u < NC; ++u) {
+        const int t = threadIdx.x + u * 256;
+        Cs[t / PCA_KCHUNK][t % PCA_KCHUNK] = cv_[u];
     }
     __syncthreads();
     const int r = threadIdx.x / (PCA_P / 4), c4 = threadIdx.x % (PCA_P / 4);
@@ -219,10 +236,30 @@ __global__ void __launch_bounds__(256) pca_gram_kernel(const float* __restrict__
     const int m = PCA_P - L;
     const int a0 = blockIdx.y * PCA_GCHUNK;
     const int rows = D - a0 < PCA_GCHUNK ? D - a0 : PCA_GCHUNK;
-    for (int u = threadIdx.x; u < rows * PCA_P; u += blockDim.x) {
-        const int a = u / PCA_P, c = u - a * PCA_P;
-        As[a][c] = A[int64_t(a0 + a) * PCA_P + c];
-        Bs[a][c] = B[int64_t(a0 + a) * PCA_P + c];
+    {  // all loads issued before any store
+        constexpr int NU = PCA_GCHUNK * PCA_P / 4 / 256;
+        float4 av[NU], bv[NU];
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+            const int t = threadIdx.x + u * 256, a = t / (PCA_P / 4), c4 = t % (PCA_P / 4);
+            const bool ok = a < rows;
+            av[u] = ok ? *reinterpret_cast<const float4*>(A + int64_t(a0 + a) * PCA_P + 4 * c4)
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+            bv[u] = ok ? *reinterpret_cast<const float4*>(B + int64_t(a0 + a) * PCA_P + 4 * c4)
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+            const int t = threadIdx.x + u * 256, a = t / (PCA_P / 4), c = 4 * (t % (PCA_P / 4));
+            As[a][c] = av[u].x;
+            As[a][c + 1] = av[u].y;
+            As[a][c + 2] = av[u].z;
+            As[a][c + 3] = av[u].w;
+            Bs[a][c] = bv[u].x;
+            Bs[a][c + 1] = bv[u].y;
+            Bs[a][c + 2] = bv[u].z;
+            Bs[a][c + 3] = bv[u].w;
+        }
     }
     __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -603,79 +640,69 @@ __global__ void __launch_bounds__(PCA_JAC_THREADS) pca_jacobi_kernel(const doubl
     for (int sweep = 0; sweep < PCA_JAC_SWEEPS && Mv > 1; ++sweep) {
         if (tid == 0) s_rot = 0;
         __syncthreads();
+        static_assert(PCA_JAC_THREADS == 32 * (PCA_P / 2), "one rotation pair per warp");
         for (int r = 0; r < n1; ++r) {
-            constexpr int PPW = 32 / (PCA_JAC_THREADS / 32);  // pairs per warp
-            int pp[PPW], qq[PPW];
-            float cs[PPW], sn[PPW], dp[PPW], dq[PPW];
-#pragma unroll
-            for (int h = 0; h < PPW; ++h) {
-                const int i = warp + h * (PCA_JAC_THREADS / 32);
-                pp[h] = qq[h] = -1;
-                cs[h] = 1.f;
-                sn[h] = 0.f;
-                dp[h] = dq[h] = 0.f;
-                if (i >= half) continue;
+            // warp w's pair of this round (round-robin: position 0 fixed, the
+            // others rotating), its rotation computed in every lane
+            int p = -1, q = -1;
+            float cs = 1.f, sn = 0.f, dp = 0.f, dq = 0.f;
+            if (warp < half) {
                 int a = 0;
-                if (i > 0) {
-                    a = i - 1 + r;
+                if (warp > 0) {
+                    a = warp - 1 + r;
                     a = 1 + (a >= n1 ? a - n1 : a);
                 }
-                int b = n1 - 1 - i + r;
+                int b = n1 - 1 - warp + r;
                 b = 1 + (b >= n1 ? b - n1 : b);
-                const int p = min(a, b), q = max(a, b);
-                if (q >= m) continue;
-                const float apq = H[p][q], app = H[p][p], aqq = H[q][q];
-                if (!(fabsf(apq) > s_thr)) continue;
-                // fast divide and reciprocal square root, then one Newton
-                // step on c = 1 / sqrt(1 + t^2) so that c^2 + s^2 = 1 to
-                // rounding (t itself need not be exact)
-                const float z = __fdividef(aqq - app, 2.f * apq);
-                const float t = __fdividef(copysignf(1.f, z), fabsf(z) + __fsqrt_rn(fmaf(z, z, 1.f)));
-                const float u = fmaf(t, t, 1.f);
-                float c = rsqrtf(u);
-                c = fmaf(-0.5f * fmaf(c * c, u, -1.f), c, c);
-                pp[h] = p;
-                qq[h] = q;
-                cs[h] = c;
-                sn[h] = t * c;
-                dp[h] = fmaf(-t, apq, app);
-                dq[h] = fmaf(t, apq, aqq);
+                const int pa = min(a, b), qa = max(a, b);
+                if (qa < m) {
+                    const float apq = H[pa][qa], app = H[pa][pa], aqq = H[qa][qa];
+                    if (fabsf(apq) > s_thr) {
+                        // fast divide and reciprocal square root, then one
+                        // Newton step on c = 1 / sqrt(1 + t^2) so that
+                        // c^2 + s^2 = 1 to rounding (t itself need not be exact)
+                        const float z = __fdividef(aqq - app, 2.f * apq);
+                        const float t = __fdividef(copysignf(1.f, z), fabsf(z) + __fsqrt_rn(fmaf(z, z, 1.f)));
+                        const float u = fmaf(t, t, 1.f);
+                        float c = rsqrtf(u);
+                        c = fmaf(-0.5f * fmaf(c * c, u, -1.f), c, c);
+                        p = pa;
+                        q = qa;
+                        cs = c;
+                        sn = t * c;
+                        dp = fmaf(-t, apq, app);
+                        dq = fmaf(t, apq, aqq);
+                    }
+                }
             }
-            bool any = false;
+            if (lane == 0 && p >= 0) s_rot = 1;
+            if (p >= 0) {  // rows p, q
 #pragma unroll
-            for (int h = 0; h < PPW; ++h) any |= pp[h] >= 0;
-            if (lane == 0 && any) s_rot = 1;
-            __syncwarp();
-#pragma unroll
-            for (int h = 0; h < PPW; ++h) {  // rows p, q
-                if (pp[h] < 0) continue;
-                const int p = pp[h], q = qq[h];
-                for (int k = lane; k < m; k += 32) {
-                    const float x = H[p][k], y = H[q][k];
-                    H[p][k] = cs[h] * x - sn[h] * y;
-                    H[q][k] = sn[h] * x + cs[h] * y;
+                for (int hh = 0; hh < PCA_P / 32; ++hh) {
+                    const int k = lane + 32 * hh;
+                    if (k < m) {
+                        const float x = H[p][k], y = H[q][k];
+                        H[p][k] = cs * x - sn * y;
+                        H[q][k] = sn * x + cs * y;
+                    }
                 }
             }
             __syncthreads();
+            if (p >= 0) {  // columns p, q (the 2 x 2 block in closed form) and the eigenvectors
 #pragma unroll
-            for (int h = 0; h < PPW; ++h) {  // columns p, q and the eigenvectors
-                if (pp[h] < 0) continue;
-                const int p = pp[h], q = qq[h];
-                for (int k = lane; k < m; k += 32) {
-                    const float x = H[k][p], y = H[k][q];
-                    if (k == p) {
-                        H[p][p] = dp[h];
-                        H[p][q] = 0.f;
-                    } else if (k == q) {
-                        H[q][p] = 0.f;
-                        H[q][q] = dq[h];
-                    } else {
-                        H[k][p] = cs[h] * x - sn[h] * y;
-                        H[k][q] = sn[h] * x + cs[h] * y;
+                for (int hh = 0; hh < PCA_P / 32; ++hh) {
+                    const int k = lane + 32 * hh;
+                    if (k < m) {
+                        const float x = H[k][p], y = H[k][q];
+                        float nx = cs * x - sn * y, ny = sn * x + cs * y;
+                        nx = k == p ? dp : (k == q ? 0.f : nx);
+                        ny = k == q ? dq : (k == p ? 0.f : ny);
+                        H[k][p] = nx;
+                        H[k][q] = ny;
+                        const float u = V[k][p], w = V[k][q];
+                        V[k][p] = cs * u - sn * w;
+                        V[k][q] = sn * u + cs * w;
                     }
-                    const float u = V[k][p], w = V[k][q];
-                    V[k][p] = cs[h] * u - sn[h] * w;
-                    V[k][q] = sn[h] * u + cs[h] * w;
                 }
             }
             __syncthreads();
