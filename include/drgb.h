@@ -118,6 +118,15 @@ int drgb_wait_selftest(drgb_ctx* ctx, int64_t limit_us, int32_t arrive, void* st
 /* Bytes of scratch the context currently holds (for memory accounting). */
 int64_t drgb_ctx_scratch_bytes(const drgb_ctx* ctx);
 
+/* Cap on the context's scratch memory (no counterpart in the paper, whose
+ * runs fail with out-of-memory when a problem does not fit, Section 3.3):
+ * bytes > 0 makes every later call that would need more scratch than `bytes`
+ * fail with DRGB_ERR_WORKSPACE before anything is enqueued (the message
+ * gives both sizes), and frees the current scratch now if it is larger
+ * (waiting for the device); 0 (the default) removes the cap.  A refused call
+ * leaves the context usable.  Errors: DRGB_ERR_INVALID (NULL, bytes < 0). */
+int drgb_set_scratch_limit(drgb_ctx* ctx, int64_t bytes);
+
 /* Number of kernels this context has launched (graph replays count every
  * kernel node they contain).  Host-side counter, for launch accounting. */
 int64_t drgb_launch_count(const drgb_ctx* ctx);
@@ -365,7 +374,9 @@ int drgb_pca(drgb_ctx* ctx, const float* X, int64_t n, int32_t D, int32_t dim, f
  * Reads row_ptr[n] back to the host (one small synchronising copy on
  * `stream`) to size the context scratch; the epoch itself is asynchronous.
  * Errors: DRGB_ERR_INVALID (NULL/aliasing/misaligned pointers, n < 1,
- * neg < 0; a malformed CSR is reported by the next synchronising call). */
+ * neg < 0; a malformed CSR is reported by the next synchronising call);
+ * DRGB_ERR_NONFINITE, reported by the next synchronising call, if Y_in holds
+ * NaN or Inf (the epoch still runs; non-finite values spread through it). */
 int drgb_embed_epoch(drgb_ctx* ctx, const float* Y_in, float* Y_out, const int32_t* row_ptr,
                      const int32_t* col, const uint32_t* q, int64_t n, float a, float b, float lr,
                      int32_t neg, int32_t epoch, uint64_t seed, void* stream);
@@ -376,8 +387,8 @@ int drgb_embed_epoch(drgb_ctx* ctx, const float* Y_in, float* Y_out, const int32
  * Because the schedule and the negatives are pure functions of (t, seed),
  * running [0, t1) then [t1, T) gives bit-identical results to [0, T).
  * Like drgb_embed_epoch it reads row_ptr[n] back first.
- * Errors: as drgb_embed_epoch, plus DRGB_ERR_INVALID if
- * 0 <= t_begin <= t_end <= n_epochs does not hold. */
+ * Errors: as drgb_embed_epoch (Y is scanned on entry), plus DRGB_ERR_INVALID
+ * if 0 <= t_begin <= t_end <= n_epochs does not hold. */
 int drgb_embed_epochs(drgb_ctx* ctx, float* Y, float* Y_tmp, const int32_t* row_ptr,
                       const int32_t* col, const uint32_t* q, int64_t n, float a, float b,
                       float lr0, int32_t neg, int32_t t_begin, int32_t t_end, int32_t n_epochs,
@@ -391,7 +402,8 @@ int drgb_embed_epochs(drgb_ctx* ctx, float* Y, float* Y_tmp, const int32_t* row_
  * the device, Y_out n x 2 FP32 on the device.  Synchronous (returns after
  * Y_out is written and the device status has been checked).  `cb` may be
  * NULL; when set it is called after every epoch (this costs one host sync per
- * epoch).  Errors: as the steps above; DRGB_ERR_NONFINITE if X holds NaN/Inf;
+ * epoch).  Errors: as the steps above; DRGB_ERR_NONFINITE if X, or the
+ * returned embedding, holds NaN/Inf;
  * DRGB_ERR_INVALID for pca_dim outside 0..56.  drgb_fit_transform_batched and
  * drgb_transform take pca_dim = 0 only. */
 int drgb_fit_transform(drgb_ctx* ctx, const float* X, int64_t n, int32_t d,

@@ -21,6 +21,7 @@ struct Ctx {
     size_t smem_per_sm = 0;       // shared memory an SM can give CTAs (bytes)
     void* scratch = nullptr;      // grown on demand, 256-byte aligned carve-outs
     size_t scratch_bytes = 0;
+    size_t scratch_limit = 0;     // largest scratch the context may allocate (0 = no limit)
     int* d_status = nullptr;      // device status word (0 = ok, else DRGB_ERR_*)
     unsigned long long* d_counter = nullptr;  // [0] uncertified rows, [4] k-NN tile products computed
     int64_t knn_tiles_total = 0;              // tile products of a full scan (last tensor-core k-NN)

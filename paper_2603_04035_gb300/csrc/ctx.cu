@@ -24,6 +24,9 @@ int set_error(Ctx* c, int code, const char* fmt, ...) {
 
 int ensure_scratch(Ctx* c, size_t bytes, cudaStream_t stream) {
     if (bytes <= c->scratch_bytes) return DRGB_OK;
+    if (c->scratch_limit && bytes > c->scratch_limit)
+        return set_error(c, DRGB_ERR_WORKSPACE, "scratch of %zu bytes needed, above the context's limit of %zu bytes",
+                         bytes, c->scratch_limit);
     if (c->scratch) {
         DRGB_CUDA(c, cudaStreamSynchronize(stream));
         DRGB_CUDA(c, cudaFree(c->scratch));
@@ -31,6 +34,7 @@ int ensure_scratch(Ctx* c, size_t bytes, cudaStream_t stream) {
         c->scratch_bytes = 0;
     }
     size_t want = bytes + bytes / 8;  // headroom against frequent regrowth
+    if (c->scratch_limit && want > c->scratch_limit) want = c->scratch_limit;
     cudaError_t e = cudaMalloc(&c->scratch, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -300,6 +304,18 @@ int drgb_ctx_destroy(drgb_ctx* c) {
 const char* drgb_last_error(const drgb_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 int64_t drgb_ctx_scratch_bytes(const drgb_ctx* c) { return c ? int64_t(c->scratch_bytes) : 0; }
+
+int drgb_set_scratch_limit(drgb_ctx* c, int64_t bytes) {
+    if (!c) return DRGB_ERR_INVALID;
+    if (bytes < 0) return set_error(c, DRGB_ERR_INVALID, "scratch limit must be >= 0");
+    c->scratch_limit = size_t(bytes);
+    if (bytes && c->scratch && c->scratch_bytes > size_t(bytes)) {  // honour the cap now
+        DRGB_CUDA(c, cudaFree(c->scratch));  // waits for work that may still use it
+        c->scratch = nullptr;
+        c->scratch_bytes = 0;
+    }
+    return DRGB_OK;
+}
 
 int64_t drgb_launch_count(const drgb_ctx* c) { return c ? c->launches : 0; }
 

@@ -28,6 +28,7 @@
 
 #include "common.cuh"
 #include "epoch.cuh"
+#include "knn.cuh"  // launch_nonfinite_scan
 
 namespace drgb {
 
@@ -847,6 +848,7 @@ int drgb_embed_epoch(drgb_ctx* c, const float* Y_in, float* Y_out, const int32_t
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     EpochScratch es;
     if ((rc = epoch_state_for(c, row_ptr, n, st, &es))) return rc;
+    if ((rc = launch_nonfinite_scan(c, Y_in, 2 * n, st))) return rc;  // reported by the next synchronising call
     EpochArgs A;
     fill_args(A, row_ptr, col, q, n, a, b, neg, seed, c->d_status, es, 0, nullptr, nullptr, 0, 0);
     A.Y_in = reinterpret_cast<const float2*>(Y_in);
@@ -870,6 +872,7 @@ int drgb_embed_epochs(drgb_ctx* c, float* Y, float* Y_tmp, const int32_t* row_pt
     DRGB_CUDA(c, cudaStreamSynchronize(st));
     if (nnz < 0) return set_error(c, DRGB_ERR_INVALID, "embed_epochs: row_ptr[n] < 0");
     if ((rc = ensure_scratch(c, epoch_scratch_bytes(n, nnz, 0), st))) return rc;
+    if ((rc = launch_nonfinite_scan(c, Y, 2 * n, st))) return rc;  // reported by the next synchronising call
     return run_epochs(c, reinterpret_cast<float2*>(Y), reinterpret_cast<float2*>(Y_tmp), row_ptr, col, q, n, a,
                       b, lr0, neg, t_begin, t_end, n_epochs, seed, st, nnz, c->scratch);
 }

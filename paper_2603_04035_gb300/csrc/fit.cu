@@ -151,5 +151,8 @@ extern "C" int drgb_fit_transform(drgb_ctx* c, const float* X, int64_t n, int32_
         }
     }
     if ((rc = stage_mark(c, 4, st))) return rc;
+    // the embedding itself is scanned too: a non-finite output (which the
+    // clipped updates should never produce) is reported, not returned silently
+    if ((rc = launch_nonfinite_scan(c, Y_out, 2 * n, st))) return rc;
     return drgb_sync(c, stream);
 }

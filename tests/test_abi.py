@@ -80,6 +80,7 @@ def test_null_context_is_rejected_without_touching_a_gpu(lib):
     assert lib.drgb_init_embedding(None, 10, 10.0, 0, None, None) == E
     assert lib.drgb_fit_transform(None, None, 10, 2, None, None, _lib.EPOCH_CB(), None, None) == E
     assert lib.drgb_pca(None, None, 10, 4, 2, None, None, None, None, None) == E
+    assert lib.drgb_set_scratch_limit(None, 0) == E
     assert lib.drgb_sync(None, None) == E
     assert lib.drgb_ctx_create(0, None) == E
     assert lib.drgb_ctx_destroy(None) == 0
