@@ -386,6 +386,8 @@ def run_ours(args):
     if rank == 0:
         peaks, peak_src = load_peaks()
         rec = fit_record(args.workload, X_host, T, m, updates, nnz, args.steps, peaks, peak_src)
+        if rec["stage_ms_per_step"].get("epochs", 0) > 0:
+            rec["roofline"]["gathers"] = roofline_gathers(drgb, dev, n, updates, rec["stage_ms_per_step"]["epochs"], T)
         rec["e2e"]["value"] = e2e_value
         rec["e2e"]["ms_per_step"] = e2e_total / len(m["e2e_ms"])
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -435,6 +437,9 @@ def leg_10m(args, drgb, dev, peaks, peak_src):
     nnd = nndescent_record(drgb, X, args.knn_mode)
     del X
     rec = fit_record("10m", X_host, T, m, updates, nnz, 1, peaks, peak_src)
+    if rec["stage_ms_per_step"].get("epochs", 0) > 0:
+        rec["roofline"]["gathers"] = roofline_gathers(drgb, dev, X_host.shape[0], updates,
+                                                      rec["stage_ms_per_step"]["epochs"], T)
     total_ms = float(sum(m["step_ms"]))
     out = {"workload": config(types.SimpleNamespace(workload="10m", knn_mode=args.knn_mode, gpus=1),
                               X_host.shape[0])["workload"],
@@ -502,6 +507,23 @@ def roofline_epoch(workload, n, nnz, updates, ep_ms, peaks, peak_src, T):
             "unit": "GB/s", "frac": achieved / peak, "peak_source": f"hbm_gbs ({peak_src})",
             "bytes_per_launch": bytes_ep, "launch_ms": per_launch_s * 1e3,
             "traffic": kernel_traffic("epoch_force_kernel", "paper_2603_04035_gb300/csrc/epoch.cu", workload)}
+
+
+def roofline_gathers(drgb, dev, n, updates, ep_ms, T):
+    """The epoch kernel against the measured random-gather rate: its
+    algorithmic gathers (one 8-byte load of Y per tail and per negative of
+    every active entry) per second, over drgb_gather_probe's rate on an n x 2
+    FP32 array (the same size as Y), measured in this run."""
+    import torch
+    Y = torch.randn((n, 2), device=dev)
+    peak = drgb.gather_probe(Y, rounds=64)
+    per_launch_s = ep_ms / T / 1e3
+    gathers = updates / T * (1 + NEG)
+    achieved = gathers / per_launch_s
+    return {"kernel": "epoch_force_kernel", "bound": "gather", "achieved": achieved / 1e9, "peak": peak / 1e9,
+            "unit": "G gathers/s", "frac": achieved / peak,
+            "peak_source": "drgb_gather_probe: random 8-byte loads from an n x 2 FP32 array, largest L1 carveout, "
+                           "measured in this run", "gathers_per_launch": gathers}
 
 
 def roofline_knn(workload, d, gemm_ms, knn_ms, tiles_done, peaks, peak_src):

@@ -115,6 +115,18 @@ int drgb_sync(drgb_ctx* ctx, void* stream);
  * out of range. */
 int drgb_wait_selftest(drgb_ctx* ctx, int64_t limit_us, int32_t arrive, void* stream);
 
+/* Random-gather probe (no counterpart in the paper; the roofline denominator
+ * of the SGD epoch, whose work is one random 8-byte load of Y per tail and per
+ * negative sample): every thread the GPU holds resident (largest L1 carveout)
+ * makes rounds x 8 loads of float2 values of Y at indices drawn from
+ * multiplicative congruential streams (seed) and mapped onto [0, n) by
+ * multiply-shift.  *gathers_per_s receives the loads per second of the timed
+ * launch (one warm-up launch first).  Y: n x 2 FP32 (device, 8-byte aligned,
+ * caller-owned), 1 <= n < 2^32; 1 <= rounds <= 4096.  Synchronous.  Errors:
+ * DRGB_ERR_INVALID (NULL, misaligned, sizes). */
+int drgb_gather_probe(drgb_ctx* ctx, const float* Y, int64_t n, int32_t rounds, uint32_t seed,
+                      double* gathers_per_s, void* stream);
+
 /* Bytes of scratch the context currently holds (for memory accounting). */
 int64_t drgb_ctx_scratch_bytes(const drgb_ctx* ctx);
 

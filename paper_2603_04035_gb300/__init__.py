@@ -33,7 +33,7 @@ from ._lib import MAX_K, Params  # noqa: F401
 
 __all__ = ["DrgbError", "Graph", "UMAP", "knn_graph", "fuzzy_weights", "find_ab",
            "init_embedding", "embed_epoch", "embed_epochs", "fit_transform", "eval_recall",
-           "eval_trust", "eval_recall_heldout", "spectral_init", "pca", "knn_nndescent", "render", "default_params", "context", "knn_uncertified", "launch_count",
+           "eval_trust", "eval_recall_heldout", "spectral_init", "pca", "knn_nndescent", "gather_probe", "render", "default_params", "context", "knn_uncertified", "launch_count",
            "set_profiling", "stage_times", "set_tuning", "get_tuning", "set_tuning_cache",
            "tuning_cache_lookup", "tuning_cache_store", "knn_tiles", "fit_transform_batched",
            "autotune_epoch", "mlp_param_count", "mlp_init", "mlp_sample", "mlp_grad", "mlp_train",
@@ -207,6 +207,16 @@ def knn_nndescent(X: torch.Tensor, k: int = 15, seed: int = 1, delta: float = 0.
     _check(_lib.load().drgb_knn_nndescent(ctx, _ptr(X), n, d, k, seed, delta, max_iter, _ptr(idx), _ptr(dist),
                                           C.byref(it), rates, _stream(X.device)), ctx)
     return idx, dist, [rates[t] for t in range(it.value)]
+
+
+def gather_probe(Y: torch.Tensor, rounds: int = 256, seed: int = 1) -> float:
+    """Random 8-byte gathers per second from the rows of Y (n x 2 FP32, CUDA)."""
+    Y = _cuda(Y, torch.float32, "Y", 2)
+    out = C.c_double()
+    ctx = context(Y.device.index)
+    _check(_lib.load().drgb_gather_probe(ctx, _ptr(Y), Y.shape[0], rounds, seed, C.byref(out),
+                                         _stream(Y.device)), ctx)
+    return out.value
 
 
 def knn_uncertified(device=None) -> int:

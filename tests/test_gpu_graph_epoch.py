@@ -285,3 +285,18 @@ def test_set_tuning_rejects_unsupported_values(drgb):
     with pytest.raises(drgb.DrgbError):
         drgb.set_tuning(99, 4)
 
+
+
+def test_gather_probe(drgb):
+    # the epoch's roofline denominator: random 8-byte loads per second; an
+    # array that fits in L1 is served at least as fast as one that only fits in L2
+    import torch
+    small = torch.randn((70_000, 2), device="cuda")
+    big = torch.randn((8_000_000, 2), device="cuda")
+    rs, rb = drgb.gather_probe(small, rounds=32), drgb.gather_probe(big, rounds=32)
+    assert 1e9 < rb and 1e9 < rs < 1e13, (rs, rb)
+    assert rs > 0.8 * rb
+    with pytest.raises(drgb.DrgbError):
+        drgb.gather_probe(small, rounds=0)
+    with pytest.raises(drgb.DrgbError):
+        drgb.gather_probe(small.view(-1)[1:-1].view(-1, 2), rounds=4)   # not 8-byte aligned
