@@ -187,6 +187,109 @@ def oracle_fit_estimate(X: np.ndarray, n_query: int, n_sub: int, n_ep: int, seed
     return t_knn + t_graph + t_ep, sample
 
 
+def _cpu(value, unit, sample, **extra):
+    rec = {"value": value, "unit": unit, "cores": os.cpu_count(), "kind": "oracle", "sample": sample}
+    rec.update(extra)
+    return rec
+
+
+def oracle_pca_baseline(imgs: np.ndarray):
+    """The oracle's PCA (FP64 covariance, eigh of the 50 leading) of the whole
+    raw image set, timed in full."""
+    from oracle import pca as opca
+    t0 = time.perf_counter()
+    opca.pca(imgs, 50)
+    sec = time.perf_counter() - t0
+    return _cpu(1.0 / sec, "PCAs/s", f"oracle PCA (FP64 NumPy) of all {imgs.shape[0]} x {imgs.shape[1]} rows, "
+                "timed in full", seconds=sec)
+
+
+def oracle_nndescent_baseline(X: np.ndarray, iterations: int, n_sub: int = 2000):
+    """The oracle's NNDescent iteration timed on an n_sub-point subsample (one
+    iteration from the random start) and scaled by n / n_sub and by the GPU
+    run's iteration count: the per-point work (about k + k^2 candidates of d
+    values each) does not depend on n."""
+    from oracle import nndescent as onnd
+    Xs = np.ascontiguousarray(X[:n_sub], dtype=np.float64)
+    G0 = onnd.init_graph(n_sub, K_NN, 1)
+    t0 = time.perf_counter()
+    onnd.iterate(Xs, G0)
+    sec = (time.perf_counter() - t0) * X.shape[0] / n_sub * iterations
+    return _cpu(sec * 1e3, "ms", f"oracle NNDescent (FP64 NumPy): one iteration on the first {n_sub} points, "
+                f"x{X.shape[0] / n_sub:.0f} points, x{iterations} iterations", higher_is_better=False)
+
+
+def oracle_render_baseline(Y: np.ndarray, rgb: np.ndarray, width: int, height: int, radius: float, alpha: float,
+                           n_sub: int = 2000):
+    """The oracle's renderer: the splat loop timed on n_sub points and scaled
+    to all points, plus the resolve of the whole frame, timed in full."""
+    from oracle import render as orender
+    view = orender.fit_view(Y, width, height)
+    t0 = time.perf_counter()
+    A, C = orender.accumulate(Y[:n_sub], rgb[:n_sub], width, height, radius, alpha, view)
+    t_splat = (time.perf_counter() - t0) * Y.shape[0] / n_sub
+    t0 = time.perf_counter()
+    orender.to_u8(orender.resolve(A, C, (1.0, 1.0, 1.0)))
+    sec = t_splat + time.perf_counter() - t0
+    return _cpu(1.0 / sec, "frames/s", f"oracle renderer (FP64 Python/NumPy): splats of {n_sub} of "
+                f"{Y.shape[0]} points timed and scaled x{Y.shape[0] / n_sub:.0f}, resolve of the "
+                f"{width}x{height} frame timed in full", seconds_per_frame=sec)
+
+
+def oracle_batched_baseline(X: np.ndarray, off, T: int, n_query: int = 100, n_sub: int = 4000):
+    """The oracle's fits of all instances, from two costs measured on the
+    largest instance: exact k-NN per (query row x point) on n_query rows, and
+    graph + epochs per point on an n_sub-point subsample (2 epochs, x T/2);
+    instance b then costs knn n_b^2 + rest n_b."""
+    from oracle import fuzzy as ofuzzy, knn as oknn, sgd as osgd
+    sizes = np.diff(np.asarray(off))
+    b = int(np.argmax(sizes))
+    Xb = X[off[b]:off[b + 1]]
+    nb = Xb.shape[0]
+    g = np.random.default_rng(0)
+    rows = g.choice(nb, size=n_query, replace=False)
+    t0 = time.perf_counter()
+    oknn.knn_rows(Xb, rows, K_NN)
+    c_knn = (time.perf_counter() - t0) / (n_query * nb)
+    sub = np.sort(g.choice(nb, size=min(n_sub, nb), replace=False))
+    si, sd = oknn.knn(Xb[sub], K_NN)
+    t0 = time.perf_counter()
+    gr = ofuzzy.build_csr(si, sd, T, K_NN)
+    Y = osgd.init_embedding(len(sub), 1, 10.0)
+    for t in range(2):
+        Y = osgd.epoch(Y, gr["row_ptr"], gr["col"], gr["q"], 1.577, 0.895, 1.0 - t / T, NEG, t, 2)
+    t_rest = time.perf_counter() - t0
+    c_rest = (t_rest - 0.0) / len(sub) * T / 2
+    sec = float(sum(c_knn * float(n) ** 2 + c_rest * float(n) for n in sizes))
+    return _cpu(float(sizes.sum()) / sec, "points/s",
+                f"oracle fits (FP64 NumPy) of all {len(sizes)} instances, from costs measured on the largest "
+                f"(n = {nb}): exact k-NN of {n_query} rows (cost per row x point, x n_b^2), graph and 2 of {T} "
+                f"epochs on {len(sub)} points (cost per point, x n_b)", seconds=sec)
+
+
+def oracle_mlp_baseline(X: np.ndarray, g, n_steps: int, n_new: int, n_sub: int = 20_000):
+    """The oracle's learned form: the gradient of a 512-edge batch (BF16
+    emulated, as the GPU rounds) scaled to a 4096-edge step and by the
+    training steps, and the network's image of n_sub points scaled to the
+    held-out count."""
+    from oracle import mlp as omlp
+    rp, col, q = (v.cpu().numpy() for v in (g.row_ptr, g.col, g.q))
+    n, d = X.shape
+    P = np.random.default_rng(0).normal(size=omlp.param_count()) * 0.05
+    rows = omlp.sample(rp, col, q, n, 512, NEG, 0, 1)
+    t0 = time.perf_counter()
+    omlp.grad(P, X, rows, d, 512, NEG, 1.577, 0.895)
+    t_step = (time.perf_counter() - t0) * 4096 / 512
+    t0 = time.perf_counter()
+    omlp.embed(P, X[:n_sub], d)
+    t_inf = (time.perf_counter() - t0) * n_new / n_sub
+    return {"training": _cpu(n_steps * 4096 * (1 + NEG) / (t_step * n_steps), "sampled points/s",
+                             f"oracle gradient (FP64, BF16 emulated) of one 512-edge batch, x8 per "
+                             f"4096-edge step, x{n_steps} steps"),
+            "inference": _cpu(n_new / t_inf, "points/s",
+                              f"oracle forward (FP64, BF16 emulated) of {n_sub} points, x{n_new / n_sub:.0f}")}
+
+
 def updates_per_fit_cpu(X: np.ndarray, n_sub: int, seed: int = 0, T: int = N_EPOCHS) -> float:
     """Edge updates of one fit estimated from the oracle's graph on a subsample
     (per-point rate x n); used only where the GPU count is unavailable."""
@@ -485,8 +588,11 @@ def leg_nndescent(args, drgb, dev, peaks=None, peak_src=None):
     """NNDescent (the paper's k-NN, Section 2.2) against the exact k-NN graph
     on the 70K workload; the 10M comparison is in the 10m leg."""
     import torch
-    X = torch.from_numpy(workload(0, "70k")).to(dev)
+    X_host = workload(0, "70k")
+    X = torch.from_numpy(X_host).to(dev)
     rec = nndescent_record(drgb, X, args.knn_mode)
+    if not getattr(args, "no_cpu_baseline", False):
+        rec["cpu_baseline"] = oracle_nndescent_baseline(X_host, rec["iterations"])
     rec.update({"workload": f"NNDescent (delta 0.015, k = {K_NN}) on the 70K workload against the exact graph",
                 "value": rec["ms"], "unit": "ms"})
     return rec
@@ -616,7 +722,10 @@ def leg_batched(args, drgb, dev, peaks=None, peak_src=None, steps=1, warmup=1):
     identical = all(torch.equal(Yb[off[b]:off[b + 1]], outs[b]) for b in range(count))
     n_tot = int(off[-1])
     step_ms = float(np.mean(ms))
-    return {"workload": f"batched: {count} Gaussian-mixture instances, n_b ~ logU[1e3, 5e4] "
+    extra = {}
+    if not getattr(args, "no_cpu_baseline", False):
+        extra["cpu_baseline"] = oracle_batched_baseline(X, off, T)
+    return {**extra, "workload": f"batched: {count} Gaussian-mixture instances, n_b ~ logU[1e3, 5e4] "
                         f"(sum {n_tot}), d=50, k={K_NN}, {T} epochs, {NEG} negatives",
             "value": n_tot / (step_ms / 1e3), "unit": "points/s", "steps": steps, "warmup": warmup,
             "ms_per_step": step_ms,
@@ -667,7 +776,11 @@ def leg_render(args, drgb, dev, peaks=None, peak_src=None, frames=800):
         e1.record()
         e1.synchronize()
     ms = e0.elapsed_time(e1)
-    return {"workload": f"render: {frames} frames of the 70K embedding at 1000x1000, splat radius 2 px, "
+    extra = {}
+    if not getattr(args, "no_cpu_baseline", False):
+        extra["cpu_baseline"] = oracle_render_baseline(Y.cpu().numpy().astype(np.float64),
+                                                       rgb.cpu().numpy().astype(np.float64), 1000, 1000, 2.0, 0.8)
+    return {**extra, "workload": f"render: {frames} frames of the 70K embedding at 1000x1000, splat radius 2 px, "
                         "one frame buffer reused",
             "value": frames / (ms / 1e3), "unit": "frames/s", "ms_total": ms, "ms_per_frame": ms / frames,
             "points_per_frame": int(Y.shape[0]), "clocks": clk.summary(),
@@ -705,7 +818,11 @@ def leg_raw(args, drgb, dev, peaks=None, peak_src=None, steps=3, warmup=1):
             pca_ms.append(e0.elapsed_time(e1))
     fm, pm = float(np.mean(fit_ms)), float(np.mean(pca_ms))
     nq = 10_000
-    return {"workload": "70K from raw: 70,000 x 784 FP32 generator images -> GPU PCA to 50 -> 15-NN, "
+    extra = {}
+    if not getattr(args, "no_cpu_baseline", False):
+        extra["cpu_baseline_pca"] = oracle_pca_baseline(imgs.astype(np.float32))
+        extra["pca_gpu_per_s"] = 1e3 / pm
+    return {**extra, "workload": "70K from raw: 70,000 x 784 FP32 generator images -> GPU PCA to 50 -> 15-NN, "
                         "fuzzy graph, 500 epochs (fit_transform with pca_dim=50)",
             "value": 1e3 / fm, "unit": "embeds/s", "steps": steps, "warmup": warmup, "ms_per_embed": fm,
             "ms_pca": pm, "pca_share": pm / fm,
@@ -761,12 +878,15 @@ def leg_mlp(args, drgb, dev, peaks=None, peak_src=None, steps=3, warmup=1):
         e1.synchronize()
         plain_ms = e0.elapsed_time(e1)
     nq = 10_000
+    extra = {}
+    if not getattr(args, "no_cpu_baseline", False):
+        extra["cpu_baseline"] = oracle_mlp_baseline(X, g, n_steps, n_new)
     Ymt = drgb.mlp_embed(P, Xd)
     hm = drgb.eval_recall_heldout(Xd, Ymt, Xnd, Ym, K_NN, nq)
     hp = drgb.eval_recall_heldout(Xd, Yt, Xnd, Yp, K_NN, nq)
     qm = (drgb.eval_recall(Xnd, Ym, K_NN, nq), drgb.eval_trust(Xnd, Ym, K_NN, nq))
     qp = (drgb.eval_recall(Xnd, Yp, K_NN, nq), drgb.eval_trust(Xnd, Yp, K_NN, nq))
-    return {"workload": f"learned form: MLP 50-256-256-2 trained {args.mlp_passes} passes "
+    return {**extra, "workload": f"learned form: MLP 50-256-256-2 trained {args.mlp_passes} passes "
                         f"({n_steps} steps of 4096 edges + {NEG} negatives) on the 70K graph; "
                         f"inference on {n_new} held-out points",
             "value": n_new / (mlp_ms / 1e3), "unit": "points/s", "steps": steps, "warmup": warmup,
