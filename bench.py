@@ -511,7 +511,7 @@ def run_ours(args):
             torch.cuda.empty_cache()
             legs = {}
             for name, fn in (("10m", leg_10m), ("batched", leg_batched), ("mlp", leg_mlp), ("render", leg_render),
-                             ("raw", leg_raw), ("nndescent", leg_nndescent)):
+                             ("raw", leg_raw), ("nndescent", leg_nndescent), ("spectral", leg_spectral)):
                 try:
                     legs[name] = fn(args, drgb, dev, peaks, peak_src)
                 except Exception as e:  # a failed leg is reported, not hidden
@@ -832,6 +832,44 @@ def leg_raw(args, drgb, dev, peaks=None, peak_src=None, steps=3, warmup=1):
             "clocks": clk.summary(), "l2": "inputs 220 MB > L2",
             "paper_context": "UMAP fit_transform incl. PCA 2.60 s on Fashion-MNIST 70K x 784, M3 Ultra "
                              "(Table 1)"}
+
+
+# ---------------------------------------------------------------- spectral layout
+def leg_spectral(args, drgb, dev, peaks=None, peak_src=None, steps=3):
+    """The spectral initial layout on a connected 10,000-point sheet graph
+    (a 2-D manifold in 50-d, where the leading eigenvalues separate): the GPU
+    layout timed on the GPU's graph, the oracle's on its own graph of the same
+    points, and their leading eigenvalues side by side."""
+    import torch
+    import datagen as dg
+    X, _ = dg.sheet(10_000, 50, seed=1)
+    Xd = torch.from_numpy(X).to(dev)
+    idx, dist = drgb.knn_graph(Xd, K_NN)
+    g = drgb.fuzzy_weights(idx, dist, EPOCHS["2k"])
+    drgb.spectral_init(g, 10.0, seed=4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(steps):
+        e0.record()
+        Y, ev = drgb.spectral_init(g, 10.0, seed=4)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    rec = {"workload": "spectral layout of the fuzzy graph of a 10,000-point sheet (d = 50, k = 15)",
+           "value": float(np.mean(ms)), "unit": "ms", "higher_is_better": False, "steps": steps,
+           "eigenvalues": list(ev)}
+    if not getattr(args, "no_cpu_baseline", False):
+        from oracle import fuzzy as ofuzzy, knn as oknn, spectral as ospec
+        oi, od = oknn.knn(X, K_NN)
+        og = ofuzzy.build_csr(oi, od, EPOCHS["2k"], K_NN)
+        t0 = time.perf_counter()
+        _, ovals = ospec.spectral_init(og["row_ptr"], og["col"], og["w"], X.shape[0], 10.0, seed=4)
+        sec = time.perf_counter() - t0
+        rec["cpu_baseline"] = _cpu(sec * 1e3, "ms", "oracle spectral layout (FP64, dense eigh up to 8,000 rows, "
+                                   "else Lanczos) of its own graph of the same points, timed in full",
+                                   higher_is_better=False)
+        rec["oracle_eigenvalues"] = [float(v) for v in ovals]
+    return rec
 
 
 # ---------------------------------------------------------------- learned form
