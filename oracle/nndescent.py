@@ -21,6 +21,11 @@ CUDA path):
   the candidates of i are C(i) = G(i) united with G(j) for every j in G(i),
   without i; the new G(i) is the k candidates with the smallest (squared
   distance, index), in that order.
+* with reverse = True (the basic algorithm of Dong et al., which Section 2.2
+  cites: the join runs over each point's general neighbours, its own list
+  and the points whose lists hold it): R(i) = up to k of the points j with i
+  in G(j), the k with the smallest (squared distance, j); B(i) = G(i) united
+  with R(i); C(i) = B(i) united with B(u) for every u in B(i), without i.
 * updates u_t = sum_i |G_{t+1}(i) minus G_t(i)| (new neighbours entering the
   lists); rate_t = u_t / (n k).  The loop stops after the first iteration
   whose rate is below delta, or after max_iter iterations.
@@ -66,21 +71,45 @@ def init_graph(n: int, k: int, seed: int) -> np.ndarray:
     return G
 
 
+def reverse_lists(G: np.ndarray, d2: np.ndarray, k: int) -> np.ndarray:
+    """R(i) for every i (int64 n x k, -1 where fewer): the points j whose list
+    G(j) holds i, the k with the smallest (d2 of that entry, j)."""
+    n, kk = G.shape
+    owner = np.repeat(np.arange(n), kk)
+    tgt = G.ravel()
+    order = np.lexsort((owner, d2.ravel(), tgt))       # by target, then distance, then owner
+    tgt_s, own_s = tgt[order], owner[order]
+    lo = np.searchsorted(tgt_s, np.arange(n), side="left")
+    hi = np.searchsorted(tgt_s, np.arange(n), side="right")
+    R = np.full((n, k), -1, dtype=np.int64)
+    for i in range(n):
+        m = min(k, hi[i] - lo[i])
+        R[i, :m] = own_s[lo[i]:lo[i] + m]
+    return R
+
+
 def candidates(G: np.ndarray, i: int) -> np.ndarray:
     """C(i): G(i) and the lists of its members, without i, as a sorted set."""
     c = np.unique(np.concatenate([G[i], G[G[i]].ravel()]))
     return c[c != i]
 
 
-def iterate(X, G: np.ndarray):
+def iterate(X, G: np.ndarray, reverse: bool = False):
     """One synchronous iteration: (new lists, their squared distances, updates)."""
     X64 = np.asarray(X, dtype=np.float64)
     n, k = G.shape
     new = np.empty_like(G)
     new_d2 = np.empty((n, k))
     updates = 0
+    if reverse:
+        R = reverse_lists(G, ((X64[G] - X64[:, None, :]) ** 2).sum(axis=2), k)
+        B = [np.unique(np.concatenate([G[i], R[i][R[i] >= 0]])) for i in range(n)]
     for i in range(n):
-        c = candidates(G, i)
+        if reverse:
+            c = np.unique(np.concatenate([B[i]] + [B[u] for u in B[i]]))
+            c = c[c != i]
+        else:
+            c = candidates(G, i)
         d2 = ((X64[c] - X64[i]) ** 2).sum(axis=1)
         order = np.lexsort((c, d2))[:k]
         new[i] = c[order]
@@ -89,7 +118,8 @@ def iterate(X, G: np.ndarray):
     return new, new_d2, updates
 
 
-def nndescent(X, k: int, seed: int, delta: float = DELTA, max_iter: int = MAX_ITER, G0=None):
+def nndescent(X, k: int, seed: int, delta: float = DELTA, max_iter: int = MAX_ITER, G0=None,
+              reverse: bool = False):
     """(idx n x k, Euclidean dist n x k, iterations run, rate of each iteration).
 
     G0 replaces the random start when given (for tests)."""
@@ -99,11 +129,11 @@ def nndescent(X, k: int, seed: int, delta: float = DELTA, max_iter: int = MAX_IT
     rates: list[float] = []
     d2 = None
     for _ in range(max_iter):
-        G, d2, u = iterate(X64, G)
+        G, d2, u = iterate(X64, G, reverse)
         rates.append(u / (n * k))
         if rates[-1] < delta:
             break
     return G, np.sqrt(d2), len(rates), rates
 
 
-__all__ = ["init_graph", "candidates", "iterate", "nndescent", "TAG_NND", "DELTA", "MAX_ITER"]
+__all__ = ["init_graph", "reverse_lists", "candidates", "iterate", "nndescent", "TAG_NND", "DELTA", "MAX_ITER"]

@@ -104,3 +104,47 @@ def test_recall_against_brute_force():
     # the lists are sorted by (distance, index) with the direct distances
     assert np.all(np.diff(dist, axis=1) >= 0)
     assert np.allclose(dist, np.sqrt(((X[idx] - X[:, None, :]) ** 2).sum(axis=2)), rtol=1e-12)
+
+
+def test_reverse_lists_by_hand():
+    # points 0, 1, 2, 10 on a line, k = 1, lists [1], [0], [1], [2]:
+    # 0 is held by 1; 1 by 0 and 2 (equal distance 1: the lower index wins);
+    # 2 by 3; nobody holds 3
+    X = np.array([[0.0], [1.0], [2.0], [10.0]])
+    G = np.array([[1], [0], [1], [2]])
+    d2 = ((X[G] - X[:, None, :]) ** 2).sum(axis=2)
+    assert nnd.reverse_lists(G, d2, 1)[:, 0].tolist() == [1, 0, 3, -1]
+    R2 = nnd.reverse_lists(G, d2, 2)
+    assert R2[1].tolist() == [0, 2] and R2[3].tolist() == [-1, -1]
+
+
+def test_one_iteration_with_reverse_neighbours_by_hand():
+    # points 0, 1, 3, 10, k = 1, start [3], [3], [3], [0]: R = [3], [], [], [2]
+    # (3 is held by 0, 1, 2 at squared distances 100, 81, 49); B = {3}, {3},
+    # {3}, {0, 2}; the candidates give new lists 2, 0, 0, 2 (4 updates), where
+    # the forward-only iteration gives 3, 0, 0, 0 (2 updates)
+    X = np.array([[0.0], [1.0], [3.0], [10.0]])
+    G0 = np.array([[3], [3], [3], [0]])
+    G, d2, u = nnd.iterate(X, G0, reverse=True)
+    assert G[:, 0].tolist() == [2, 0, 0, 2] and u == 4
+    assert d2[:, 0].tolist() == [9.0, 1.0, 9.0, 49.0]
+    Gf, _, uf = nnd.iterate(X, G0)
+    assert Gf[:, 0].tolist() == [3, 0, 0, 0] and uf == 2
+
+
+def test_reverse_form_keeps_the_fixed_point_and_is_not_worse():
+    g = np.random.default_rng(4)
+    X = np.concatenate([g.normal(size=(150, 12)) + 4 * c for c in range(4)])
+    ref, ref_d = knn.knn(X, 10)
+    G, d2, u = nnd.iterate(X, ref, reverse=True)
+    assert u == 0 and np.array_equal(G, ref)
+    G = nnd.init_graph(len(X), 10, seed=7)
+    prev = np.sort(((X[G] - X[:, None, :]) ** 2).sum(axis=2), axis=1)
+    for _ in range(3):
+        G, d2, u = nnd.iterate(X, G, reverse=True)
+        assert np.all(d2 <= prev + 1e-12)
+        prev = d2
+    rec = lambda idx: np.mean([len(set(a) & set(b)) / 10 for a, b in zip(idx.tolist(), ref.tolist())])
+    f = nnd.nndescent(X, 10, seed=7)[0]
+    r = nnd.nndescent(X, 10, seed=7, reverse=True)[0]
+    assert rec(r) >= rec(f) - 0.005 and rec(r) > 0.95
