@@ -62,7 +62,8 @@ typedef struct drgb_params {
     uint64_t seed_neg;    /* Philox key of the negative samples */
     int32_t knn_mode;     /* 0 auto, 1 exact FP32 scan, 2 BF16 / 3 FP16 tensor-core + FP32 re-rank,
                              4 approximate NNDescent (drgb_knn_nndescent with seed_init, delta 0.015,
-                             at most 30 iterations; fit_transform only) */
+                             at most 30 iterations, the reverse form when k <= 16; fit_transform
+                             only) */
     int32_t flags;        /* DRGB_FLAG_* bits */
     int32_t pca_dim;      /* 0 (default): none; 1..56: fit_transform first projects X on its pca_dim
                              leading principal components (drgb_pca) when d > pca_dim (Section 3:
@@ -230,6 +231,12 @@ int drgb_knn_tiles(drgb_ctx* ctx, int64_t* done, int64_t* total, void* stream);
  *   iteration  the candidates of i are its list and the lists of its
  *              members, without i; its new list is the k candidates of
  *              smallest (squared FP32 distance sum_j (x_cj - x_ij)^2, index);
+ *   reverse    0: that candidate set (the paper's wording); 1 (k <= 16): the
+ *              basic algorithm of Dong et al., which Section 2.2 cites: R(i)
+ *              = up to k of the points whose lists hold i, the k of smallest
+ *              (squared distance, index), and the candidates of i are its
+ *              general neighbours B(i) = list + R(i) and B(u) for each u in
+ *              B(i), without i;
  *   stop       after the first iteration in which (new neighbours entering
  *              the lists) / (n k) < delta, or after max_iter iterations.
  *   X          n x d FP32 row-major (device), 1 <= d <= 1024
@@ -238,13 +245,14 @@ int drgb_knn_tiles(drgb_ctx* ctx, int64_t* done, int64_t* total, void* stream);
  *   iterations NULL, or host int: the iterations run
  *   rates      NULL, or host array of max_iter doubles: each iteration's
  *              update rate
- * Scratch: 12 n k bytes in the context's.  Synchronous (one synchronisation
- * per iteration to read its update count).  Errors: as drgb_knn_graph, plus
- * DRGB_ERR_INVALID for delta outside [0, 1], max_iter outside 1..1000 or
- * d > 1024; DRGB_ERR_NONFINITE if X holds NaN/Inf. */
+ * Scratch: 12 n k bytes in the context's (about 24 n k more with reverse).
+ * Synchronous (one synchronisation per iteration to read its update count).
+ * Errors: as drgb_knn_graph, plus DRGB_ERR_INVALID for delta outside [0, 1],
+ * max_iter outside 1..1000, d > 1024 or reverse with k > 16;
+ * DRGB_ERR_NONFINITE if X holds NaN/Inf. */
 int drgb_knn_nndescent(drgb_ctx* ctx, const float* X, int64_t n, int32_t d, int32_t k, uint64_t seed,
-                       double delta, int32_t max_iter, int32_t* idx_out, float* dist_out, int32_t* iterations,
-                       double* rates, void* stream);
+                       double delta, int32_t max_iter, int32_t reverse, int32_t* idx_out, float* dist_out,
+                       int32_t* iterations, double* rates, void* stream);
 
 /* -------------------------------------------------------- fuzzy weights */
 

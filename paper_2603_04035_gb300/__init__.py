@@ -194,9 +194,11 @@ def knn_graph(X: torch.Tensor, k: int = 15, mode: int = 0):
     return idx, dist
 
 
-def knn_nndescent(X: torch.Tensor, k: int = 15, seed: int = 1, delta: float = 0.015, max_iter: int = 30):
+def knn_nndescent(X: torch.Tensor, k: int = 15, seed: int = 1, delta: float = 0.015, max_iter: int = 30,
+                  reverse: bool = False):
     """Approximate k-NN graph by NNDescent: (idx int32, dist float32, update
-    rate of each iteration run)."""
+    rate of each iteration run); reverse=True joins over general neighbours
+    (own list and reverse neighbours, k <= 16)."""
     X = _cuda(X, torch.float32, "X", 2)
     n, d = X.shape
     idx = torch.empty((n, k), dtype=torch.int32, device=X.device)
@@ -204,8 +206,8 @@ def knn_nndescent(X: torch.Tensor, k: int = 15, seed: int = 1, delta: float = 0.
     it = C.c_int32(0)
     rates = (C.c_double * max(1, max_iter))()
     ctx = context(X.device.index)
-    _check(_lib.load().drgb_knn_nndescent(ctx, _ptr(X), n, d, k, seed, delta, max_iter, _ptr(idx), _ptr(dist),
-                                          C.byref(it), rates, _stream(X.device)), ctx)
+    _check(_lib.load().drgb_knn_nndescent(ctx, _ptr(X), n, d, k, seed, delta, max_iter, int(reverse), _ptr(idx),
+                                          _ptr(dist), C.byref(it), rates, _stream(X.device)), ctx)
     return idx, dist, [rates[t] for t in range(it.value)]
 
 

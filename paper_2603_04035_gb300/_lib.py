@@ -65,8 +65,8 @@ SIGNATURES = {
     "drgb_knn_tiles": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), vp]),
     "drgb_set_scratch_limit": (C.c_int, [vp, i64]),
     "drgb_gather_probe": (C.c_int, [vp, vp, i64, i32, C.c_uint32, C.POINTER(C.c_double), vp]),
-    "drgb_knn_nndescent": (C.c_int, [vp, vp, i64, i32, i32, u64, C.c_double, i32, vp, vp, C.POINTER(C.c_int32),
-                                     C.POINTER(C.c_double), vp]),
+    "drgb_knn_nndescent": (C.c_int, [vp, vp, i64, i32, i32, u64, C.c_double, i32, i32, vp, vp,
+                                     C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]),
     "drgb_fuzzy_weights": (C.c_int, [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, i64, vp, vp, vp]),
     "drgb_fuzzy_weights_static": (C.c_int, [vp, vp, i64, i32, i32, vp, vp, vp, vp, i64, vp, vp, vp]),
     "drgb_find_ab": (C.c_int, [f32, f32, C.POINTER(C.c_float), C.POINTER(C.c_float)]),

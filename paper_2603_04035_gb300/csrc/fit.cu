@@ -80,7 +80,8 @@ extern "C" int drgb_fit_transform(drgb_ctx* c, const float* X, int64_t n, int32_
     const size_t fb = Carve::round(fit_bytes(n, k));
     const size_t zb = do_pca ? Carve::round(size_t(n) * dk * 4) : 0;
     const bool spectral = (p->flags & DRGB_FLAG_INIT_SPECTRAL) != 0;
-    const size_t kb = nnd ? nnd_scratch_bytes(n, k) : knn_scratch_bytes(n, dk, k, p->knn_mode);
+    const bool nnd_rev = k <= 16;  // the reverse form (general neighbours) where a warp holds them
+    const size_t kb = nnd ? nnd_scratch_bytes(n, k, nnd_rev) : knn_scratch_bytes(n, dk, k, p->knn_mode);
     // the PCA's, then the k-NN's, then the spectral layout's scratch share one
     // region (each is free by the time the next starts)
     const size_t sb = spectral ? spectral_scratch_bytes(n, int64_t(2) * n * k, c->num_sms) : 0;
@@ -109,7 +110,7 @@ extern "C" int drgb_fit_transform(drgb_ctx* c, const float* X, int64_t n, int32_
     }
     if ((rc = stage_mark(c, 0, st))) return rc;
     if (nnd)  // synchronises the stream once per iteration
-        rc = nnd_run(c, Xk, n, dk, k, p->seed_init, NND_DELTA, NND_ITER_DEFAULT, b.idx, b.dist, nullptr, nullptr,
+        rc = nnd_run(c, Xk, n, dk, k, p->seed_init, NND_DELTA, NND_ITER_DEFAULT, nnd_rev, b.idx, b.dist, nullptr, nullptr,
                      knn_scratch, st);
     else
         rc = knn_run(c, Xk, n, dk, k, p->knn_mode, b.idx, b.dist, st, knn_scratch);

@@ -13,6 +13,11 @@
 //              indices, if 64 words were not enough);
 //   iteration  C(i) = G(i) united with G(j), j in G(i), without i; the new
 //              G(i) is the k candidates of smallest (squared distance, index);
+//   reverse    (optional: the basic algorithm of Dong et al., which Section
+//              2.2 cites) R(i) = up to k of the points whose lists hold i,
+//              the k of smallest (squared distance, index); the join runs
+//              over general neighbours B(i) = G(i) united with R(i): C(i) =
+//              B(i) united with B(u), u in B(i), without i;
 //   updates    the number of new neighbours entering the lists; the loop
 //              stops after the first iteration whose rate (updates / n k) is
 //              below delta, or after max_iter iterations.
@@ -43,9 +48,10 @@ struct NndLayout {
     size_t bytes;
 };
 
-static NndLayout nnd_layout(int k, int d) {
+static NndLayout nnd_layout(int k, int d, bool rev) {
     NndLayout L;
-    L.cmax = k + k * k;
+    const int b = rev ? 2 * k : k;  // general neighbours of a point
+    L.cmax = b + b * b;
     L.H = 1;
     L.logH = 0;
     while (L.H < 2 * L.cmax) {
@@ -119,9 +125,10 @@ __device__ __forceinline__ float nnd_dist2(const float* __restrict__ xc, const f
     return s;
 }
 
-template <bool PAIRS>
+template <bool PAIRS, bool REV>
 __global__ void __launch_bounds__(NND_WARPS * 32) nnd_iter_kernel(const float* __restrict__ X, int64_t n, int d,
                                                                   int k, NndLayout L, const int32_t* __restrict__ G,
+                                                                  const int32_t* __restrict__ R,
                                                                   int32_t* __restrict__ Gn, float* __restrict__ Dn,
                                                                   unsigned long long* __restrict__ updates) {
     extern __shared__ __align__(16) unsigned char nsm[];
@@ -136,15 +143,22 @@ __global__ void __launch_bounds__(NND_WARPS * 32) nnd_iter_kernel(const float* _
         for (int t = lane; t < L.H; t += 32) table[t] = -1;
         if (lane == 0) *cnt = 0;
         for (int t = lane; t < d; t += 32) xq[t] = X[i * d + t];
-        const int g = lane < k ? G[i * k + lane] : -1;
-        int nb[DRGB_MAX_K];  // lane l < k: entry l of the list of G(i)[r]
+        // lanes < k hold G(i); with REV lanes k..2k-1 hold R(i) (-1 pads)
+        const int g = lane < k ? G[i * k + lane] : ((REV && lane < 2 * k) ? R[i * k + lane - k] : -1);
+        const int nbk = REV ? 2 * k : k;
+        int nb[DRGB_MAX_K];  // lane l: entry l of the general neighbours of the point in lane r
 #pragma unroll
         for (int r = 0; r < DRGB_MAX_K; ++r) {
             const int jr = __shfl_sync(0xffffffffu, g, r);
-            nb[r] = (r < k && lane < k) ? G[int64_t(jr) * k + lane] : -1;
+            int v = -1;
+            if (r < nbk && jr >= 0) {
+                if (lane < k) v = G[int64_t(jr) * k + lane];
+                else if (REV && lane < 2 * k) v = R[int64_t(jr) * k + lane - k];
+            }
+            nb[r] = v;
         }
         __syncwarp();
-        if (lane < k) nnd_insert(g, table, L.H, L.logH, list, cnt);
+        if (g >= 0) nnd_insert(g, table, L.H, L.logH, list, cnt);
 #pragma unroll
         for (int r = 0; r < DRGB_MAX_K; ++r)
             if (nb[r] >= 0 && nb[r] != int(i)) nnd_insert(nb[r], table, L.H, L.logH, list, cnt);
@@ -186,6 +200,58 @@ __global__ void __launch_bounds__(NND_WARPS * 32) nnd_iter_kernel(const float* _
     }
 }
 
+// Squared FP32 distances of a graph's entries (the start's, for the reverse
+// lists of the first iteration).
+template <bool PAIRS>
+__global__ void nnd_graph_dist_kernel(const float* __restrict__ X, int d, int k, const int32_t* __restrict__ G,
+                                      int64_t nk, float* __restrict__ D2) {
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < nk; t += int64_t(gridDim.x) * blockDim.x)
+        D2[t] = nnd_dist2<PAIRS>(X + int64_t(G[t]) * d, X + (t / k) * d, d);
+}
+
+// Reverse lists: count the entries pointing at each point, scan, fill
+// (owner, distance) pairs in any order, then keep per point the k of
+// smallest (distance, owner), exactly, by k rounds of a warp minimum.
+__global__ void nnd_rcount_kernel(const int32_t* __restrict__ G, int64_t nk, int32_t* __restrict__ cnt) {
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < nk; t += int64_t(gridDim.x) * blockDim.x)
+        atomicAdd(&cnt[G[t]], 1);
+}
+
+__global__ void nnd_rfill_kernel(const int32_t* __restrict__ G, const float* __restrict__ D2, int64_t nk, int k,
+                                 const int32_t* __restrict__ start, int32_t* __restrict__ cur,
+                                 uint64_t* __restrict__ rkey) {
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < nk; t += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t tgt = G[t];
+        const int pos = atomicAdd(&cur[tgt], 1);
+        rkey[start[tgt] + pos] = (uint64_t(__float_as_uint(D2[t])) << 32) | uint32_t(t / k);
+    }
+}
+
+__global__ void nnd_rselect_kernel(const int32_t* __restrict__ start, const uint64_t* __restrict__ rkey, int64_t n,
+                                   int k, int32_t* __restrict__ R) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; i < n;
+         i += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+        const int32_t e0 = start[i], e1 = start[i + 1];
+        uint64_t lo = 0, mine = ~0ull;
+        for (int r = 0; r < k; ++r) {
+            uint64_t best = ~0ull;
+            for (int32_t e = e0 + lane; e < e1; e += 32) {
+                const uint64_t key = rkey[e];
+                if (key >= lo && key < best) best = key;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const uint64_t ob = __shfl_xor_sync(0xffffffffu, best, o);
+                best = ob < best ? ob : best;
+            }
+            if (lane == r) mine = best;
+            lo = best + 1;
+        }
+        if (lane < k) R[i * k + lane] = mine == ~0ull ? -1 : int32_t(uint32_t(mine));
+    }
+}
+
 __global__ void nnd_final_kernel(const int32_t* __restrict__ G, const float* __restrict__ D2, int64_t nk,
                                  int32_t* __restrict__ idx, float* __restrict__ dist) {
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < nk; t += int64_t(gridDim.x) * blockDim.x) {
@@ -194,43 +260,75 @@ __global__ void nnd_final_kernel(const int32_t* __restrict__ G, const float* __r
     }
 }
 
-size_t nnd_scratch_bytes(int64_t n, int k) {
+size_t nnd_scratch_bytes(int64_t n, int k, bool reverse) {
     const size_t nk = size_t(n) * k;
-    return 2 * Carve::round(nk * 4) + Carve::round(nk * 4) + 256 + 4096;
+    size_t b = 2 * Carve::round(nk * 4) + Carve::round(nk * 4) + 256 + 4096;
+    if (reverse)
+        b += 3 * Carve::round(size_t(n + 1) * 4) + Carve::round(scan_scratch_elems(n) * 4) + Carve::round(nk * 8) +
+             Carve::round(nk * 4);
+    return b;
 }
 
-int nnd_run(Ctx* c, const float* X, int64_t n, int d, int k, uint64_t seed, double delta, int max_iter,
+int nnd_run(Ctx* c, const float* X, int64_t n, int d, int k, uint64_t seed, double delta, int max_iter, bool rev,
             int32_t* idx_out, float* dist_out, int32_t* iters_out, double* rates_out, void* scratch,
             cudaStream_t st) {
     const size_t nk = size_t(n) * k;
+    if (rev && 2 * k > 32) return set_error(c, DRGB_ERR_INVALID, "knn_nndescent: the reverse form takes k <= 16");
     Carve cv(scratch);
     int32_t* Ga = cv.take<int32_t>(nk);
     int32_t* Gb = cv.take<int32_t>(nk);
     float* D2 = cv.take<float>(nk);
     unsigned long long* upd = cv.take<unsigned long long>(4);
-    const NndLayout L = nnd_layout(k, d);
+    int32_t *rcnt = nullptr, *rstart = nullptr, *rcur = nullptr, *stmp = nullptr, *R = nullptr;
+    uint64_t* rkey = nullptr;
+    if (rev) {
+        rcnt = cv.take<int32_t>(n + 1);
+        rstart = cv.take<int32_t>(n + 1);
+        rcur = cv.take<int32_t>(n + 1);
+        stmp = cv.take<int32_t>(scan_scratch_elems(n));
+        rkey = cv.take<uint64_t>(nk);
+        R = cv.take<int32_t>(nk);
+    }
+    const NndLayout L = nnd_layout(k, d, rev);
     int wpb = NND_WARPS;
     while (wpb > 1 && size_t(wpb) * L.bytes > NND_SMEM_CAP) wpb >>= 1;
     if (size_t(wpb) * L.bytes > NND_SMEM_CAP)
         return set_error(c, DRGB_ERR_INVALID, "knn_nndescent: k = %d, d = %d need too much shared memory", k, d);
     const bool pairs = (d % 2 == 0) && aligned(X, 8);
     const size_t smem = size_t(wpb) * L.bytes;
-    if (pairs) DRGB_CUDA(c, cudaFuncSetAttribute(nnd_iter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    else DRGB_CUDA(c, cudaFuncSetAttribute(nnd_iter_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    auto kern = pairs ? (rev ? nnd_iter_kernel<true, true> : nnd_iter_kernel<true, false>)
+                      : (rev ? nnd_iter_kernel<false, true> : nnd_iter_kernel<false, false>);
+    DRGB_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     int per_sm = 0;
-    if (pairs) DRGB_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nnd_iter_kernel<true>, wpb * 32, smem));
-    else DRGB_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nnd_iter_kernel<false>, wpb * 32, smem));
+    DRGB_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem));
     const int64_t need = (n + wpb - 1) / wpb;
     const int64_t cap = int64_t(c->num_sms) * (per_sm > 0 ? per_sm : 1) * 8;
     const unsigned grid = unsigned(need < cap ? need : cap);
 
     nnd_init_kernel<<<grid_for(n, 128, c->num_sms * 16), 128, 0, st>>>(n, k, uint32_t(seed), uint32_t(seed >> 32), Ga);
     DRGB_CHECK_LAUNCH(c);
+    const int eg = grid_for(int64_t(nk), 256, c->num_sms * 8);
+    if (rev) {  // the start's distances, for the first reverse lists
+        if (pairs) nnd_graph_dist_kernel<true><<<eg, 256, 0, st>>>(X, d, k, Ga, int64_t(nk), D2);
+        else nnd_graph_dist_kernel<false><<<eg, 256, 0, st>>>(X, d, k, Ga, int64_t(nk), D2);
+        DRGB_CHECK_LAUNCH(c);
+    }
     int it = 0;
     for (; it < max_iter;) {
+        if (rev) {
+            DRGB_CUDA(c, cudaMemsetAsync(rcnt, 0, size_t(n) * 4, st));
+            DRGB_CUDA(c, cudaMemsetAsync(rcur, 0, size_t(n) * 4, st));
+            nnd_rcount_kernel<<<eg, 256, 0, st>>>(Ga, int64_t(nk), rcnt);
+            DRGB_CHECK_LAUNCH(c);
+            int rc = exclusive_scan(c, rcnt, rstart, n, stmp, st);
+            if (rc) return rc;
+            nnd_rfill_kernel<<<eg, 256, 0, st>>>(Ga, D2, int64_t(nk), k, rstart, rcur, rkey);
+            DRGB_CHECK_LAUNCH(c);
+            nnd_rselect_kernel<<<grid_for(n * 32, 256, c->num_sms * 8), 256, 0, st>>>(rstart, rkey, n, k, R);
+            DRGB_CHECK_LAUNCH(c);
+        }
         DRGB_CUDA(c, cudaMemsetAsync(upd, 0, sizeof(unsigned long long), st));
-        if (pairs) nnd_iter_kernel<true><<<grid, wpb * 32, smem, st>>>(X, n, d, k, L, Ga, Gb, D2, upd);
-        else nnd_iter_kernel<false><<<grid, wpb * 32, smem, st>>>(X, n, d, k, L, Ga, Gb, D2, upd);
+        kern<<<grid, wpb * 32, smem, st>>>(X, n, d, k, L, Ga, R, Gb, D2, upd);
         DRGB_CHECK_LAUNCH(c);
         unsigned long long h = 0;
         DRGB_CUDA(c, cudaMemcpyAsync(&h, upd, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -252,17 +350,19 @@ int nnd_run(Ctx* c, const float* X, int64_t n, int d, int k, uint64_t seed, doub
 using namespace drgb;
 
 extern "C" int drgb_knn_nndescent(drgb_ctx* c, const float* X, int64_t n, int32_t d, int32_t k, uint64_t seed,
-                                  double delta, int32_t max_iter, int32_t* idx_out, float* dist_out,
-                                  int32_t* iterations, double* rates, void* stream) {
+                                  double delta, int32_t max_iter, int32_t reverse, int32_t* idx_out,
+                                  float* dist_out, int32_t* iterations, double* rates, void* stream) {
     int rc = check_knn_args(c, X, n, d, k, idx_out, dist_out);
     if (rc) return rc;
     if (!(delta >= 0.0 && delta <= 1.0) || max_iter < 1 || max_iter > NND_MAX_ITER || d > NND_MAX_D)
         return set_error(c, DRGB_ERR_INVALID, "knn_nndescent: need 0 <= delta <= 1, 1 <= max_iter <= %d, d <= %d",
                          NND_MAX_ITER, NND_MAX_D);
+    if (reverse && k > 16) return set_error(c, DRGB_ERR_INVALID, "knn_nndescent: the reverse form takes k <= 16");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if ((rc = ensure_scratch(c, nnd_scratch_bytes(n, k), st))) return rc;
+    if ((rc = ensure_scratch(c, nnd_scratch_bytes(n, k, reverse != 0), st))) return rc;
     if ((rc = launch_nonfinite_scan(c, X, n * d, st))) return rc;
-    rc = nnd_run(c, X, n, d, k, seed, delta, max_iter, idx_out, dist_out, iterations, rates, c->scratch, st);
+    rc = nnd_run(c, X, n, d, k, seed, delta, max_iter, reverse != 0, idx_out, dist_out, iterations, rates,
+                 c->scratch, st);
     if (rc) return rc;
     return drgb_sync(c, stream);
 }

@@ -28,9 +28,10 @@ def _mixture(n, d, seed, clusters=6, spread=4.0):
     return (centres[np.arange(n) % clusters] + g.normal(size=(n, d))).astype(np.float32)
 
 
-def _gpu(drgb, X, k, seed, delta, max_iter):
+def _gpu(drgb, X, k, seed, delta, max_iter, reverse=False):
     import torch
-    idx, dist, rates = drgb.knn_nndescent(torch.from_numpy(X).cuda(), k, seed=seed, delta=delta, max_iter=max_iter)
+    idx, dist, rates = drgb.knn_nndescent(torch.from_numpy(X).cuda(), k, seed=seed, delta=delta, max_iter=max_iter,
+                                          reverse=reverse)
     return idx.cpu().numpy().astype(np.int64), dist.cpu().numpy().astype(np.float64), rates
 
 
@@ -53,6 +54,19 @@ def test_iterations_match_oracle(drgb, d, k):
         assert len(grates) == oit == t
         _compare(X, gi, gd, oi, od, max_rows=5)
         assert np.allclose(grates, orates, atol=5 * 1.0 / (len(X) * k) + 1e-12)
+
+
+@pytest.mark.parametrize("d,k", [(20, 15), (7, 16), (50, 4)])
+def test_reverse_form_iterations_match_oracle(drgb, d, k):
+    # the reverse lists are chosen by (distance, owner) too, so an FP32/FP64
+    # near-tie there can also move a few rows; the same bounds apply
+    X = _mixture(2500, d, seed=d + 100)
+    for t in (1, 3):
+        gi, gd, grates = _gpu(drgb, X, k, seed=5, delta=0.0, max_iter=t, reverse=True)
+        oi, od, oit, orates = onnd.nndescent(X, k, seed=5, delta=0.0, max_iter=t, reverse=True)
+        assert len(grates) == oit == t
+        _compare(X, gi, gd, oi, od, max_rows=10)
+        assert np.allclose(grates, orates, atol=10 * 1.0 / (len(X) * k) + 1e-12)
 
 
 def test_converged_graph_matches_oracle_and_recall(drgb):
@@ -93,6 +107,8 @@ def test_edge_cases(drgb):
 def test_rejects_bad_arguments(drgb):
     import torch
     X = torch.zeros((100, 8), dtype=torch.float32, device="cuda")
+    with pytest.raises(drgb.DrgbError):
+        drgb.knn_nndescent(X, 17, reverse=True)
     for kw in (dict(delta=-0.1), dict(delta=1.5), dict(max_iter=0), dict(max_iter=1001)):
         with pytest.raises(drgb.DrgbError):
             drgb.knn_nndescent(X, 5, **kw)
@@ -120,6 +136,11 @@ def test_70k_recall_against_the_exact_graph(drgb):
     # the floor guards against a regression, not the method's ceiling
     assert same > 0.55, same
     assert rates[-1] < 0.015 and len(rates) < 30
+    # the reverse form (the basic algorithm of the method the paper cites)
+    # finds more of the exact neighbours
+    ri, rd, rrates = drgb.knn_nndescent(Xd, 15, seed=1, reverse=True)
+    same_rev = (ri.unsqueeze(2) == ei.unsqueeze(1)).any(dim=2).float().mean().item()
+    assert same_rev > same + 0.1, (same_rev, same)
     # every kept distance is the FP32 distance of its pair, and no list holds its own point
     rows = torch.arange(len(X), device="cuda").unsqueeze(1)
     assert not (gi == rows).any()
