@@ -181,8 +181,11 @@ int drgb_tuning_cache_store(const char* path, const char* key, int32_t epoch_war
  * records CUDA events on its stream between its stages; drgb_stage_times
  * (synchronous: waits for the events) writes up to `max` elapsed times in
  * milliseconds: [0] k-NN graph, [1] fuzzy graph, [2] initialisation,
- * [3] epoch loop, [4] the tensor-core k-NN kernel alone (0 if the exact
- * scan ran), and returns the number written (or a negative error). */
+ * [3] epoch loop, and within [0], for the tensor-core k-NN (each 0 if the
+ * exact scan ran): [4] the GEMM + selection kernel alone, [5] its ordering
+ * and operand staging, [6] the FP32 re-rank and certificate, [7] the exact
+ * re-scan of uncertified rows; returns the number written (or a negative
+ * error). */
 int drgb_set_profiling(drgb_ctx* ctx, int on);
 int drgb_stage_times(drgb_ctx* ctx, float* ms, int max);
 

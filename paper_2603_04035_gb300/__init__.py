@@ -168,7 +168,7 @@ def set_profiling(on: bool, device=None) -> None:
     _check(_lib.load().drgb_set_profiling(context(device), int(bool(on))), context(device))
 
 
-STAGES = ("knn", "fuzzy", "init", "epochs", "knn_gemm")
+STAGES = ("knn", "fuzzy", "init", "epochs", "knn_gemm", "knn_prep", "knn_rerank", "knn_rescan")
 
 
 def stage_times(device=None) -> dict:

@@ -122,6 +122,7 @@ int drgb_fit_transform_batched(drgb_ctx* c, const float* X_cat, const int64_t* o
     float a = 0.f, bb = 0.f;
     if ((rc = drgb_find_ab(p->spread, p->min_dist, &a, &bb))) return set_error(c, rc, "bad spread/min_dist");
     c->stage_marks = 0;
+    c->knn_marks = 0;
     if ((rc = launch_nonfinite_scan(c, X_cat, N * d, st))) return rc;
     if ((rc = stage_mark(c, 0, st))) return rc;
     DRGB_CUDA(c, cudaMemsetAsync(fail_count, 0, size_t(count) * 4, st));

@@ -31,9 +31,12 @@ struct Ctx {
     std::string device_name;      // for tuning-cache keys
     std::string tuning_cache;     // JSON file of tuned settings ("" = none)
     bool profiling = false;       // record stage events in fit_transform
-    cudaEvent_t stage_ev[8] = {};
+    cudaEvent_t stage_ev[11] = {};
     int stage_marks = 0;
-    bool gemm_marked = false;     // events 6, 7 bracket the tensor-core k-NN kernel
+    // events 6..10 of the tensor-core k-NN recorded in this fit (bit idx - 6):
+    // 8 its start, 6 and 7 around the GEMM kernel, 9 after the re-rank, 10
+    // after the re-scan of uncertified rows
+    unsigned knn_marks = 0;
     // The executable graph of the last epoch loop, refreshed in place
     // (cudaGraphExecUpdate) when the next loop has the same shape.
     cudaGraphExec_t epoch_exec = nullptr;

@@ -46,11 +46,11 @@ int ensure_scratch(Ctx* c, size_t bytes, cudaStream_t stream) {
 }
 
 int stage_mark(Ctx* c, int idx, cudaStream_t st) {
-    if (!c->profiling || idx < 0 || idx >= 8) return DRGB_OK;
+    if (!c->profiling || idx < 0 || idx >= 11) return DRGB_OK;
     if (!c->stage_ev[idx]) DRGB_CUDA(c, cudaEventCreate(&c->stage_ev[idx]));
     DRGB_CUDA(c, cudaEventRecord(c->stage_ev[idx], st));
     if (idx < 6 && idx + 1 > c->stage_marks) c->stage_marks = idx + 1;
-    if (idx == 7) c->gemm_marked = true;
+    if (idx >= 6) c->knn_marks |= 1u << (idx - 6);
     return DRGB_OK;
 }
 
@@ -375,7 +375,7 @@ int drgb_set_profiling(drgb_ctx* c, int on) {
     if (!c) return DRGB_ERR_INVALID;
     c->profiling = on != 0;
     c->stage_marks = 0;
-    c->gemm_marked = false;
+    c->knn_marks = 0;
     return DRGB_OK;
 }
 
@@ -386,13 +386,21 @@ int drgb_stage_times(drgb_ctx* c, float* ms, int max) {
         DRGB_CUDA(c, cudaEventSynchronize(c->stage_ev[s + 1]));
         DRGB_CUDA(c, cudaEventElapsedTime(&ms[m], c->stage_ev[s], c->stage_ev[s + 1]));
     }
-    if (m == 4 && max > 4) {  // [4]: the tensor-core k-NN kernel alone (0 if it did not run)
-        ms[4] = 0.f;
-        if (c->gemm_marked) {
-            DRGB_CUDA(c, cudaEventSynchronize(c->stage_ev[7]));
-            DRGB_CUDA(c, cudaEventElapsedTime(&ms[4], c->stage_ev[6], c->stage_ev[7]));
+    auto span = [&](int a, int b, float* out) -> int {
+        *out = 0.f;
+        if ((c->knn_marks >> (a - 6) & 1u) && (c->knn_marks >> (b - 6) & 1u)) {
+            DRGB_CUDA(c, cudaEventSynchronize(c->stage_ev[b]));
+            DRGB_CUDA(c, cudaEventElapsedTime(out, c->stage_ev[a], c->stage_ev[b]));
         }
-        m = 5;
+        return DRGB_OK;
+    };
+    // [4] the tensor-core k-NN kernel alone, [5] its ordering and staging,
+    // [6] the re-rank, [7] the re-scan of uncertified rows (0 where the
+    // tensor-core path did not run or, for [7], deferred its re-scan)
+    static const int from[4] = {6, 8, 7, 9}, to[4] = {7, 6, 9, 10};
+    for (int s = 0; m == 4 + s && m < max && s < 4; ++s, ++m) {
+        int rc = span(from[s], to[s], &ms[m]);
+        if (rc) return rc;
     }
     return m;
 }

@@ -99,7 +99,7 @@ extern "C" int drgb_fit_transform(drgb_ctx* c, const float* X, int64_t n, int32_
     if (rc) return set_error(c, rc, "fit_transform: bad spread/min_dist");
 
     c->stage_marks = 0;
-    c->gemm_marked = false;
+    c->knn_marks = 0;
     rc = launch_nonfinite_scan(c, X, n * d, st);
     if (rc) return rc;
     const float* Xk = X;

@@ -18,22 +18,6 @@ static constexpr int KNN_THREADS = 128;
 static constexpr int TP = 32;  // points per tile
 static constexpr int DC = 32;  // dimensions per tile
 
-template <int K>
-__device__ __forceinline__ void topk_insert(float (&D)[K], int32_t (&I)[K], float d, int32_t j) {
-    // precondition: d < D[K-1]
-#pragma unroll
-    for (int s = K - 1; s > 0; --s) {
-        const bool shift = d < D[s - 1];
-        const bool place = !shift && d < D[s];
-        D[s] = shift ? D[s - 1] : (place ? d : D[s]);
-        I[s] = shift ? I[s - 1] : (place ? j : I[s]);
-    }
-    if (d < D[0]) {
-        D[0] = d;
-        I[0] = j;
-    }
-}
-
 // Accumulate squared distances between this thread's query and TP database
 // points starting at p0, over all d dimensions.
 __device__ __forceinline__ void tile_distances(const float* __restrict__ X, int64_t n, int d,
@@ -113,11 +97,13 @@ knn_exact_kernel(const float* __restrict__ X, int64_t n, int d, int k,
         orow = int64_t(blockIdx.y) * n_rows + r;
     }
     // admission bound: the square of the k-th listed distance, rounded up past
-    // the rounding of the square root and of this square
+    // the rounding of the square root and of this square, plus the smallest
+    // normal number so that a k-th distance of 0 (k or more exact copies of
+    // the query) still admits the points at distance 0 (the test is strict)
     float T = INFINITY;
     if (ub && valid) {
         const float u = ub[qi * k + k - 1];
-        T = u * u * (1.0f + 1e-6f);
+        T = fmaf(u * u, 1.0f + 1e-6f, 1.17549435e-38f);
         if (!(T < INFINITY)) T = INFINITY;
     }
     float D[K];
@@ -233,18 +219,6 @@ __global__ void merge_partials_kernel(const int32_t* __restrict__ pidx, const fl
     }
 }
 
-int launch_knn_exact_rows(Ctx* c, const float* X, int64_t n, int d, int k, const int32_t* rows32,
-                          const int32_t* n_rows_dev, int64_t max_rows, int32_t* idx_out,
-                          float* dist_out, cudaStream_t st, void* part_scratch, size_t part_bytes) {
-    // The number of rows is small in practice; read it and spread the scan
-    // over database chunks so that the rows are not serialised on a few SMs.
-    int32_t cnt32 = 0;
-    DRGB_CUDA(c, cudaMemcpyAsync(&cnt32, n_rows_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    DRGB_CUDA(c, cudaStreamSynchronize(st));
-    return launch_knn_exact_rows_n(c, X, n, d, k, rows32, n_rows_dev, cnt32 < max_rows ? cnt32 : max_rows, idx_out,
-                                   dist_out, st, part_scratch, part_bytes);
-}
-
 int launch_knn_exact_rows_n(Ctx* c, const float* X, int64_t n, int d, int k, const int32_t* rows32,
                             const int32_t* n_rows_dev, int64_t cnt, int32_t* idx_out, float* dist_out,
                             cudaStream_t st, void* part_scratch, size_t part_bytes) {
@@ -279,11 +253,17 @@ int launch_knn_exact_rows_n(Ctx* c, const float* X, int64_t n, int d, int k, con
         knn_exact_kernel<32><<<grid, KNN_THREADS, 0, st>>>(X, n, d, k, nullptr, cnt, pidx, pd2, 0, rows32,
                                                           nullptr, chunk, nullptr, dist_out);
     DRGB_CHECK_LAUNCH(c);
+    return launch_merge_partials(c, pidx, pd2, cnt, int(C), k, rows32, idx_out, dist_out, st);
+}
+
+int launch_merge_partials(Ctx* c, const int32_t* pidx, const float* pd2, int64_t cnt, int C, int k,
+                          const int32_t* rows32, int32_t* idx_out, float* dist_out, cudaStream_t st) {
+    if (cnt <= 0) return DRGB_OK;
     const int mb = grid_for(cnt, 4, c->num_sms * 8);   // one warp per row, 4 warps per CTA
     if (k <= 16)
-        merge_partials_kernel<16><<<mb, 128, 0, st>>>(pidx, pd2, cnt, int(C), k, rows32, idx_out, dist_out);
+        merge_partials_kernel<16><<<mb, 128, 0, st>>>(pidx, pd2, cnt, C, k, rows32, idx_out, dist_out);
     else
-        merge_partials_kernel<32><<<mb, 128, 0, st>>>(pidx, pd2, cnt, int(C), k, rows32, idx_out, dist_out);
+        merge_partials_kernel<32><<<mb, 128, 0, st>>>(pidx, pd2, cnt, C, k, rows32, idx_out, dist_out);
     DRGB_CHECK_LAUNCH(c);
     return DRGB_OK;
 }

@@ -4,27 +4,46 @@
 
 namespace drgb {
 
+// Insert (d, j) into a list D[0..K) sorted ascending by d, dropping the last
+// entry; precondition d < D[K-1].  Equal values keep their arrival order.
+template <int K>
+__device__ __forceinline__ void topk_insert(float (&D)[K], int32_t (&I)[K], float d, int32_t j) {
+#pragma unroll
+    for (int s = K - 1; s > 0; --s) {
+        const bool shift = d < D[s - 1];
+        const bool place = !shift && d < D[s];
+        D[s] = shift ? D[s - 1] : (place ? d : D[s]);
+        I[s] = shift ? I[s - 1] : (place ? j : I[s]);
+    }
+    if (d < D[0]) {
+        D[0] = d;
+        I[0] = j;
+    }
+}
+
 int check_knn_args(Ctx* c, const float* X, int64_t n, int d, int k, const void* idx_out,
                    const void* dist_out);
 // Exact FP32 scan for the given query rows (rows == nullptr: rows 0..n_rows-1).
 int launch_knn_exact(Ctx* c, const float* X, int64_t n, int d, int k, const int64_t* rows,
                      int64_t n_rows, int32_t* idx_out, float* dist_out, bool write_sqrt,
                      cudaStream_t st);
-// Exact FP32 scan of the rows listed in rows32[0 .. *n_rows_dev) (at most
-// max_rows); results are written to those rows.  On entry each listed row of
-// idx_out/dist_out must already hold k distinct points other than the row in
-// ascending order of their FP32 distances (the direct sum over dimensions),
-// INFINITY where it has fewer: the scan keeps only points within the listed
-// k-th distance.  Synchronises `st` once to read the count, then splits the
-// scan over database chunks (partial lists in part_scratch, merged by a
-// second kernel).
-int launch_knn_exact_rows(Ctx* c, const float* X, int64_t n, int d, int k, const int32_t* rows32,
-                          const int32_t* n_rows_dev, int64_t max_rows, int32_t* idx_out,
-                          float* dist_out, cudaStream_t st, void* part_scratch, size_t part_bytes);
-// The same scan with the row count `cnt` known on the host (no synchronisation).
+// Exact FP32 scan of the rows listed in rows32[0 .. cnt) (cnt known on the
+// host; n_rows_dev, the same count on the device, is read by the single-pass
+// form).  On entry each listed row of idx_out/dist_out must already hold k
+// distinct points other than the row in ascending order of their FP32
+// distances (the direct sum over dimensions), INFINITY where it has fewer:
+// the scan keeps only points within the listed k-th distance.  The scan is
+// split over database chunks (partial lists in part_scratch, merged by a
+// second kernel); results are written to the listed rows.
 int launch_knn_exact_rows_n(Ctx* c, const float* X, int64_t n, int d, int k, const int32_t* rows32,
                             const int32_t* n_rows_dev, int64_t cnt, int32_t* idx_out, float* dist_out,
                             cudaStream_t st, void* part_scratch, size_t part_bytes);
+// Merge C partial k-lists per listed row: list l of row r at
+// (l * cnt + r) * k in pidx/pd2 (squared distances, ascending by (distance,
+// index), ended early by index -1); the k best by (distance, index) go to
+// row rows32[r] of idx_out/dist_out (Euclidean distances).
+int launch_merge_partials(Ctx* c, const int32_t* pidx, const float* pd2, int64_t cnt, int C, int k,
+                          const int32_t* rows32, int32_t* idx_out, float* dist_out, cudaStream_t st);
 // Exact FP32 k-NN of the nq rows of Q among the n rows of X (no self exclusion).
 int launch_knn_query(Ctx* c, const float* Q, int64_t nq, const float* X, int64_t n, int d, int k,
                      int32_t* idx_out, float* dist_out, cudaStream_t st);

@@ -202,17 +202,49 @@ tc_colstats_kernel(const float* __restrict__ X, int64_t n, int d, float* __restr
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    // the partials of blocks g, g + G, ... (G = TC_STAT_WARPS * 32 / 64
+    // groups per column) are summed by one thread each, eight blocks' loads
+    // in flight at a time, and the groups are then added in order
+    constexpr int G = TC_STAT_WARPS * 32 / 64;
+    __shared__ double s_gs[G][64];
+    __shared__ float s_glo[G][64], s_ghi[G][64];
+    {
+        const int c = threadIdx.x & 63, g = threadIdx.x >> 6;
+        double sg = 0.0;
+        float lo = INFINITY, hi = -INFINITY;
+        const int nb = int(gridDim.x);
+        for (int b0 = g; b0 < nb; b0 += 8 * G) {
+            float vs[8], vl[8], vh[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int b = b0 + u * G;
+                const float* pb = partial + int64_t(b < nb ? b : 0) * 3 * 64;
+                vs[u] = b < nb ? __ldcg(pb + c) : 0.f;
+                vl[u] = b < nb ? __ldcg(pb + 64 + c) : INFINITY;
+                vh[u] = b < nb ? __ldcg(pb + 128 + c) : -INFINITY;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                sg += double(vs[u]);
+                lo = fminf(lo, vl[u]);
+                hi = fmaxf(hi, vh[u]);
+            }
+        }
+        s_gs[g][c] = sg;
+        s_glo[g][c] = lo;
+        s_ghi[g][c] = hi;
+    }
+    __syncthreads();
     if (threadIdx.x < d) {
         const int c = threadIdx.x;
-        double s = 0.0;
+        double sum = 0.0;
         float lo = INFINITY, hi = -INFINITY;
-        for (int b = 0; b < int(gridDim.x); ++b) {
-            const float* pb = partial + int64_t(b) * 3 * 64;
-            s += double(__ldcg(pb + c));
-            lo = fminf(lo, __ldcg(pb + 64 + c));
-            hi = fmaxf(hi, __ldcg(pb + 128 + c));
+        for (int g = 0; g < G; ++g) {
+            sum += s_gs[g][c];
+            lo = fminf(lo, s_glo[g][c]);
+            hi = fmaxf(hi, s_ghi[g][c]);
         }
-        const float m = float(s / double(n));
+        const float m = float(sum / double(n));
         mean[c] = m;
         const float amax = fmaxf(0.f, fmaxf(hi - m, m - lo));
         atomicMax(&maxbits[2], __float_as_uint(amax));
@@ -223,7 +255,10 @@ tc_colstats_kernel(const float* __restrict__ X, int64_t n, int d, float* __restr
 // are stored in the original units (the scale S is a power of two).
 // Position i of the operands holds point perm[i] (positions >= n: padding);
 // norms and residuals are stored at the point's own index, and Xp (FP32, n x d)
-// receives the rows in position order.
+// receives the rows in position order.  A warp takes STAGE_ROWS consecutive
+// positions at a time and issues all their loads before using any.
+static constexpr int STAGE_ROWS = 4;
+
 template <bool F16>
 __global__ void tc_stage_kernel(const float* __restrict__ X, int64_t n, int64_t n_pad, int d,
                                 const float* __restrict__ mean, const int32_t* __restrict__ perm,
@@ -234,62 +269,80 @@ __global__ void tc_stage_kernel(const float* __restrict__ X, int64_t n, int64_t 
     const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
     const float S = operand_scale<F16>(maxbits), inv_S = 1.0f / S;
     const float C = F16 ? 32768.0f : 1.0f, inv_C = 1.0f / C;
+    const float m0 = lane < d ? mean[lane] : 0.f, m1 = lane + 32 < d ? mean[lane + 32] : 0.f;
     float nmax = 0.f, rmax = 0.f;
-    for (int64_t i = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n_pad; i += warps) {
-        float xc[2], xb[2];
-        float sq = 0.f, rs = 0.f, cs = 0.f;
-        const int64_t src = i < n ? int64_t(perm[i]) : -1;
+    for (int64_t i0 = (int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5)) * STAGE_ROWS; i0 < n_pad;
+         i0 += warps * STAGE_ROWS) {
+        int64_t src[STAGE_ROWS];
+        float xr[STAGE_ROWS][2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int c = lane + 32 * h;
-            float v = 0.f;
-            if (i < n && c < d) {
-                const float x = X[src * d + c];
-                Xp[i * d + c] = x;
-                v = (x - mean[c]) * inv_S;
-            }
-            xc[h] = v;
-            xb[h] = from_op<F16>(to_op<F16>(v));
-            sq = fmaf(xb[h], xb[h], sq);
-            const float r = v - xb[h];
-            rs = fmaf(r, r, rs);
-            cs = fmaf(v, v, cs);
-        }
+        for (int u = 0; u < STAGE_ROWS; ++u) src[u] = i0 + u < n ? int64_t(perm[i0 + u]) : -1;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            sq += __shfl_xor_sync(0xffffffffu, sq, o);
-            rs += __shfl_xor_sync(0xffffffffu, rs, o);
-            cs += __shfl_xor_sync(0xffffffffu, cs, o);
-        }
-        // three-way split of n / C (huge for padding rows: never selected)
-        const float nv = i < n ? sq * inv_C : (F16 ? 65504.0f : 3.0e38f);
-        const op16 nh = to_op<F16>(nv);
-        const float r1 = nv - from_op<F16>(nh);
-        const op16 nm = to_op<F16>(r1);
-        const op16 nl = to_op<F16>(r1 - from_op<F16>(nm));
+        for (int u = 0; u < STAGE_ROWS; ++u)
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int c = lane + 32 * h;
-            op16 a = to_op<F16>(xb[h]);
-            op16 b = to_op<F16>(-2.0f * xb[h]);
-            if (c == d || c == d + 1 || c == d + 2) {
-                a = to_op<F16>(C);
-                b = c == d ? nh : (c == d + 1 ? nm : nl);
+            for (int h = 0; h < 2; ++h) {
+                const int c = lane + 32 * h;
+                xr[u][h] = (src[u] >= 0 && c < d) ? X[src[u] * d + c] : 0.f;
             }
-            XA[i * TC_K + c] = a;
-            XB[i * TC_K + c] = b;
-        }
-        if (lane == 0) {
-            // residual norm, widened by the FP32 rounding of the centring and
-            // scaling and (FP16) by a possible flush of subnormal operands
-            const float flush = F16 ? 6.2e-5f * sqrtf(float(d)) : 0.f;
-            const float delta = (sqrtf(rs) * (1.0f + 1e-6f) + 2.4e-7f * sqrtf(cs) + flush) * S;
-            if (i < n) {
-                norm[src] = sq * S * S;
-                resid[src] = delta;
-                nmax = fmaxf(nmax, sq * S * S);
-                rmax = fmaxf(rmax, delta);
+#pragma unroll
+        for (int u = 0; u < STAGE_ROWS; ++u) {
+            const int64_t i = i0 + u;
+            if (i >= n_pad) break;
+            float xc[2], xb[2];
+            float sq = 0.f, rs = 0.f, cs = 0.f;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = lane + 32 * h;
+                float v = 0.f;
+                if (i < n && c < d) {
+                    const float x = xr[u][h];
+                    Xp[i * d + c] = x;
+                    v = (x - (h ? m1 : m0)) * inv_S;
+                }
+                xc[h] = v;
+                xb[h] = from_op<F16>(to_op<F16>(v));
+                sq = fmaf(xb[h], xb[h], sq);
+                const float r = v - xb[h];
+                rs = fmaf(r, r, rs);
+                cs = fmaf(v, v, cs);
             }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sq += __shfl_xor_sync(0xffffffffu, sq, o);
+                rs += __shfl_xor_sync(0xffffffffu, rs, o);
+                cs += __shfl_xor_sync(0xffffffffu, cs, o);
+            }
+            // three-way split of n / C (huge for padding rows: never selected)
+            const float nv = i < n ? sq * inv_C : (F16 ? 65504.0f : 3.0e38f);
+            const op16 nh = to_op<F16>(nv);
+            const float r1 = nv - from_op<F16>(nh);
+            const op16 nm = to_op<F16>(r1);
+            const op16 nl = to_op<F16>(r1 - from_op<F16>(nm));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = lane + 32 * h;
+                op16 a = to_op<F16>(xb[h]);
+                op16 b = to_op<F16>(-2.0f * xb[h]);
+                if (c == d || c == d + 1 || c == d + 2) {
+                    a = to_op<F16>(C);
+                    b = c == d ? nh : (c == d + 1 ? nm : nl);
+                }
+                XA[i * TC_K + c] = a;
+                XB[i * TC_K + c] = b;
+            }
+            if (lane == 0) {
+                // residual norm, widened by the FP32 rounding of the centring and
+                // scaling and (FP16) by a possible flush of subnormal operands
+                const float flush = F16 ? 6.2e-5f * sqrtf(float(d)) : 0.f;
+                const float delta = (sqrtf(rs) * (1.0f + 1e-6f) + 2.4e-7f * sqrtf(cs) + flush) * S;
+                if (i < n) {
+                    norm[src[u]] = sq * S * S;
+                    resid[src[u]] = delta;
+                    nmax = fmaxf(nmax, sq * S * S);
+                    rmax = fmaxf(rmax, delta);
+                }
+            }
+            (void)xc;
         }
     }
     if (lane == 0) {
@@ -949,6 +1002,170 @@ tc_rerank_kernel(const float* __restrict__ Xp, const int32_t* __restrict__ perm,
     }
 }
 
+// Exact re-scan of the uncertified rows over the cells they can reach.  CTA
+// (cell C, listed row r) scans the positions of cell C for row q = rows[r],
+// unless the cell's sphere lies beyond the row's re-ranked k-th distance u.
+// For a point p of C, |x_q - p| >= |x_q - c_C| - |p - c_C|; the FP32 values
+// D~ of |x_q - c_C| and r~_C >= max |p - c_C| carry a relative error below
+// 1e-5 each (sums of at most 61 squares), and a point that can enter the
+// row's k nearest has FP32 distance <= u, exact distance <= u (1 + 1.1e-5).
+// So C is skipped when D~ - r~_C - 1e-5 (D~ + r~_C) > u (1 + 2e-5).
+// The scan itself is the FP32 scan's arithmetic: squared distance
+// sum_c (x_qc - p_c)^2 over the dimensions in order, kept when below the
+// admission bound of the k-th distance, per thread sorted by distance, then
+// merged by (distance, index) within each warp and over the CTA's warps into
+// partial list (C, r), which launch_merge_partials combines over the cells.
+// Within a cell, positions follow the point index (the cell sort is stable),
+// so every per-thread list is ordered by (distance, index).  The cell's
+// points are staged 128 at a time with asynchronous copies into two
+// alternating buffers, the next tile in flight while the current one is used.
+static constexpr int RS_THREADS = 128;
+static constexpr int RS_PITCH = 65;  // floats per staged point (d <= 61), odd: conflict-free
+static constexpr size_t RS_SMEM = size_t(2) * RS_THREADS * RS_PITCH * 4;
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+template <int KL>
+__global__ void __launch_bounds__(RS_THREADS)
+tc_rescan_kernel(const float* __restrict__ X, const float* __restrict__ Xp, const int32_t* __restrict__ perm,
+                 int d, int k, const int32_t* __restrict__ rows, int cnt, const int32_t* __restrict__ cell_beg,
+                 const float* __restrict__ cell_c, const float* __restrict__ cell_r,
+                 const float* __restrict__ dist_in, int32_t* __restrict__ pidx, float* __restrict__ pd2) {
+    extern __shared__ __align__(16) float s_pts[];   // [2][RS_THREADS][RS_PITCH]
+    __shared__ float s_x[64];
+    __shared__ float s_part[RS_THREADS / 32];
+    __shared__ float s_wd[RS_THREADS / 32][32];
+    __shared__ int32_t s_wi[RS_THREADS / 32][32];
+    const int C = blockIdx.x, r = blockIdx.y, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int32_t q = rows[r];
+    const int64_t out = (int64_t(C) * cnt + r) * k;
+    for (int c = t; c < 64; c += RS_THREADS) s_x[c] = c < d ? X[int64_t(q) * d + c] : 0.f;
+    __syncthreads();
+    float part = 0.f;
+    for (int c = t; c < d; c += RS_THREADS) {
+        const float df = s_x[c] - cell_c[int64_t(C) * d + c];
+        part = fmaf(df, df, part);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) s_part[w] = part;
+    __syncthreads();
+    const float Dc = sqrtf(s_part[0] + s_part[1] + s_part[2] + s_part[3]);
+    const float rc = cell_r[C];
+    const float u = dist_in[int64_t(q) * k + k - 1];
+    if (Dc - rc - 1e-5f * (Dc + rc) > u * (1.0f + 2e-5f)) {  // false for u = INFINITY
+        if (t == 0) pidx[out] = -1;
+        return;
+    }
+    // admission bound: as in the FP32 scan's re-scan (the smallest normal
+    // number keeps a k-th distance of 0 admitting distance 0)
+    float T = fmaf(u * u, 1.0f + 1e-6f, 1.17549435e-38f);
+    if (!(T < INFINITY)) T = INFINITY;
+    float D[KL];
+    int32_t I[KL];
+#pragma unroll
+    for (int s2 = 0; s2 < KL; ++s2) {
+        D[s2] = T;
+        I[s2] = -1;
+    }
+    const int32_t b = cell_beg[C], e = cell_beg[C + 1];
+    // warp w copies points w, w + 4, ... of a tile, lanes on dimensions
+    // (lane, lane + 32)
+    auto stage = [&](int32_t p0, float* buf) {
+        const int m = e - p0 < RS_THREADS ? e - p0 : RS_THREADS;
+        for (int row = w; row < m; row += RS_THREADS / 32) {
+            const float* src = Xp + int64_t(p0 + row) * d;
+            if (lane < d) cp_async4(buf + row * RS_PITCH + lane, src + lane);
+            if (lane + 32 < d) cp_async4(buf + row * RS_PITCH + lane + 32, src + lane + 32);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (b < e) stage(b, s_pts);
+    int buf = 0;
+    for (int32_t p0 = b; p0 < e; p0 += RS_THREADS, buf ^= 1) {
+        const bool more = p0 + RS_THREADS < e;
+        if (more) {
+            stage(p0 + RS_THREADS, s_pts + (buf ^ 1) * RS_THREADS * RS_PITCH);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
+        const float* tile = s_pts + buf * RS_THREADS * RS_PITCH;
+        if (p0 + t < e) {
+            float a = 0.f;
+            for (int c = 0; c < d; ++c) {
+                const float df = s_x[c] - tile[t * RS_PITCH + c];
+                a = fmaf(df, df, a);
+            }
+            if (a < D[KL - 1]) {
+                const int32_t j = perm[p0 + t];
+                if (j != q) topk_insert<KL>(D, I, a, j);
+            }
+        }
+        __syncthreads();  // the buffer is refilled two tiles later
+    }
+    // the warp's k best by (distance, index): k rounds of a warp-wide minimum
+    // over the lanes' list heads, the owner popping its head
+    for (int s2 = 0; s2 < k; ++s2) {
+        float bd = I[0] >= 0 ? D[0] : INFINITY;
+        int32_t bi = I[0] >= 0 ? I[0] : INT32_MAX;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+            const int32_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (od < bd || (od == bd && oi < bi)) {
+                bd = od;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            s_wd[w][s2] = bd;
+            s_wi[w][s2] = bi == INT32_MAX ? -1 : bi;
+        }
+        if (I[0] >= 0 && I[0] == bi && D[0] == bd) {
+#pragma unroll
+            for (int s3 = 0; s3 < KL - 1; ++s3) {
+                D[s3] = D[s3 + 1];
+                I[s3] = I[s3 + 1];
+            }
+            D[KL - 1] = T;
+            I[KL - 1] = -1;
+        }
+    }
+    __syncthreads();
+    // the CTA's k best from the four sorted warp lists (lanes 0..3 hold heads)
+    if (w == 0) {
+        int ptr = 0;
+        for (int s2 = 0; s2 < k; ++s2) {
+            float hd = INFINITY;
+            int32_t hi = INT32_MAX;
+            if (lane < RS_THREADS / 32 && ptr < k && s_wi[lane][ptr] >= 0) {
+                hd = s_wd[lane][ptr];
+                hi = s_wi[lane][ptr];
+            }
+            float bd = hd;
+            int32_t bi = hi;
+#pragma unroll
+            for (int o = 2; o > 0; o >>= 1) {
+                const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+                const int32_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (od < bd || (od == bd && oi < bi)) {
+                    bd = od;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                pidx[out + s2] = bi == INT32_MAX ? -1 : bi;
+                pd2[out + s2] = bd;
+            }
+            if (lane < RS_THREADS / 32 && hi == bi && hd == bd && bi != INT32_MAX) ++ptr;
+        }
+    }
+}
+
 // Positions past n hold themselves (padding); with a single cell the whole
 // order is the identity and the cell covers every position.
 __global__ void tc_identity_kernel(int32_t* __restrict__ perm, int64_t n, int64_t n_pad, bool all,
@@ -1020,6 +1237,7 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
     const int K = tc_cells(n_pad, n);
     void* order_scratch = K > 1 ? cv.take<char>(knn_order_scratch_bytes(n, d, K)) : nullptr;
 
+    if ((rc = stage_mark(c, 8, st))) return rc;
     DRGB_CUDA(c, cudaMemsetAsync(maxbits, 0, 64, st));
     DRGB_CUDA(c, cudaMemsetAsync(fail_count, 0, 64, st));
     tc_colstats_kernel<<<nblk, TC_STAT_WARPS * 32, 0, st>>>(X, n, d, partial, mean, maxbits);
@@ -1030,7 +1248,7 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
                                                                            cell_r);
     DRGB_CHECK_LAUNCH(c);
     if (K > 1 && (rc = knn_order(c, X, n, d, K, perm, cell_beg, cell_c, cell_r, order_scratch, st))) return rc;
-    tc_stage_kernel<F16><<<grid_for(n_pad, 8, c->num_sms * 16), 256, 0, st>>>(X, n, n_pad, d, mean, perm, XA,
+    tc_stage_kernel<F16><<<grid_for(n_pad, 8 * STAGE_ROWS, c->num_sms * 8), 256, 0, st>>>(X, n, n_pad, d, mean, perm, XA,
                                                                               XB, norm, resid, maxbits, Xp);
     DRGB_CHECK_LAUNCH(c);
 
@@ -1073,12 +1291,33 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
         Xp, perm, n, d, k, cand_idx, cand_s, norm, resid, maxbits, lbstop, idx_out, dist_out,
         defer_rows ? defer_rows : fail_rows, defer_count ? defer_count : fail_count);
     DRGB_CHECK_LAUNCH(c);
+    if ((rc = stage_mark(c, 9, st))) return rc;
     if (defer_rows) return DRGB_OK;  // the caller re-scans the uncertified rows
-    // exact FP32 scan of the uncertified rows (row list and count on the device)
+    // exact FP32 scan of the uncertified rows (row list on the device, the
+    // count read back once): over the cells each row can reach when their
+    // partial lists fit, else over all points in chunks
     DRGB_CUDA(c, cudaMemcpyAsync(c->d_counter, fail_count, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-    rc = launch_knn_exact_rows(c, X, n, d, k, fail_rows, fail_count, n, idx_out, dist_out, st, part,
-                               TC_PART_BYTES);
-    return rc;
+    int32_t cnt32 = 0;
+    DRGB_CUDA(c, cudaMemcpyAsync(&cnt32, fail_count, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    DRGB_CUDA(c, cudaStreamSynchronize(st));
+    const int64_t cnt = cnt32 < n ? cnt32 : n;
+    if (cnt > 0 && K > 1 && size_t(cnt) * K * k * 8 + 1024 <= TC_PART_BYTES && cnt <= 65535) {
+        Carve pc(part);
+        int32_t* pidx = pc.take<int32_t>(size_t(cnt) * K * k);
+        float* pd2 = pc.take<float>(size_t(cnt) * K * k);
+        const dim3 grid(static_cast<unsigned>(K), static_cast<unsigned>(cnt));
+        auto rs = k <= 16 ? tc_rescan_kernel<16> : tc_rescan_kernel<32>;
+        DRGB_CUDA(c, cudaFuncSetAttribute(rs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(RS_SMEM)));
+        rs<<<grid, RS_THREADS, RS_SMEM, st>>>(X, Xp, perm, d, k, fail_rows, int(cnt), cell_beg, cell_c, cell_r,
+                                              dist_out, pidx, pd2);
+        DRGB_CHECK_LAUNCH(c);
+        rc = launch_merge_partials(c, pidx, pd2, cnt, K, k, fail_rows, idx_out, dist_out, st);
+    } else {
+        rc = launch_knn_exact_rows_n(c, X, n, d, k, fail_rows, fail_count, cnt, idx_out, dist_out, st, part,
+                                     TC_PART_BYTES);
+    }
+    if (rc) return rc;
+    return stage_mark(c, 10, st);
 }
 
 int knn_tc(Ctx* c, const float* X, int64_t n, int d, int k, bool f16, int32_t* idx_out, float* dist_out,

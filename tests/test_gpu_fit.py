@@ -113,3 +113,24 @@ def test_umap_class_front_end(drgb):
     X, _ = datagen.mixture(400, 16, 4, seed=3)
     Y = drgb.UMAP(n_epochs=30, seed=4).fit_transform(X)
     assert tuple(Y.shape) == (400, 2)
+
+
+def test_stage_times_split_the_knn_stage(drgb):
+    # the tensor-core k-NN's sub-stages (ordering and staging, GEMM, re-rank,
+    # re-scan) are recorded inside the k-NN stage and add up to at most it
+    import torch
+    X = torch.from_numpy(datagen.mixture(5000, 50, 10, 1)[0]).cuda()
+    drgb.set_profiling(True)
+    try:
+        drgb.fit_transform(X, n_epochs=20, knn_mode=3)
+        st = drgb.stage_times()
+        drgb.fit_transform(X, n_epochs=20, knn_mode=1)
+        st1 = drgb.stage_times()
+    finally:
+        drgb.set_profiling(False)
+    parts = ("knn_gemm", "knn_prep", "knn_rerank", "knn_rescan")
+    assert set(parts) <= set(st), st
+    assert all(st[p] > 0 for p in parts[:3]) and st["knn_rescan"] >= 0
+    assert sum(st[p] for p in parts) <= st["knn"] * 1.001 + 1e-3, st
+    # the exact scan records no sub-stage
+    assert all(st1[p] == 0 for p in parts), st1

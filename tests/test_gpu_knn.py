@@ -62,12 +62,18 @@ def test_tensor_core_ragged_tiles(drgb, n, d, k, mode):
 
 
 @pytest.mark.parametrize("mode", [2, 3])
-def test_tensor_core_matches_exact_scan_bitwise(drgb, mode):
-    # both paths finish with the same FP32 arithmetic on the same candidates
-    X, _ = datagen.mixture(6000, 50, 12, seed=5)
+@pytest.mark.parametrize("d", [50, 49])
+def test_tensor_core_matches_exact_scan_bitwise(drgb, mode, d):
+    # both paths finish with the same FP32 arithmetic on the same candidates,
+    # and the rows the certificate leaves are re-scanned over the cells they
+    # can reach (an odd d as well as an even one)
+    X, _ = datagen.mixture(6000, d, 12, seed=5)
     gi2, gd2 = _run(drgb, X, 15, mode)
+    unc = drgb.knn_uncertified()
     gi1, gd1 = _run(drgb, X, 15, 1)
     assert np.array_equal(gi1, gi2) and np.array_equal(gd1, gd2)
+    if mode == 2:
+        assert unc > 0   # the BF16 certificate leaves rows to the re-scan
 
 
 @pytest.mark.parametrize("mode", [2, 3])
@@ -92,6 +98,24 @@ def test_planted_duplicates_resolve_by_index(drgb, mode):
     oi, od = oknn.knn(X, 15)
     assert np.array_equal(gi, oi)          # exact ties are broken by index on both sides
     assert np.all(gd[:40, 0] == 0.0) and np.all(gd[:5, 2] == 0.0)
+
+
+@pytest.mark.parametrize("mode", [2, 3])
+def test_many_exact_copies_through_the_rescan(drgb, mode):
+    # 40 copies of one point among 6,000: for each copy the other copies fill
+    # all 32 candidate slots at distance 0, so no certificate can hold and
+    # the row goes to the exact re-scan with a k-th distance of 0; the
+    # re-scan must still admit the points at distance exactly 0
+    g = np.random.default_rng(11)
+    X = g.normal(size=(6000, 20)).astype(np.float32)
+    copies = np.arange(100, 6000, 150)[:40]
+    X[copies] = X[copies[0]]
+    gi, gd = _run(drgb, X, 15, mode)
+    oi, od = oknn.knn_rows(X, copies, 15)
+    assert np.array_equal(gi[copies], oi) and np.all(gd[copies] == 0.0)
+    rows = np.arange(0, 6000, 97)
+    oi, od = oknn.knn_rows(X, rows, 15)
+    check_knn(X, rows, gi[rows], gd[rows], oi, od, 15)
 
 
 def test_all_points_identical(drgb):
