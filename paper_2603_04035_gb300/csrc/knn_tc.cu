@@ -913,10 +913,28 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 // distance over the dimensions in order (the FP32 scan's arithmetic, so every
 // mode returns the same bits), and a bitonic network over the lanes orders the
 // candidates by (distance, index).
-static constexpr int RR_WARPS = 4;
-static constexpr int RR_PITCH = 65;  // floats per staged row (d <= 64), odd: conflict-free
+// Asynchronous 4-byte copy global -> shared (completes at cp.async.wait_group).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
 
-template <bool F16>
+static constexpr int RR_WARPS = 4;
+
+// Floats per staged row.  Odd d: d rounded up to an odd count, so that the
+// lanes of a warp reading one column of 32 rows hit 32 distinct banks.  Even
+// d (rows read as float pairs): twice an odd number of pairs, which keeps the
+// 64-bit reads of a half-warp on distinct bank pairs.
+static inline int rr_pitch(int d) { return (d & 1) ? d : 2 * ((d >> 1) | 1); }
+static inline size_t rr_smem(int d) { return size_t(RR_WARPS) * (32 * rr_pitch(d) + 64) * 4; }
+
+__device__ __forceinline__ void cp_async8(float* dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// PAIRS (even d): rows are copied and read as float pairs, lane l taking
+// dimensions (2l, 2l + 1); the dimensions are still added in order, so both
+// forms give the same bits.
+template <bool F16, bool PAIRS>
 __global__ void __launch_bounds__(RR_WARPS * 32)
 tc_rerank_kernel(const float* __restrict__ Xp, const int32_t* __restrict__ perm, int64_t n, int d, int k,
                  const int32_t* __restrict__ cand_pos, const float* __restrict__ cand_s,
@@ -924,9 +942,11 @@ tc_rerank_kernel(const float* __restrict__ Xp, const int32_t* __restrict__ perm,
                  const unsigned int* __restrict__ maxbits, const float* __restrict__ lbstop,
                  int32_t* __restrict__ idx_out, float* __restrict__ dist_out, int32_t* __restrict__ fail_rows,
                  int32_t* __restrict__ fail_count) {
-    __shared__ float s_rows[RR_WARPS][32 * RR_PITCH];
-    __shared__ float s_q[RR_WARPS][64];
+    extern __shared__ __align__(16) float s_rr[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pitch = PAIRS ? 2 * ((d >> 1) | 1) : d;
+    float* s_rows = s_rr + w * (32 * pitch + 64);   // [32][pitch] candidate rows
+    float* s_q = s_rows + 32 * pitch;               // [64] the query row
     const float n_max = __uint_as_float(maxbits[0]);
     const float r_max = __uint_as_float(maxbits[1]);
     const float S = operand_scale<F16>(maxbits);
@@ -936,33 +956,53 @@ tc_rerank_kernel(const float* __restrict__ Xp, const int32_t* __restrict__ perm,
         const int64_t i = perm[p];
         const int32_t q = cand_pos[p * TC_KP + lane];
         const bool valid = q >= 0 && q < n && q != p;
-        // stage the query row and the 32 candidate rows
-        for (int c = lane; c < d; c += 32) s_q[w][c] = Xp[p * d + c];
-        {
-            // every lane loads dimensions (lane, lane + 32) of all 32 rows
-            // before storing any, so the 64 loads are in flight together
-            float v0[32], v1[32];
-            const int qv = valid ? q : -1;
-#pragma unroll
+        // stage the query row and the 32 candidate rows with asynchronous
+        // copies: all of a lane's copies are in flight together and hold no
+        // registers
+        const int qv = valid ? q : -1;
+        if constexpr (PAIRS) {
+            const int h = d >> 1;
+            if (lane < h) cp_async8(s_q + 2 * lane, Xp + p * d + 2 * lane);
+#pragma unroll 8
             for (int t = 0; t < 32; ++t) {
                 const int32_t qt = __shfl_sync(0xffffffffu, qv, t);
-                v0[t] = (qt >= 0 && lane < d) ? Xp[int64_t(qt) * d + lane] : 0.f;
-                v1[t] = (qt >= 0 && lane + 32 < d) ? Xp[int64_t(qt) * d + lane + 32] : 0.f;
+                if (qt >= 0 && lane < h) cp_async8(s_rows + t * pitch + 2 * lane, Xp + int64_t(qt) * d + 2 * lane);
             }
-#pragma unroll
+        } else {
+            for (int c = lane; c < d; c += 32) cp_async4(s_q + c, Xp + p * d + c);
+#pragma unroll 8
             for (int t = 0; t < 32; ++t) {
-                s_rows[w][t * RR_PITCH + lane] = v0[t];
-                s_rows[w][t * RR_PITCH + lane + 32] = v1[t];
+                const int32_t qt = __shfl_sync(0xffffffffu, qv, t);
+                if (qt >= 0) {
+                    const float* src = Xp + int64_t(qt) * d;
+                    if (lane < d) cp_async4(s_rows + t * pitch + lane, src + lane);
+                    if (lane + 32 < d) cp_async4(s_rows + t * pitch + lane + 32, src + lane + 32);
+                }
             }
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncwarp();
         float a = INFINITY;
         int32_t jj = INT32_MAX;
         if (valid) {
             a = 0.f;
-            for (int c = 0; c < d; ++c) {
-                const float df = s_q[w][c] - s_rows[w][lane * RR_PITCH + c];
-                a = fmaf(df, df, a);
+            if constexpr (PAIRS) {
+                const float2* row2 = reinterpret_cast<const float2*>(s_rows + lane * pitch);
+                const float2* q2 = reinterpret_cast<const float2*>(s_q);
+#pragma unroll 5
+                for (int c2 = 0; c2 < (d >> 1); ++c2) {
+                    const float2 x = q2[c2], y = row2[c2];
+                    float df = x.x - y.x;
+                    a = fmaf(df, df, a);
+                    df = x.y - y.y;
+                    a = fmaf(df, df, a);
+                }
+            } else {
+                for (int c = 0; c < d; ++c) {
+                    const float df = s_q[c] - s_rows[lane * pitch + c];
+                    a = fmaf(df, df, a);
+                }
             }
             jj = perm[q];
         }
@@ -1002,9 +1042,12 @@ tc_rerank_kernel(const float* __restrict__ Xp, const int32_t* __restrict__ perm,
     }
 }
 
-// Exact re-scan of the uncertified rows over the cells they can reach.  CTA
-// (cell C, listed row r) scans the positions of cell C for row q = rows[r],
-// unless the cell's sphere lies beyond the row's re-ranked k-th distance u.
+// Exact re-scan of the uncertified rows over the cells they can reach.  The
+// cells are cut into chunks of at most CH positions (chunk_beg[C] = the first
+// chunk of cell C; chunks of one cell are consecutive), so that a large cell
+// does not become one long scan.  CTA (chunk y, listed row r) scans chunk y
+// of its cell C for row q = rows[r], unless the cell's sphere lies beyond the
+// row's re-ranked k-th distance u.
 // For a point p of C, |x_q - p| >= |x_q - c_C| - |p - c_C|; the FP32 values
 // D~ of |x_q - c_C| and r~_C >= max |p - c_C| carry a relative error below
 // 1e-5 each (sums of at most 61 squares), and a point that can enter the
@@ -1014,7 +1057,7 @@ tc_rerank_kernel(const float* __restrict__ Xp, const int32_t* __restrict__ perm,
 // sum_c (x_qc - p_c)^2 over the dimensions in order, kept when below the
 // admission bound of the k-th distance, per thread sorted by distance, then
 // merged by (distance, index) within each warp and over the CTA's warps into
-// partial list (C, r), which launch_merge_partials combines over the cells.
+// partial list (y, r), which launch_merge_partials combines over the chunks.
 // Within a cell, positions follow the point index (the cell sort is stable),
 // so every per-thread list is ordered by (distance, index).  The cell's
 // points are staged 128 at a time with asynchronous copies into two
@@ -1022,15 +1065,25 @@ tc_rerank_kernel(const float* __restrict__ Xp, const int32_t* __restrict__ perm,
 static constexpr int RS_THREADS = 128;
 static constexpr int RS_PITCH = 65;  // floats per staged point (d <= 61), odd: conflict-free
 static constexpr size_t RS_SMEM = size_t(2) * RS_THREADS * RS_PITCH * 4;
+static constexpr int64_t RS_CHUNK_MIN = 1024;  // positions per chunk of a cell (at least)
 
-__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+// chunk_beg[C] = sum over cells c < C of ceil(|c| / CH) (one CTA, K <= 128).
+__global__ void tc_chunks_kernel(const int32_t* __restrict__ cell_beg, int K, int32_t CH,
+                                 int32_t* __restrict__ chunk_beg) {
+    if (threadIdx.x != 0) return;
+    int32_t acc = 0;
+    for (int c = 0; c < K; ++c) {
+        chunk_beg[c] = acc;
+        acc += (cell_beg[c + 1] - cell_beg[c] + CH - 1) / CH;
+    }
+    chunk_beg[K] = acc;
 }
 
 template <int KL>
 __global__ void __launch_bounds__(RS_THREADS)
 tc_rescan_kernel(const float* __restrict__ X, const float* __restrict__ Xp, const int32_t* __restrict__ perm,
-                 int d, int k, const int32_t* __restrict__ rows, int cnt, const int32_t* __restrict__ cell_beg,
+                 int d, int k, const int32_t* __restrict__ rows, int cnt, int K, int32_t CH,
+                 const int32_t* __restrict__ cell_beg, const int32_t* __restrict__ chunk_beg,
                  const float* __restrict__ cell_c, const float* __restrict__ cell_r,
                  const float* __restrict__ dist_in, int32_t* __restrict__ pidx, float* __restrict__ pd2) {
     extern __shared__ __align__(16) float s_pts[];   // [2][RS_THREADS][RS_PITCH]
@@ -1038,9 +1091,23 @@ tc_rescan_kernel(const float* __restrict__ X, const float* __restrict__ Xp, cons
     __shared__ float s_part[RS_THREADS / 32];
     __shared__ float s_wd[RS_THREADS / 32][32];
     __shared__ int32_t s_wi[RS_THREADS / 32][32];
-    const int C = blockIdx.x, r = blockIdx.y, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int y = blockIdx.x, r = blockIdx.y, t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int32_t q = rows[r];
-    const int64_t out = (int64_t(C) * cnt + r) * k;
+    const int64_t out = (int64_t(y) * cnt + r) * k;
+    if (y >= chunk_beg[K]) {  // past the last chunk
+        if (t == 0) pidx[out] = -1;
+        return;
+    }
+    int C = 0;  // the cell holding chunk y: the last C with chunk_beg[C] <= y
+    for (int lo = 0, hi = K - 1; lo <= hi;) {
+        const int mid = (lo + hi) >> 1;
+        if (chunk_beg[mid] <= y) {
+            C = mid;
+            lo = mid + 1;
+        } else {
+            hi = mid - 1;
+        }
+    }
     for (int c = t; c < 64; c += RS_THREADS) s_x[c] = c < d ? X[int64_t(q) * d + c] : 0.f;
     __syncthreads();
     float part = 0.f;
@@ -1070,7 +1137,8 @@ tc_rescan_kernel(const float* __restrict__ X, const float* __restrict__ Xp, cons
         D[s2] = T;
         I[s2] = -1;
     }
-    const int32_t b = cell_beg[C], e = cell_beg[C + 1];
+    const int32_t b = cell_beg[C] + (y - chunk_beg[C]) * CH;
+    const int32_t e = cell_beg[C + 1] - b < CH ? cell_beg[C + 1] : b + CH;
     // warp w copies points w, w + 4, ... of a tile, lanes on dimensions
     // (lane, lane + 32)
     auto stage = [&](int32_t p0, float* buf) {
@@ -1287,10 +1355,14 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
     DRGB_CHECK_LAUNCH(c);
     if ((rc = stage_mark(c, 7, st))) return rc;
 
-    tc_rerank_kernel<F16><<<grid_for(n, RR_WARPS, c->num_sms * 8), RR_WARPS * 32, 0, st>>>(
-        Xp, perm, n, d, k, cand_idx, cand_s, norm, resid, maxbits, lbstop, idx_out, dist_out,
-        defer_rows ? defer_rows : fail_rows, defer_count ? defer_count : fail_count);
-    DRGB_CHECK_LAUNCH(c);
+    {
+        auto rr = (d & 1) ? tc_rerank_kernel<F16, false> : tc_rerank_kernel<F16, true>;
+        DRGB_CUDA(c, cudaFuncSetAttribute(rr, cudaFuncAttributeMaxDynamicSharedMemorySize, int(rr_smem(d))));
+        rr<<<grid_for(n, RR_WARPS, c->num_sms * 8), RR_WARPS * 32, rr_smem(d), st>>>(
+            Xp, perm, n, d, k, cand_idx, cand_s, norm, resid, maxbits, lbstop, idx_out, dist_out,
+            defer_rows ? defer_rows : fail_rows, defer_count ? defer_count : fail_count);
+        DRGB_CHECK_LAUNCH(c);
+    }
     if ((rc = stage_mark(c, 9, st))) return rc;
     if (defer_rows) return DRGB_OK;  // the caller re-scans the uncertified rows
     // exact FP32 scan of the uncertified rows (row list on the device, the
@@ -1301,17 +1373,27 @@ static int knn_tc_impl(Ctx* c, const float* X, int64_t n, int d, int k, int32_t*
     DRGB_CUDA(c, cudaMemcpyAsync(&cnt32, fail_count, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     DRGB_CUDA(c, cudaStreamSynchronize(st));
     const int64_t cnt = cnt32 < n ? cnt32 : n;
-    if (cnt > 0 && K > 1 && size_t(cnt) * K * k * 8 + 1024 <= TC_PART_BYTES && cnt <= 65535) {
+    // chunks: at least RS_CHUNK_MIN positions, at most as many as the
+    // partial lists' scratch holds (at most n / CH + K chunks in all)
+    int64_t CH = RS_CHUNK_MIN;
+    const size_t per_list = size_t(cnt > 0 ? cnt : 1) * k * 8;
+    const int64_t max_lists = int64_t((TC_PART_BYTES - 4096) / per_list) - K;
+    if (max_lists > 0 && CH * max_lists < n) CH = (n + max_lists - 1) / max_lists;
+    const int64_t nchunk = (n + CH - 1) / CH + K;
+    if (cnt > 0 && K > 1 && max_lists > 0 && nchunk <= int64_t(INT32_MAX) && cnt <= 65535) {
         Carve pc(part);
-        int32_t* pidx = pc.take<int32_t>(size_t(cnt) * K * k);
-        float* pd2 = pc.take<float>(size_t(cnt) * K * k);
-        const dim3 grid(static_cast<unsigned>(K), static_cast<unsigned>(cnt));
+        int32_t* pidx = pc.take<int32_t>(size_t(cnt) * nchunk * k);
+        float* pd2 = pc.take<float>(size_t(cnt) * nchunk * k);
+        int32_t* chunk_beg = pc.take<int32_t>(TC_CELLS + 1);
+        tc_chunks_kernel<<<1, 32, 0, st>>>(cell_beg, K, int32_t(CH), chunk_beg);
+        DRGB_CHECK_LAUNCH(c);
+        const dim3 grid(static_cast<unsigned>(nchunk), static_cast<unsigned>(cnt));
         auto rs = k <= 16 ? tc_rescan_kernel<16> : tc_rescan_kernel<32>;
         DRGB_CUDA(c, cudaFuncSetAttribute(rs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(RS_SMEM)));
-        rs<<<grid, RS_THREADS, RS_SMEM, st>>>(X, Xp, perm, d, k, fail_rows, int(cnt), cell_beg, cell_c, cell_r,
-                                              dist_out, pidx, pd2);
+        rs<<<grid, RS_THREADS, RS_SMEM, st>>>(X, Xp, perm, d, k, fail_rows, int(cnt), K, int32_t(CH), cell_beg,
+                                              chunk_beg, cell_c, cell_r, dist_out, pidx, pd2);
         DRGB_CHECK_LAUNCH(c);
-        rc = launch_merge_partials(c, pidx, pd2, cnt, K, k, fail_rows, idx_out, dist_out, st);
+        rc = launch_merge_partials(c, pidx, pd2, cnt, int(nchunk), k, fail_rows, idx_out, dist_out, st);
     } else {
         rc = launch_knn_exact_rows_n(c, X, n, d, k, fail_rows, fail_count, cnt, idx_out, dist_out, st, part,
                                      TC_PART_BYTES);
