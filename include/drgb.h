@@ -296,8 +296,7 @@ int drgb_fuzzy_weights(drgb_ctx* ctx, const int32_t* idx, const float* dist, int
  *     n k up to roughly 440 000, e.g. n = 29 000 at k = 15) are rejected
  *     with DRGB_ERR_WORKSPACE before anything is enqueued.
  *   - The first call on each device, with that device current, looks up the
- *     array's device address (cudaGetSymbolAddress); make that first call
- *     before any stream capture.
+ *     array's device address (cudaGetSymbolAddress).
  *   - Every call shares the one array, which keeps the previous call's
  *     contents (each call clears what must start at zero): calls that overlap
  *     on the GPU, from two streams or two host threads, race.
