@@ -122,13 +122,26 @@ __global__ void in_scatter_kernel(const int32_t* __restrict__ idx, int64_t n, in
 // ---------------------------------------------------------------- pass 5
 // Warp per row: every element's destination is its rank (the p values of one
 // row are distinct), so the result is the ascending order regardless of the
-// order the scatter produced.
+// order the scatter produced.  A row of at most 32 elements (the common case:
+// the mean in-degree is k) is held one element per lane and ranked through
+// shuffles; longer rows are ranked by reading the row back.
 __global__ void in_sort_kernel(const int32_t* __restrict__ in_ptr, const int32_t* __restrict__ src,
                                int32_t* __restrict__ dst, int64_t n) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
     for (int64_t j = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n; j += warps) {
         const int32_t b = in_ptr[j], m = in_ptr[j + 1] - b;
+        if (m <= 32) {
+            const int32_t x = lane < m ? src[b + lane] : INT32_MAX;
+            int32_t rank = 0;
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                const int32_t y = __shfl_sync(0xffffffffu, x, t);
+                rank += (t < m && y < x) ? 1 : 0;
+            }
+            if (lane < m) dst[b + rank] = x;
+            continue;
+        }
         for (int32_t a = lane; a < m; a += 32) {
             const int32_t x = src[b + a];
             int32_t rank = 0;

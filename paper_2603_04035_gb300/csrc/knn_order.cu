@@ -13,7 +13,7 @@
 
 namespace drgb {
 
-static constexpr int ORD_SUB = 1536;      // largest subsample for the pivot choice (one CTA; 203 KB at d = 64)
+static constexpr int ORD_SUB = 1536;      // largest subsample for the pivot choice (distance matrix 9.4 MB)
 static constexpr int ORD_PER_PIVOT = 16;  // subsample points per pivot
 static constexpr int ORD_THREADS = 1024;
 static constexpr int ORD_PPT = (ORD_SUB + ORD_THREADS - 1) / ORD_THREADS;  // subsample points per thread
@@ -45,46 +45,54 @@ __global__ void sub_gather_kernel(const float* __restrict__ X, int64_t n, int d,
     }
 }
 
-// Farthest-point sampling in one CTA over the FP16 subsample S (the pivot
-// choice is a heuristic; any deterministic choice is valid).  Pivot 0 is the
-// first subsample point; pivot it + 1 is the subsample point farthest from
-// pivots 0..it (ties: the lowest subsample index).  Each thread keeps the
-// running minimum distances of its ORD_PPT points in registers; one barrier
-// per step (the per-warp maxima are double-buffered by step parity).
-__global__ void __launch_bounds__(ORD_THREADS) fps_cta_kernel(const __half2* __restrict__ S, int64_t n, int m,
-                                                           int pitch, int K, int32_t* __restrict__ pivots) {
-    extern __shared__ __align__(16) uint8_t s_raw[];
-    unsigned long long* s_best = reinterpret_cast<unsigned long long*>(s_raw);  // [2][32]
-    __half2* s_x = reinterpret_cast<__half2*>(s_best + 64);                    // [m][pitch]
-    const int words = m * pitch;
+// Squared distances between the points of the FP16 subsample S, as FP32 sums
+// over the dimension pairs in order: Dm[p m + i] = |s_i - s_p|^2 (block p
+// holds row p; symmetric, since fl(a - b) = -fl(b - a)).
+__global__ void sub_dist_kernel(const __half2* __restrict__ S, int m, int pitch, float* __restrict__ Dm) {
+    extern __shared__ __align__(16) __half2 s_p[];  // [pitch]: point p
+    const int p = blockIdx.x;
+    for (int c = threadIdx.x; c < pitch; c += blockDim.x) s_p[c] = S[int64_t(p) * pitch + c];
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const __half2* xv = S + int64_t(i) * pitch;
+        float sq = 0.f;
 #pragma unroll 4
-    for (int t = threadIdx.x; t < words; t += ORD_THREADS) s_x[t] = S[t];
+        for (int c = 0; c < pitch; ++c) {
+            const float2 a = __half22float2(xv[c]), b = __half22float2(s_p[c]);
+            float df = a.x - b.x;
+            sq = fmaf(df, df, sq);
+            df = a.y - b.y;
+            sq = fmaf(df, df, sq);
+        }
+        Dm[int64_t(p) * m + i] = sq;
+    }
+}
+
+// Farthest-point sampling in one CTA over the subsample's distance matrix Dm
+// (the pivot choice is a heuristic; any deterministic choice is valid).
+// Pivot 0 is the first subsample point; pivot it + 1 is the subsample point
+// farthest from pivots 0..it (ties: the lowest subsample index).  Each thread
+// keeps the running minimum distances of its ORD_PPT points in registers and
+// reads row p of Dm for the new pivot p; one barrier per step (the per-warp
+// maxima are double-buffered by step parity).
+__global__ void __launch_bounds__(ORD_THREADS) fps_cta_kernel(const float* __restrict__ Dm, int64_t n, int m, int K,
+                                                           int32_t* __restrict__ pivots) {
+    __shared__ unsigned long long s_best[2][32];
     float mn[ORD_PPT];
 #pragma unroll
     for (int j = 0; j < ORD_PPT; ++j) mn[j] = INFINITY;
-    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int p = 0;
     for (int it = 0; it < K; ++it) {
         if (threadIdx.x == 0) pivots[it] = int32_t(sub_point(p, n));
         if (it == K - 1) break;
-        const __half2* pv = s_x + p * pitch;
+        const float* row = Dm + int64_t(p) * m;
         unsigned long long best = 0;
 #pragma unroll
         for (int j = 0; j < ORD_PPT; ++j) {
             const int i = threadIdx.x + j * ORD_THREADS;
             if (i < m) {
-                const __half2* xv = s_x + i * pitch;
-                float sq = 0.f;
-#pragma unroll 4
-                for (int c = 0; c < pitch; ++c) {
-                    const float2 a = __half22float2(xv[c]), b = __half22float2(pv[c]);
-                    float df = a.x - b.x;
-                    sq = fmaf(df, df, sq);
-                    df = a.y - b.y;
-                    sq = fmaf(df, df, sq);
-                }
-                mn[j] = fminf(mn[j], sq);
+                mn[j] = fminf(mn[j], row[i]);
                 const unsigned long long key = (uint64_t(__float_as_uint(mn[j])) << 32) | uint64_t(~uint32_t(i));
                 best = key > best ? key : best;
             }
@@ -94,7 +102,7 @@ __global__ void __launch_bounds__(ORD_THREADS) fps_cta_kernel(const __half2* __r
             const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
             best = other > best ? other : best;
         }
-        unsigned long long* sb = s_best + (it & 1) * 32;
+        unsigned long long* sb = s_best[it & 1];
         if (lane == 0) sb[warp] = best;
         __syncthreads();
         unsigned long long bb = sb[lane];  // ORD_THREADS / 32 = 32 warps
@@ -227,8 +235,9 @@ size_t knn_order_scratch_bytes(int64_t n, int d, int K) {
     const int64_t nchunk = (n + ORD_CHUNK - 1) / ORD_CHUNK;
     const size_t kc = size_t(K) * nchunk;
     const int64_t m = n < ORD_SUB ? n : ORD_SUB;
-    return Carve::round(size_t(K) * 4) + Carve::round(size_t(m) * sub_pitch(d) * 4) + Carve::round(size_t(n) * 4) * 2 + 2 * Carve::round(kc * 4) +
-           Carve::round(scan_scratch_elems(int64_t(kc)) * 4) + 4096;
+    return Carve::round(size_t(K) * 4) + Carve::round(size_t(m) * sub_pitch(d) * 4) + Carve::round(size_t(m) * m * 4) +
+           Carve::round(size_t(n) * 4) * 2 + 2 * Carve::round(kc * 4) + Carve::round(scan_scratch_elems(int64_t(kc)) * 4) +
+           4096;
 }
 
 int knn_order(Ctx* c, const float* X, int64_t n, int d, int K, int32_t* perm, int32_t* cell_beg, float* centre,
@@ -244,6 +253,7 @@ int knn_order(Ctx* c, const float* X, int64_t n, int d, int K, int32_t* perm, in
     Carve cv(scratch);
     int32_t* pivots = cv.take<int32_t>(K);
     __half2* S = cv.take<__half2>(size_t(m) * pitch);
+    float* Dm = cv.take<float>(size_t(m) * m);
     int32_t* cell = cv.take<int32_t>(n);
     float* cdist = cv.take<float>(n);
     int32_t* counts = cv.take<int32_t>(kc);
@@ -252,9 +262,9 @@ int knn_order(Ctx* c, const float* X, int64_t n, int d, int K, int32_t* perm, in
 
     sub_gather_kernel<<<grid_for(int64_t(m) * pitch, 256, c->num_sms), 256, 0, st>>>(X, n, d, m, pitch, S);
     DRGB_CHECK_LAUNCH(c);
-    const size_t fsm = 64 * 8 + size_t(m) * pitch * 4;
-    DRGB_CUDA(c, cudaFuncSetAttribute(fps_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fsm)));
-    fps_cta_kernel<<<1, ORD_THREADS, fsm, st>>>(S, n, m, pitch, K, pivots);
+    sub_dist_kernel<<<m, 256, size_t(pitch) * 4, st>>>(S, m, pitch, Dm);
+    DRGB_CHECK_LAUNCH(c);
+    fps_cta_kernel<<<1, ORD_THREADS, 0, st>>>(Dm, n, m, K, pivots);
     DRGB_CHECK_LAUNCH(c);
     // the pivots are the cells' centres; a cell's radius is the largest
     // distance from its points to its pivot (the assignment's own distances)
