@@ -1065,7 +1065,7 @@ tc_rerank_kernel(const float* __restrict__ Xp, const int32_t* __restrict__ perm,
 static constexpr int RS_THREADS = 128;
 static constexpr int RS_PITCH = 65;  // floats per staged point (d <= 61), odd: conflict-free
 static constexpr size_t RS_SMEM = size_t(2) * RS_THREADS * RS_PITCH * 4;
-static constexpr int64_t RS_CHUNK_MIN = 1024;  // positions per chunk of a cell (at least)
+static constexpr int64_t RS_CHUNK_MIN = 2048;  // positions per chunk of a cell (at least)
 
 // chunk_beg[C] = sum over cells c < C of ceil(|c| / CH) (one CTA, K <= 128).
 __global__ void tc_chunks_kernel(const int32_t* __restrict__ cell_beg, int K, int32_t CH,
