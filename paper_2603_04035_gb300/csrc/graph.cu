@@ -120,13 +120,21 @@ __global__ void in_scatter_kernel(const int32_t* __restrict__ idx, int64_t n, in
 }
 
 // ---------------------------------------------------------------- pass 5
-// Warp per row: every element's destination is its rank (the p values of one
-// row are distinct), so the result is the ascending order regardless of the
+// Warp per row, ascending order of the row's (distinct) p values whatever
 // order the scatter produced.  A row of at most 32 elements (the common case:
-// the mean in-degree is k) is held one element per lane and ranked through
-// shuffles; longer rows are ranked by reading the row back.
+// the mean in-degree is k) is held one element per lane and every element
+// goes to its rank, counted through shuffles; rows of up to IS_WARP_MAX
+// elements are ranked by reading the row back for every element.  Longer
+// rows (hubs: at 70K the in-degree reaches 620) of up to IS_BIG_MAX elements
+// are listed in big_rows for in_sort_big_kernel; beyond that the warp ranks
+// them itself.
+static constexpr int IS_WARP_MAX = 128;
+static constexpr int IS_BIG_MAX = 8192;
+static constexpr int IS_BIG_THREADS = 256;
+
 __global__ void in_sort_kernel(const int32_t* __restrict__ in_ptr, const int32_t* __restrict__ src,
-                               int32_t* __restrict__ dst, int64_t n) {
+                               int32_t* __restrict__ dst, int64_t n, int32_t* __restrict__ big_rows,
+                               unsigned int* __restrict__ big_cnt) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
     for (int64_t j = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n; j += warps) {
@@ -142,12 +150,51 @@ __global__ void in_sort_kernel(const int32_t* __restrict__ in_ptr, const int32_t
             if (lane < m) dst[b + rank] = x;
             continue;
         }
+        if (m > IS_WARP_MAX && m <= IS_BIG_MAX) {
+            if (lane == 0) big_rows[atomicAdd(big_cnt, 1u)] = int32_t(j);
+            continue;
+        }
         for (int32_t a = lane; a < m; a += 32) {
             const int32_t x = src[b + a];
             int32_t rank = 0;
             for (int32_t t = 0; t < m; ++t) rank += src[b + t] < x;
             dst[b + rank] = x;
         }
+    }
+}
+
+// CTA per listed row: the row, padded with INT32_MAX to a power of two, is
+// sorted ascending by a bitonic network in shared memory.
+__global__ void __launch_bounds__(IS_BIG_THREADS)
+in_sort_big_kernel(const int32_t* __restrict__ in_ptr, const int32_t* __restrict__ src,
+                   int32_t* __restrict__ dst, const int32_t* __restrict__ big_rows,
+                   const unsigned int* __restrict__ big_cnt) {
+    extern __shared__ int32_t s_row[];  // [IS_BIG_MAX]
+    const unsigned cnt = *big_cnt;
+    for (unsigned r = blockIdx.x; r < cnt; r += gridDim.x) {
+        const int64_t j = big_rows[r];
+        const int32_t b = in_ptr[j], m = in_ptr[j + 1] - b;
+        int P = 2 * IS_WARP_MAX;
+        while (P < m) P <<= 1;
+        __syncthreads();  // the previous row's read-back is done
+        for (int a = threadIdx.x; a < P; a += IS_BIG_THREADS) s_row[a] = a < m ? src[b + a] : INT32_MAX;
+        __syncthreads();
+        for (int kk = 2; kk <= P; kk <<= 1) {
+            for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                for (int a = threadIdx.x; a < P; a += IS_BIG_THREADS) {
+                    const int l = a ^ jj;
+                    if (l > a) {
+                        const int32_t x = s_row[a], y = s_row[l];
+                        if ((x > y) == ((a & kk) == 0)) {
+                            s_row[a] = y;
+                            s_row[l] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int a = threadIdx.x; a < m; a += IS_BIG_THREADS) dst[b + a] = s_row[a];
     }
 }
 
@@ -371,7 +418,18 @@ int build_fuzzy_graph(Ctx* c, const int32_t* idx, const float* dist, int64_t n, 
     if (rc) return rc;
     in_scatter_kernel<<<grid_for(int64_t(nk), TB, gmax), TB, 0, st>>>(idx, n, k, in_ptr, in_fill, in_src);
     DRGB_CHECK_LAUNCH(c);
-    in_sort_kernel<<<grid_for(n, TB / 32, gmax), TB, 0, st>>>(in_ptr, in_src, in_sorted, n);
+    {
+        // rows longer than a warp ranks well go to a CTA each; keep_cnt is
+        // free until the prune pass and holds their list
+        int32_t* big_rows = keep_cnt;
+        unsigned int* big_cnt = wmax + 32;
+        DRGB_CUDA(c, cudaMemsetAsync(big_cnt, 0, 4, st));
+        in_sort_kernel<<<grid_for(n, TB / 32, gmax), TB, 0, st>>>(in_ptr, in_src, in_sorted, n, big_rows, big_cnt);
+        DRGB_CHECK_LAUNCH(c);
+        const size_t big_smem = size_t(IS_BIG_MAX) * 4;
+        in_sort_big_kernel<<<c->num_sms * 2, IS_BIG_THREADS, big_smem, st>>>(in_ptr, in_src, in_sorted, big_rows,
+                                                                              big_cnt);
+    }
     DRGB_CHECK_LAUNCH(c);
     merge_kernel<<<grid_for(n, TB / 32, gmax), TB, 0, st>>>(out_col, out_w, in_ptr, in_sorted, w_dir, n, k,
                                                            tcol, tw, tcnt, wmax);
