@@ -204,8 +204,10 @@ int drgb_stage_times(drgb_ctx* ctx, float* ms, int max);
  * an FP32 re-rank, 3 the same GEMM with FP16 operands (power-of-two scaled;
  * 8x smaller rounding residual at the same tensor-core rate).  In modes 2
  * and 3, rows whose candidate set cannot be certified to contain the exact
- * FP32 k nearest are recomputed by the exact scan, so every mode returns the
- * same exact result.
+ * FP32 k nearest are recomputed by the exact scan (over the spatial cells
+ * each such row can reach), so every mode returns the same exact result;
+ * these modes synchronise `stream` once, to read the number of such rows
+ * (drgb_knn_uncertified reports it).
  * Errors: DRGB_ERR_INVALID if n < k + 1, k < 1, k > DRGB_MAX_K, d < 1,
  * a pointer is NULL or X is not 4-byte aligned. */
 int drgb_knn_graph(drgb_ctx* ctx, const float* X, int64_t n, int32_t d, int32_t k,
